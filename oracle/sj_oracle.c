@@ -1,0 +1,186 @@
+/*
+ * CPU oracle for the sieved multi-way join -- TEST INFRASTRUCTURE ONLY.
+ *
+ * Only the test suite, the package smoke check and the CPU-baseline leg of the
+ * benchmark may load this file's library.  It shares no code, header or
+ * constant table with the CUDA library and is deliberately plain and slow.
+ *
+ * What it computes is the plain definition of the join the method returns:
+ * SieveJoin prunes with Bloom filters, which never drop a matching tuple
+ * (Sec. 1, Sec. 2.1), and then runs an ordinary binary join plan over the pruned
+ * relations (Sec. 2.2, enumeration phase), so the final COUNT / SUM / tuples are
+ * those of the unpruned natural join.  This file holds
+ *
+ *   - a chained-bucket binary hash join level (pairs of matching rows, and the
+ *     aggregate form used at the last level), and
+ *   - a nested-loop enumeration of a whole tree-shaped join (the brute force
+ *     used on tiny inputs).
+ *
+ * COUNT is kept in 128 bits so overflow of 2^63 can be reported; SUM is the
+ * int64 sum taken modulo 2^64 (two's complement wrap), which is order-free.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef unsigned __int128 u128;
+
+/* ---------------- chained hash table over an int32 key column ------------- */
+
+typedef struct {
+    int64_t *head;   /* bucket -> first row, -1 = none */
+    int64_t *next;   /* row -> next row in the same bucket, -1 = end */
+    uint64_t mask;
+} chain_table;
+
+static uint64_t bucket_of(int32_t key, uint64_t mask) {
+    /* Knuth multiplicative hashing; any function works for a chained table. */
+    uint64_t x = (uint64_t)(uint32_t)key * 11400714819323198485ull;
+    return (x >> 29) & mask;
+}
+
+static int chain_build(chain_table *t, const int32_t *keys, int64_t n) {
+    uint64_t nb = 1;
+    while (nb < (uint64_t)(n > 0 ? n : 1)) nb <<= 1;
+    t->mask = nb - 1;
+    t->head = (int64_t *)malloc(nb * sizeof(int64_t));
+    t->next = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+    if (!t->head || !t->next) { free(t->head); free(t->next); return -1; }
+    for (uint64_t b = 0; b < nb; ++b) t->head[b] = -1;
+    for (int64_t r = 0; r < n; ++r) {
+        uint64_t b = bucket_of(keys[r], t->mask);
+        t->next[r] = t->head[b];
+        t->head[b] = r;
+    }
+    return 0;
+}
+
+static void chain_free(chain_table *t) { free(t->head); free(t->next); }
+
+/* Number of (probe row, build row) pairs with equal keys; -1 if out of memory. */
+int64_t orc_join_pairs_count(const int32_t *pk, int64_t np, const int32_t *bk, int64_t nb) {
+    chain_table t;
+    if (chain_build(&t, bk, nb)) return -1;
+    int64_t total = 0;
+    for (int64_t i = 0; i < np; ++i)
+        for (int64_t r = t.head[bucket_of(pk[i], t.mask)]; r >= 0; r = t.next[r])
+            if (bk[r] == pk[i]) ++total;
+    chain_free(&t);
+    return total;
+}
+
+/* Fill the matching pairs, probe-row order; returns 0, or -1 if out of memory. */
+int orc_join_pairs_fill(const int32_t *pk, int64_t np, const int32_t *bk, int64_t nb,
+                        int64_t *out_probe, int64_t *out_build) {
+    chain_table t;
+    if (chain_build(&t, bk, nb)) return -1;
+    int64_t o = 0;
+    for (int64_t i = 0; i < np; ++i)
+        for (int64_t r = t.head[bucket_of(pk[i], t.mask)]; r >= 0; r = t.next[r])
+            if (bk[r] == pk[i]) { out_probe[o] = i; out_build[o] = r; ++o; }
+    chain_free(&t);
+    return 0;
+}
+
+/*
+ * Last join level folded into the aggregate: for every matching pair (i, r)
+ * COUNT += 1 and SUM += psum[i] + bval[r] (mod 2^64).  psum / bval may be NULL
+ * (treated as 0).  out[0..1] = COUNT as a 128-bit value (lo, hi), out[2] = SUM.
+ */
+int orc_join_agg(const int32_t *pk, int64_t np, const uint64_t *psum,
+                 const int32_t *bk, int64_t nb, const uint64_t *bval, uint64_t *out) {
+    chain_table t;
+    if (chain_build(&t, bk, nb)) return -1;
+    u128 count = 0;
+    uint64_t sum = 0;
+    for (int64_t i = 0; i < np; ++i)
+        for (int64_t r = t.head[bucket_of(pk[i], t.mask)]; r >= 0; r = t.next[r])
+            if (bk[r] == pk[i]) {
+                count += 1;
+                sum += (psum ? psum[i] : 0) + (bval ? bval[r] : 0);
+            }
+    chain_free(&t);
+    out[0] = (uint64_t)count;
+    out[1] = (uint64_t)(count >> 64);
+    out[2] = sum;
+    return 0;
+}
+
+/* ---------------- nested-loop brute force over a whole join tree ---------- */
+
+typedef struct {
+    int nrel;
+    const int64_t *nrows;
+    const int32_t *const *cols;   /* relation r, column c at cols[coloff[r] + c] */
+    const int *coloff;
+    int nedge;
+    const int *edges;             /* 4 ints per edge: rel_a, col_a, rel_b, col_b */
+    const int32_t *preds;         /* 3 per relation: col (<0 none), lo, hi */
+    int nagg;
+    const int *agg;               /* 3 per term: rel, col, wide */
+    int64_t *cur;                 /* chosen row per relation */
+    u128 count;
+    uint64_t sum;
+} nl_state;
+
+static int32_t nl_val(const nl_state *s, int rel, int col, int64_t row) {
+    return s->cols[s->coloff[rel] + col][row];
+}
+
+static void nl_rec(nl_state *s, int depth) {
+    if (depth == s->nrel) {
+        uint64_t v = 0;
+        for (int a = 0; a < s->nagg; ++a) {
+            int rel = s->agg[3 * a], col = s->agg[3 * a + 1], wide = s->agg[3 * a + 2];
+            int64_t row = s->cur[rel];
+            int64_t x;
+            if (wide) {
+                uint64_t lo = (uint32_t)nl_val(s, rel, col, row);
+                uint64_t hi = (uint32_t)nl_val(s, rel, col + 1, row);
+                x = (int64_t)(lo | (hi << 32));
+            } else {
+                x = (int64_t)nl_val(s, rel, col, row);
+            }
+            v += (uint64_t)x;
+        }
+        s->count += 1;
+        s->sum += v;
+        return;
+    }
+    for (int64_t row = 0; row < s->nrows[depth]; ++row) {
+        const int32_t *p = s->preds + 3 * depth;
+        if (p[0] >= 0) {
+            int32_t v = nl_val(s, depth, p[0], row);
+            if (v < p[1] || v >= p[2]) continue;
+        }
+        int ok = 1;
+        s->cur[depth] = row;
+        for (int e = 0; e < s->nedge && ok; ++e) {
+            int ra = s->edges[4 * e], ca = s->edges[4 * e + 1];
+            int rb = s->edges[4 * e + 2], cb = s->edges[4 * e + 3];
+            /* check each edge once, when its later relation is chosen */
+            int later = ra > rb ? ra : rb;
+            if (later != depth) continue;
+            if (nl_val(s, ra, ca, s->cur[ra]) != nl_val(s, rb, cb, s->cur[rb])) ok = 0;
+        }
+        if (ok) nl_rec(s, depth + 1);
+    }
+}
+
+/* out[0..1] = COUNT (lo, hi), out[2] = SUM mod 2^64. */
+int orc_nested_loop(int nrel, const int64_t *nrows, const int32_t *const *cols,
+                    const int *coloff, int nedge, const int *edges, const int32_t *preds,
+                    int nagg, const int *agg, uint64_t *out) {
+    nl_state s;
+    s.nrel = nrel; s.nrows = nrows; s.cols = cols; s.coloff = coloff;
+    s.nedge = nedge; s.edges = edges; s.preds = preds; s.nagg = nagg; s.agg = agg;
+    s.cur = (int64_t *)calloc((size_t)nrel, sizeof(int64_t));
+    if (!s.cur) return -1;
+    s.count = 0; s.sum = 0;
+    nl_rec(&s, 0);
+    free(s.cur);
+    out[0] = (uint64_t)s.count;
+    out[1] = (uint64_t)(s.count >> 64);
+    out[2] = s.sum;
+    return 0;
+}

@@ -1,0 +1,327 @@
+"""Pins of the CPU oracle against things other than itself.
+
+Every oracle function is checked here against what the paper or the
+mathematics fixes: hand-worked examples (tests/golden), the closed form of the
+synthetic R, S, T benchmark (Sec. 3.1.1), brute-force enumeration on tiny
+inputs, direct-lookup evaluation of star joins, the Bloom filter's
+no-false-negative property, Eq. 3's expected number of set bits, the
+false-positive rate of the layout, the Bloomjoin cardinality of Eq. 1 (read as
+survivors = semijoin + non-matching x FPR), and the exact inverse of the hash
+mixer.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2308_16370_b300 import inputs
+from conftest import load_golden, workload_from_golden
+
+
+# ------------------------------------------------------------------ joins: hand-worked
+def test_hand_chain3_count_sum_tuples():
+    g = load_golden("hand_chain3.json")
+    w = workload_from_golden(g)
+    for fn in (oracle.hash_join, oracle.nested_loop, oracle.agg_propagation):
+        r = fn(w)
+        assert r["count"] == g["expected_count"]
+        assert r["sum"] == g["expected_sum_a_plus_d"]
+    m = oracle.hash_join(w, mode=oracle.MATERIALIZE,
+                         refs=[(0, 0, 0), (0, 1, 0), (1, 1, 0), (2, 1, 0)])
+    got = sorted(zip(*[c.tolist() for c in m["cols"]]))
+    assert got == sorted(tuple(t) for t in g["expected_tuples_abcd"])
+
+
+def test_hand_chain3_full_reduction_and_sieve_superset():
+    g = load_golden("hand_chain3.json")
+    w = workload_from_golden(g)
+    red = oracle.semijoin_reduction(w)
+    for i, exp in enumerate(g["expected_full_reduction"]):
+        assert [c.tolist() for c in red[i]] == exp
+    sv, _ = oracle.sieve_path(w)
+    for i in range(3):
+        got = set(zip(*[c.tolist() for c in sv[i]]))
+        assert set(zip(*g["expected_full_reduction"][i])) <= got
+
+
+def test_hand_star():
+    g = load_golden("hand_star.json")
+    w = workload_from_golden(g)
+    w["root"] = 0
+    for fn in (oracle.hash_join, oracle.nested_loop, oracle.agg_propagation):
+        r = fn(w)
+        assert (r["count"], r["sum"]) == (g["expected_count"], g["expected_sum"])
+
+
+# ------------------------------------------------------------------ joins: closed form
+@pytest.mark.parametrize("r,d", [(10, 1), (10, 3), (40, 2)])
+def test_freitag_closed_form(r, d):
+    """|R |x| S |x| T| = r d^3 and SUM(R.x) = d^3 * sum of the r common values."""
+    top = 200
+    w = inputs.freitag_rst(r, d, top=top)
+    common = np.arange((top - r) // 2 + 1, (top + r) // 2 + 1)
+    assert len(common) == r
+    exp_sum = d ** 3 * int(common.sum())
+    for fn in (oracle.hash_join, oracle.agg_propagation):
+        res = fn(w)
+        assert res["count"] == r * d ** 3
+        assert res["sum"] == exp_sum
+    if r * d <= 40:
+        res = oracle.nested_loop(w)
+        assert (res["count"], res["sum"]) == (r * d ** 3, exp_sum)
+
+
+# ------------------------------------------------------------------ joins: brute force
+@pytest.mark.parametrize("seed", range(12))
+def test_hash_join_and_propagation_vs_nested_loop(seed):
+    g = np.random.default_rng(100 + seed)
+    nrel = int(g.integers(1, 5))
+    w = inputs.random_tree_join(g, nrel, g.integers(0, 14, nrel), domain=6,
+                                star_like=bool(seed % 3 == 0))
+    bf = oracle.nested_loop(w)
+    hj = oracle.hash_join(w)
+    ap = oracle.agg_propagation(w)
+    assert (hj["count"], hj["sum"]) == (bf["count"], bf["sum"])
+    assert (ap["count"], ap["sum"]) == (bf["count"], bf["sum"])
+    m = oracle.hash_join(w, mode=oracle.MATERIALIZE)
+    assert m["count"] == bf["count"]
+
+
+def test_negative_values_and_wide_sum():
+    """SUM is int64 modulo 2^64: negative values and 64-bit (two-word) terms."""
+    g = np.random.default_rng(7)
+    R = [g.integers(-5, 5, 30, dtype=np.int32), g.integers(0, 4, 30, dtype=np.int32)]
+    big = g.integers(-(1 << 62), 1 << 62, 25, dtype=np.int64)
+    S = [g.integers(0, 4, 25, dtype=np.int32),
+         (big & 0xFFFFFFFF).astype(np.uint32).view(np.int32), (big >> 32).astype(np.int32)]
+    w = {"rels": [R, S], "edges": [(0, 1, 1, 0)], "preds": [None, None], "root": 1,
+         "sum": [(0, 0, 0), (1, 1, 1)]}
+    exp_c, exp_s = 0, 0
+    for i in range(30):
+        for j in range(25):
+            if R[1][i] == S[0][j]:
+                exp_c += 1
+                exp_s += int(R[0][i]) + int(big[j])
+    exp_s %= 1 << 64
+    for fn in (oracle.hash_join, oracle.nested_loop, oracle.agg_propagation):
+        r = fn(w)
+        assert (r["count"], r["sum"]) == (exp_c, exp_s)
+
+
+def test_star_direct_lookup():
+    """Dense-key dimensions: COUNT/SUM by direct indexing of the dimension rows."""
+    w = inputs.star(nfact=20000, ndim=3, dim_rows=500, sel=0.3, seed=11)
+    fact = w["rels"][0]
+    ok = np.ones(len(fact[0]), dtype=bool)
+    for i in range(3):
+        pk, attr = w["rels"][1 + i]
+        _, lo, hi = w["preds"][1 + i]
+        assert np.array_equal(pk, np.arange(500))
+        a = attr[fact[i]]
+        ok &= (a >= lo) & (a < hi)
+    meas = fact[3].view(np.uint32).astype(np.int64) | (fact[4].astype(np.int64) << 32)
+    exp = (int(ok.sum()), int(meas[ok].sum()) % (1 << 64))
+    for fn in (oracle.hash_join, oracle.agg_propagation):
+        r = fn(w)
+        assert (r["count"], r["sum"]) == exp
+
+
+def test_agg_propagation_overflow_flag():
+    """COUNT >= 2^63 is reported: 4 relations of 2^16 rows all on key 0 give 2^64."""
+    n = 1 << 16
+    z = np.zeros(n, dtype=np.int32)
+    w = {"rels": [[z, z]] * 4, "edges": inputs.chain_edges(4), "preds": [None] * 4,
+         "root": 3, "sum": []}
+    r = oracle.agg_propagation(w)
+    assert r["overflow"] and r["count"] == 0 and r["count_approx"] == 2.0 ** 64
+
+
+# ------------------------------------------------------------------ hash mixer
+def test_fmix64_inverse_and_fixed_point():
+    """fmix64 is a bijection: undo it with the modular inverses of its
+    multipliers (derived here, not typed in) and inverse xor-shifts."""
+    C1, C2 = 0xFF51AFD7ED558CCD, 0xC4CEB9FE1A85EC53
+    M = (1 << 64) - 1
+    i1, i2 = pow(C1, -1, 1 << 64), pow(C2, -1, 1 << 64)
+
+    def unshift33(y):
+        return y ^ (y >> 33)  # 33 >= 64/2, so one step inverts x ^= x >> 33
+
+    g = np.random.default_rng(3)
+    xs = [int(v) for v in g.integers(0, 1 << 63, 200, dtype=np.int64)] + [0, 1, M, 1 << 63]
+    hs = oracle.fmix64(np.array(xs, dtype=np.uint64))
+    for x, h in zip(xs, hs.tolist()):
+        y = unshift33(int(h))
+        y = (y * i2) & M
+        y = unshift33(y)
+        y = (y * i1) & M
+        y = unshift33(y)
+        assert y == x
+    assert int(oracle.fmix64(np.array([0], dtype=np.uint64))[0]) == 0
+
+
+def test_fmix64_avalanche():
+    g = np.random.default_rng(5)
+    x = g.integers(0, 1 << 63, 20000, dtype=np.int64).astype(np.uint64)
+    h0 = oracle.fmix64(x)
+    for b in (0, 7, 31, 32, 63):
+        h1 = oracle.fmix64(x ^ np.uint64(1 << b))
+        d = np.unpackbits((h0 ^ h1).view(np.uint8)).reshape(-1, 64).sum(1)
+        assert abs(d.mean() - 32) < 0.3
+
+
+# ------------------------------------------------------------------ Bloom filter
+@pytest.mark.parametrize("layout", [oracle.BLOCKED256, oracle.CLASSIC])
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
+def test_bloom_no_false_negatives(layout, k):
+    g = np.random.default_rng(k)
+    keys = g.integers(-(1 << 31), (1 << 31) - 1, 5000, dtype=np.int64).astype(np.int32)
+    keys[:3] = [np.iinfo(np.int32).min, np.iinfo(np.int32).max, 0]
+    f = oracle.bloom_build(keys, 8, k, layout, seed=123)
+    assert f["words"].size == 8 * oracle.bloom_nblocks(5000, 8)
+    assert oracle.bloom_contains(f, keys).all()
+
+
+def test_bloom_classic_k1_is_a_hashed_bitset():
+    """k = 1 CLASSIC reduces to a bitset indexed by (low 32 bits of h) mod m."""
+    g = np.random.default_rng(9)
+    keys = g.integers(0, 1 << 30, 3000, dtype=np.int64).astype(np.int32)
+    probe = g.integers(0, 1 << 30, 20000, dtype=np.int64).astype(np.int32)
+    f = oracle.bloom_build(keys, 8, 1, oracle.CLASSIC, seed=5)
+    m = 256 * f["nblocks"]
+    slot = lambda ks: set((oracle.key_hash(ks, 5) & np.uint64(0xFFFFFFFF)) % np.uint64(m))
+    ins = slot(keys)
+    exp = np.array([int(s) in ins for s in
+                    ((oracle.key_hash(probe, 5) & np.uint64(0xFFFFFFFF)) % np.uint64(m))])
+    assert np.array_equal(oracle.bloom_contains(f, probe), exp)
+    bits = np.unpackbits(f["words"].view(np.uint8), bitorder="little")
+    assert bits.sum() == len(ins)
+
+
+def test_bloom_blocked_bits_stay_in_one_block():
+    """Each key sets 1..k bits, all inside one aligned 256-bit block."""
+    g = np.random.default_rng(10)
+    for key in g.integers(-(1 << 31), (1 << 31) - 1, 50, dtype=np.int64).astype(np.int32):
+        f = oracle.bloom_build(np.array([key] * 1 + [], dtype=np.int32), 8 * 256 * 4, 3,
+                               oracle.BLOCKED256, seed=1)
+        nz = np.nonzero(f["words"])[0]
+        assert len(set(nz // 8)) == 1
+        bits = np.unpackbits(f["words"].view(np.uint8)).sum()
+        assert 1 <= bits <= 3
+
+
+def _poisson_mix(lam, fn, jmax=None):
+    jmax = jmax or int(lam + 12 * math.sqrt(lam) + 30)
+    p = math.exp(-lam)
+    tot = 0.0
+    for j in range(jmax):
+        tot += p * fn(j)
+        p *= lam / (j + 1)
+    return tot
+
+
+@pytest.mark.parametrize("k", [1, 3])
+def test_eq3_expected_set_bits(k):
+    """Eq. 3: F(1 - e^{-D/F}) bits are set (k = 1), generalised to
+    m(1 - e^{-kD/m}) for k hashes; BLOCKED256 follows the Poisson mixture over
+    block loads of 256(1 - (1 - 1/256)^{kj})."""
+    g = np.random.default_rng(20 + k)
+    D = 200_000
+    keys = g.choice(1 << 30, D, replace=False).astype(np.int32)
+    for layout in (oracle.CLASSIC, oracle.BLOCKED256):
+        f = oracle.bloom_build(keys, 8, k, layout, seed=77)
+        m = 256 * f["nblocks"]
+        got = int(np.unpackbits(f["words"].view(np.uint8)).sum())
+        if layout == oracle.CLASSIC:
+            exp = m * (1 - math.exp(-k * D / m))
+        else:
+            lam = D / f["nblocks"]
+            exp = f["nblocks"] * _poisson_mix(lam, lambda j: 256 * (1 - (1 - 1 / 256) ** (k * j)))
+        assert abs(got - exp) / exp < 0.01, (layout, got, exp)
+
+
+@pytest.mark.parametrize("bpk,k", [(8, 3), (4, 2), (16, 4)])
+def test_false_positive_rate(bpk, k):
+    """FPR of CLASSIC against (1 - e^{-kn/m})^k, of BLOCKED256 against the
+    Poisson mixture sum_j P(j) (1 - (1 - 1/256)^{kj})^k, within a 4-sigma
+    binomial band plus a 4% model allowance."""
+    g = np.random.default_rng(bpk * 10 + k)
+    n = 100_000
+    keys = g.choice(1 << 29, n, replace=False).astype(np.int32)
+    neg = (g.choice(1 << 29, 1_000_000, replace=False) + (1 << 29)).astype(np.int32)
+    for layout in (oracle.CLASSIC, oracle.BLOCKED256):
+        f = oracle.bloom_build(keys, bpk, k, layout, seed=99)
+        m = 256 * f["nblocks"]
+        fpr = oracle.bloom_contains(f, neg).mean()
+        if layout == oracle.CLASSIC:
+            exp = (1 - math.exp(-k * n / m)) ** k
+        else:
+            lam = n / f["nblocks"]
+            exp = _poisson_mix(lam, lambda j: (1 - (1 - 1 / 256) ** (k * j)) ** k)
+        sig = math.sqrt(exp * (1 - exp) / len(neg))
+        assert abs(fpr - exp) <= 4 * sig + 0.04 * exp, (layout, fpr, exp)
+
+
+def test_bloomjoin_cardinality_eq1():
+    """Eq. 1 as read here: survivors of T = SC_T + (C_T - SC_T) * FPR."""
+    g = np.random.default_rng(31)
+    S = g.integers(0, 400_000, 50_000, dtype=np.int32)
+    T = g.integers(0, 400_000, 300_000, dtype=np.int32)
+    f = oracle.bloom_build(S, 8, 3, oracle.CLASSIC, seed=4)
+    kept = oracle.sieve([T], [(0, f)])[0]
+    sc = int(np.isin(T, S).sum())
+    D = len(np.unique(S))
+    m = 256 * f["nblocks"]
+    fpr = (1 - math.exp(-3 * D / m)) ** 3
+    exp = sc + (len(T) - sc) * fpr
+    sig = math.sqrt((len(T) - sc) * fpr)
+    assert abs(len(kept) - exp) <= 4 * sig + 0.04 * (len(T) - sc) * fpr
+
+
+# ------------------------------------------------------------------ sieve path
+@pytest.mark.parametrize("seed", range(8))
+@pytest.mark.parametrize("passes", [oracle.FWD_BWD, oracle.BWD_ONLY])
+def test_sieve_path_superset_and_same_join(seed, passes):
+    """No false negatives: every sieved relation contains its exact full
+    reduction, keeps input order, and the join over it is unchanged."""
+    g = np.random.default_rng(200 + seed)
+    nrel = int(g.integers(2, 5))
+    w = inputs.random_tree_join(g, nrel, g.integers(0, 60, nrel), domain=20,
+                                star_like=bool(seed % 2))
+    # tag rows with their index to check order and containment
+    tagged = dict(w, rels=[r + [np.arange(len(r[0]), dtype=np.int32)] for r in w["rels"]])
+    sv, steps = oracle.sieve_path(tagged, passes=passes, bits_per_key=2, k=1, seed=seed)
+    red = oracle.semijoin_reduction(tagged)
+    for i in range(nrel):
+        ids = sv[i][-1]
+        assert np.all(np.diff(ids) > 0)
+        assert set(red[i][-1].tolist()) <= set(ids.tolist())
+        sel = oracle.select(tagged["rels"][i], w["preds"][i])
+        assert set(ids.tolist()) <= set(sel[-1].tolist())
+    base = oracle.hash_join(w)
+    sj = oracle.hash_join(w, rels=[r[:-1] for r in sv], presieved=True)
+    assert (sj["count"], sj["sum"]) == (base["count"], base["sum"])
+    nsieve = sum(1 for s in steps if s[0] in ("fwd", "bwd"))
+    exp_steps = 2 * (nrel - 1) if passes == oracle.FWD_BWD else nrel - 1
+    # in pass 1 a node with several children is sieved once by all of them
+    assert nsieve <= exp_steps
+
+
+def test_sieve_path_chain_step_count():
+    """Forward then backward over an n-way chain: 2(n-1) sieve steps."""
+    w = inputs.uniform_chain(nrel=4, nrows=1000, domain=3000, seed=3)
+    _, steps = oracle.sieve_path(w)
+    assert [s[0] for s in steps] == ["fwd"] * 3 + ["bwd"] * 3
+    assert [s[1] for s in steps] == [1, 2, 3, 2, 1, 0]
+
+
+def test_sieve_shrinks_skewed_chain():
+    """The sieve drops most tuples of a chain whose last relation covers 1% of
+    the key domain, and the join result is unchanged."""
+    w = inputs.zipf_chain(nrows=20000, domain=10000, seed=4)
+    sv, steps = oracle.sieve_path(w)
+    assert sum(len(r[0]) for r in sv) < 0.5 * sum(len(r[0]) for r in w["rels"])
+    a = oracle.agg_propagation(w)
+    b = oracle.agg_propagation(w, rels=sv, presieved=True)
+    assert (a["count"], a["sum"]) == (b["count"], b["sum"])
