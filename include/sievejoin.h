@@ -1,0 +1,305 @@
+/*
+ * sievejoin.h -- C ABI of the B300 (sm_103a) sieved multi-way join library.
+ *
+ * SieveJoin (Sec. 2.2) answers a multi-way equi-join in two phases:
+ *   1. pruning: Bloom filters are built on join keys and propagated along the
+ *      join path; every relation keeps only the tuples whose join keys pass
+ *      the filters arriving from its neighbours (Bloomjoin, Sec. 2.1, extended
+ *      to n relations), so tuples that cannot reach the result die early;
+ *   2. enumeration: an ordinary binary join plan (here a hash join) runs over
+ *      the pruned relations.
+ * Bloom filters have no false negatives (Sec. 1), so the result is exactly the
+ * natural join of the unpruned relations.
+ *
+ * Conventions shared by every entry point
+ *   - A context owns one CUDA device and one stream.  Every call enqueues its
+ *     work on that stream in call order.  Calls on one context must not run
+ *     concurrently from several host threads.
+ *   - Columns are int32, column-major (one contiguous array per column),
+ *     16-byte aligned device memory.  Relations have at most SJ_MAX_COLS
+ *     columns and fewer than 2^31 rows.  Any int32 value is a valid key.
+ *   - Return value: SJ_OK (0) or an error code.  sj_last_error() gives a
+ *     one-line description of the last failure on a context.  A failed call
+ *     leaves its output arguments untouched and frees what it allocated.
+ *   - Device memory is taken from the allocator given to sj_create (or, when
+ *     none is given, from the device's stream-ordered pool via
+ *     cudaMallocAsync on the context stream).
+ *   - Device-side waits (the look-back of the compaction scans and the probe
+ *     chains of the hash tables) are bounded: when a bound is hit the kernel
+ *     records the error in a device status word and returns; the next call
+ *     that synchronises reports SJ_ETIMEOUT or SJ_ETABLEFULL.
+ */
+#ifndef SIEVEJOIN_H
+#define SIEVEJOIN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define SJ_API __attribute__((visibility("default")))
+#else
+#define SJ_API
+#endif
+
+#define SJ_MAX_COLS 8    /* columns per relation */
+#define SJ_MAX_REL 8     /* relations per join path */
+#define SJ_MAX_PROBES 4  /* filters probed by one sieve step */
+#define SJ_MAX_TERMS 8   /* SUM terms / projected output columns */
+
+typedef int sj_status;
+enum {
+    SJ_OK = 0,
+    SJ_EINVAL = 1,      /* bad argument: null pointer, column out of range, not a tree, ... */
+    SJ_ENOMEM = 2,      /* the allocator returned NULL */
+    SJ_ETABLEFULL = 3,  /* a hash-table probe chain exceeded its bound */
+    SJ_ETIMEOUT = 4,    /* a bounded device wait gave up */
+    SJ_EOVERFLOW = 5,   /* COUNT(*) reached 2^63 */
+    SJ_ECUDA = 6        /* a CUDA runtime call failed; see sj_last_error */
+};
+
+typedef struct sj_ctx sj_ctx;
+typedef struct sj_rel_s *sj_rel;
+typedef struct sj_filter_s *sj_filter;
+
+/* Allocator callbacks: return 256-byte aligned device memory, or NULL. */
+typedef void *(*sj_alloc_fn)(size_t bytes, void *user);
+typedef void (*sj_free_fn)(void *ptr, size_t bytes, void *user);
+
+/* ------------------------------------------------------------------ context */
+
+/*
+ * Create a context on `device` that enqueues on `cuda_stream` (a cudaStream_t;
+ * NULL = the legacy default stream).  `alloc`/`free_` may both be NULL (use
+ * cudaMallocAsync / cudaFreeAsync on the stream) or both be set; `user` is
+ * passed back to them.  The context owns a small device status word and a
+ * scratch area for the compaction scans.
+ */
+SJ_API sj_status sj_create(sj_ctx **out, int device, void *cuda_stream, sj_alloc_fn alloc,
+                    sj_free_fn free_, void *user);
+/* Synchronise the stream and release everything the context still owns. */
+SJ_API sj_status sj_destroy(sj_ctx *ctx);
+/* Wait for all work enqueued on the context; report device-side errors. */
+SJ_API sj_status sj_sync(sj_ctx *ctx);
+SJ_API const char *sj_last_error(const sj_ctx *ctx);
+SJ_API const char *sj_status_str(sj_status s);
+/* Library version as "major.minor.patch". */
+SJ_API const char *sj_version(void);
+
+/* ---------------------------------------------------------------- relations */
+
+enum {
+    SJ_DEVICE_BORROW = 0, /* keep the caller's device pointers; they must outlive the handle */
+    SJ_DEVICE_COPY = 1,   /* copy device columns into library memory */
+    SJ_HOST_COPY = 2      /* copy host columns (pinned memory is fastest) to the device */
+};
+
+/*
+ * Load a columnar relation (the paper's storage is column-oriented, Sec. 3.1).
+ * `cols` is an array of `ncols` column pointers with `nrows` int32 values
+ * each.  With SJ_HOST_COPY the copies are enqueued on the context stream and
+ * the host buffers must stay valid until the next sj_sync (or any call that
+ * synchronises).  Errors: SJ_EINVAL (ncols outside 1..SJ_MAX_COLS, nrows < 0
+ * or >= 2^31, a null or misaligned device pointer), SJ_ENOMEM.
+ */
+SJ_API sj_status sj_load_relation(sj_ctx *ctx, int ncols, const int32_t *const *cols, int64_t nrows,
+                           int where, sj_rel *out);
+/* Row count (host-known for every handle this library returns), column count and
+ * device column pointers (array of SJ_MAX_COLS entries; may be NULL). */
+SJ_API sj_status sj_rel_info(sj_rel rel, int64_t *nrows, int *ncols, const int32_t **cols);
+SJ_API sj_status sj_free_rel(sj_ctx *ctx, sj_rel rel);
+
+/* ------------------------------------------------------------ Bloom filters */
+
+enum { SJ_BLOCKED256 = 0, SJ_CLASSIC = 1 };
+
+/*
+ * Filter parameters.  The paper sizes Bloomjoin's filter at one bit per tuple
+ * (Sec. 2.1 step 2) and leaves the hash family open (Sec. 1 cites Kirsch and
+ * Mitzenmacher).  Here: h = fmix64(uint32(key) xor seed) (MurmurHash3's
+ * finaliser); m = 256 * max(1, ceil(bits_per_key * n / 256)) bits for n
+ * inserted rows.
+ *   SJ_BLOCKED256: block b = ((h >> 32) * nblocks) >> 32; bits (h >> 8i) & 255,
+ *                  i < k, inside the 256-bit block (eight uint32 words); k <= 4.
+ *   SJ_CLASSIC:    bits (h1 + i*h2) mod m, h1 = h & 0xffffffff,
+ *                  h2 = (h >> 32) | 1; k <= 8.
+ * Word w of the filter holds bits 32w..32w+31, least significant bit first.
+ * Defaults (a zeroed struct is read as): bits_per_key 8, k 3, BLOCKED256, seed 0.
+ */
+typedef struct {
+    uint32_t bits_per_key;
+    uint32_t k;
+    uint32_t layout;
+    uint32_t reserved;
+    uint64_t seed;
+} sj_filter_params;
+
+/* Range predicate lo <= rel[col] < hi on one relation; col < 0 means none. */
+typedef struct {
+    int32_t col;
+    int32_t lo;
+    int32_t hi;
+} sj_pred;
+
+/*
+ * Build a Bloom filter over column `key_col` of `rel` (Sec. 2.1 step 1), from
+ * the rows passing `pred` (NULL = all rows).  The handle is reusable across
+ * queries (Sec. 2.3): pass it to sj_sieve any number of times.  Errors:
+ * SJ_EINVAL, SJ_ENOMEM, SJ_ECUDA.
+ */
+SJ_API sj_status sj_build_filter(sj_ctx *ctx, sj_rel rel, int key_col, const sj_pred *pred,
+                          const sj_filter_params *params, sj_filter *out);
+/* Synchronise, then report the block count, inserted rows and the device word
+ * array (nblocks * 8 uint32 words). */
+SJ_API sj_status sj_filter_info(sj_ctx *ctx, sj_filter f, uint64_t *nblocks, uint64_t *n_inserted,
+                         const uint32_t **words);
+/* Membership test of n device keys (Sec. 2.1 step 3): out[i] = 1 if keys[i]
+ * may be in the filter, 0 if it certainly is not.  out is n device bytes. */
+SJ_API sj_status sj_filter_probe(sj_ctx *ctx, sj_filter f, const int32_t *keys, int64_t n,
+                          uint8_t *out);
+SJ_API sj_status sj_free_filter(sj_ctx *ctx, sj_filter f);
+
+/*
+ * One sieve step (Sec. 2.2, pruning phase): keep, in input order, the rows of
+ * `rel` that pass `pred` (NULL = none) and whose column key_cols[j] passes
+ * filters[j] for every j < nprobe (0 <= nprobe <= SJ_MAX_PROBES).  The kept
+ * rows (all columns) go to a new relation handle.  Synchronises to learn the
+ * row count, which it also writes to *nrows_out when that is not NULL.
+ */
+SJ_API sj_status sj_sieve(sj_ctx *ctx, sj_rel rel, int nprobe, const int *key_cols,
+                   const sj_filter *filters, const sj_pred *pred, sj_rel *out,
+                   int64_t *nrows_out);
+
+/* ---------------------------------------------------------------- join path */
+
+/* Equality rel_a.col_a = rel_b.col_b. */
+typedef struct {
+    int32_t rel_a, col_a, rel_b, col_b;
+} sj_edge;
+
+/*
+ * A tree-shaped equi-join over nrel relations (a chain R1 - R2 - ... - Rn is
+ * the paper's running case, Sec. 2.2; a star is the bitvector-filtering case
+ * of Sec. 1).  nrel - 1 edges must connect all relations without a cycle.
+ * `root` is where pass 1 of the sieve ends (-1 = the last relation, so that a
+ * chain is pruned R1 -> Rn and then Rn -> R1).  `preds` is NULL or holds
+ * one predicate per relation (col < 0 for none).
+ */
+typedef struct {
+    int32_t nrel;
+    int32_t root;
+    const sj_rel *rels;
+    const sj_edge *edges;
+    const sj_pred *preds;
+} sj_path;
+
+enum {
+    SJ_FWD_BWD = 0,  /* pass 1 toward the root, then pass 2 back to the leaves (Sec. 2.2) */
+    SJ_BWD_ONLY = 1, /* the paper's one-pass backward pruning: pass 2 only */
+    SJ_NO_SIEVE = 2  /* apply the predicates only */
+};
+
+typedef struct {
+    int32_t passes;
+    int32_t reserved;
+    sj_filter_params filter;
+} sj_sieve_opts;
+
+#define SJ_MAX_STEPS 32
+typedef struct {
+    int32_t nsteps;
+    int32_t reserved;
+    struct {
+        int32_t kind; /* 0 = predicate select, 1 = pass-1 sieve, 2 = pass-2 sieve */
+        int32_t rel;
+        int64_t rows_in;
+        int64_t rows_out;
+    } step[SJ_MAX_STEPS];
+    int64_t rows_final[SJ_MAX_REL];
+    uint64_t filter_bytes; /* device bytes of all filters built */
+} sj_sieve_stats;
+
+/*
+ * The whole pruning phase (Sec. 2.2).  Predicates are applied first.  Pass 1
+ * visits the join tree from the leaves to the root: a relation is sieved by
+ * the filters of its children, then builds -- from its surviving rows only
+ * -- the filter it sends to its parent.  Pass 2 walks from the root back to
+ * the leaves: each relation is sieved by the filter its parent built from the
+ * parent's surviving rows.  On return out_sieved[i] is a new handle holding
+ * relation i's surviving rows in input order (free with sj_free_rel).  The
+ * join over them equals the join over the inputs.  Synchronises once at the
+ * end.  `opts` NULL = SJ_FWD_BWD with default filter parameters; `stats` may
+ * be NULL.
+ */
+SJ_API sj_status sj_sieve_path(sj_ctx *ctx, const sj_path *path, const sj_sieve_opts *opts,
+                        sj_rel *out_sieved, sj_sieve_stats *stats);
+
+enum { SJ_COUNT_SUM = 0, SJ_MATERIALIZE = 1 };
+
+/* A column reference: SUM term or projected output column.  wide = 1 reads an
+ * int64 stored as two int32 columns col (low word) and col + 1 (high word). */
+typedef struct {
+    int32_t rel, col, wide, reserved;
+} sj_colref;
+
+typedef struct {
+    uint64_t count;          /* COUNT(*), exact */
+    uint64_t sum;            /* SUM of the terms as int64, two's complement mod 2^64 */
+    uint64_t intermediate;   /* tuples materialised by the non-final join levels */
+    sj_rel rows;             /* SJ_MATERIALIZE: one column per ref, caller frees */
+} sj_result;
+
+/*
+ * The enumeration phase (Sec. 2.2): a left-deep binary hash join over the
+ * path.  It starts at relation 0 and repeatedly adds the lowest-index
+ * relation adjacent to those already joined.  Every non-final level builds an
+ * open-addressing hash table on the new relation and materialises the
+ * intermediate tuples (only the columns later levels need).
+ *   SJ_COUNT_SUM: the last level probes a per-key (count, sum) table and
+ *     accumulates COUNT(*) and SUM over `refs` (int64 per result tuple,
+ *     wrapped mod 2^64); result->rows is NULL.
+ *   SJ_MATERIALIZE: result->rows holds one int32 column per ref (wide must be
+ *     0), rows in unspecified order.
+ * `inputs` NULL joins the path's own relations after applying its predicates;
+ * otherwise inputs[i] replaces relation i and is taken as already filtered by
+ * predicate i (the output of sj_sieve_path).  Synchronises at every level.
+ * Errors: SJ_EINVAL, SJ_ENOMEM, SJ_EOVERFLOW (COUNT >= 2^63), SJ_ETABLEFULL,
+ * SJ_ETIMEOUT, SJ_ECUDA.
+ */
+SJ_API sj_status sj_join(sj_ctx *ctx, const sj_path *path, const sj_rel *inputs, int mode, int nrefs,
+                  const sj_colref *refs, sj_result *result);
+
+/* ---------------------------------------------------------------- profiling */
+
+enum {
+    SJ_K_BLOOM_BUILD = 0,   /* Bloom filter build */
+    SJ_K_SIEVE = 1,         /* probe + stream compaction (also predicate selects) */
+    SJ_K_HT_BUILD = 2,      /* hash-table inserts, offsets scan and row scatter */
+    SJ_K_HT_PROBE = 3,      /* probe + match compaction of a join level */
+    SJ_K_HT_EXPAND = 4,     /* intermediate-tuple output of a join level */
+    SJ_K_AGG = 5,           /* per-key aggregate table build and final probe */
+    SJ_K_OTHER = 6,
+    SJ_K_COUNT = 7
+};
+
+/*
+ * Per-kernel-class timing with CUDA events recorded on the context stream
+ * around every launch while enabled.  sj_prof_read synchronises and returns,
+ * for class `kind`: launches, summed device milliseconds and the summed
+ * algorithmic bytes (the bytes the operation must move, counted from its
+ * inputs and outputs).  sj_counters reports, since the last sj_prof_reset,
+ * every kernel this library launched on the context (profiled or not) and
+ * the bytes it copied host-to-device and device-to-host.
+ */
+SJ_API sj_status sj_prof_enable(sj_ctx *ctx, int on);
+SJ_API sj_status sj_prof_reset(sj_ctx *ctx);
+SJ_API sj_status sj_prof_read(sj_ctx *ctx, int kind, int64_t *launches, double *ms, double *bytes);
+SJ_API sj_status sj_counters(sj_ctx *ctx, int64_t *launches, int64_t *h2d_bytes, int64_t *d2h_bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SIEVEJOIN_H */

@@ -1,0 +1,441 @@
+"""B300-native sieved multi-way join (SieveJoin, arXiv 2308.16370).
+
+Thin Python binding over the C ABI of ``libsievejoin.so`` (``include/sievejoin.h``):
+argument marshalling only, every step runs in the CUDA kernels.  PyTorch
+provides device memory, streams and zero-copy views of result columns.
+
+The library must be built first (``python -m paper_2308_16370_b300.build``);
+there is no CPU fallback, and every entry point raises if the CUDA library or
+a GPU is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+__all__ = ["Context", "Relation", "Filter", "SieveJoinError", "load_library", "LIB_PATH",
+           "BLOCKED256", "CLASSIC", "FWD_BWD", "BWD_ONLY", "NO_SIEVE", "COUNT_SUM",
+           "MATERIALIZE", "KERNEL_KINDS"]
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libsievejoin.so")
+
+BLOCKED256, CLASSIC = 0, 1
+FWD_BWD, BWD_ONLY, NO_SIEVE = 0, 1, 2
+COUNT_SUM, MATERIALIZE = 0, 1
+DEVICE_BORROW, DEVICE_COPY, HOST_COPY = 0, 1, 2
+MAX_COLS, MAX_REL, MAX_PROBES, MAX_TERMS, MAX_STEPS = 8, 8, 4, 8, 32
+KERNEL_KINDS = {"bloom_build": 0, "sieve": 1, "ht_build": 2, "ht_probe": 3, "ht_expand": 4,
+                "agg": 5, "other": 6}
+STATUS = {0: "ok", 1: "invalid argument", 2: "out of device memory", 3: "hash table full",
+          4: "device wait timed out", 5: "COUNT overflow", 6: "CUDA error"}
+
+# exported symbols of the C ABI (checked by the CPU tests against the header)
+EXPORTS = ["sj_create", "sj_destroy", "sj_sync", "sj_last_error", "sj_status_str", "sj_version",
+           "sj_load_relation", "sj_rel_info", "sj_free_rel", "sj_build_filter", "sj_filter_info",
+           "sj_filter_probe", "sj_free_filter", "sj_sieve", "sj_sieve_path", "sj_join",
+           "sj_prof_enable", "sj_prof_reset", "sj_prof_read", "sj_counters"]
+
+
+class SieveJoinError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+# ----------------------------------------------------------------------------- ctypes mirror
+class FilterParams(ctypes.Structure):
+    _fields_ = [("bits_per_key", ctypes.c_uint32), ("k", ctypes.c_uint32),
+                ("layout", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("seed", ctypes.c_uint64)]
+
+
+class Pred(ctypes.Structure):
+    _fields_ = [("col", ctypes.c_int32), ("lo", ctypes.c_int32), ("hi", ctypes.c_int32)]
+
+
+class Edge(ctypes.Structure):
+    _fields_ = [("rel_a", ctypes.c_int32), ("col_a", ctypes.c_int32),
+                ("rel_b", ctypes.c_int32), ("col_b", ctypes.c_int32)]
+
+
+class Path(ctypes.Structure):
+    _fields_ = [("nrel", ctypes.c_int32), ("root", ctypes.c_int32),
+                ("rels", ctypes.POINTER(ctypes.c_void_p)), ("edges", ctypes.POINTER(Edge)),
+                ("preds", ctypes.POINTER(Pred))]
+
+
+class SieveOpts(ctypes.Structure):
+    _fields_ = [("passes", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("filter", FilterParams)]
+
+
+class StepStat(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("rel", ctypes.c_int32),
+                ("rows_in", ctypes.c_int64), ("rows_out", ctypes.c_int64)]
+
+
+class SieveStats(ctypes.Structure):
+    _fields_ = [("nsteps", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("step", StepStat * MAX_STEPS), ("rows_final", ctypes.c_int64 * MAX_REL),
+                ("filter_bytes", ctypes.c_uint64)]
+
+
+class ColRef(ctypes.Structure):
+    _fields_ = [("rel", ctypes.c_int32), ("col", ctypes.c_int32), ("wide", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_uint64), ("sum", ctypes.c_uint64),
+                ("intermediate", ctypes.c_uint64), ("rows", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load ``libsievejoin.so``; raise if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with "
+                           "`python -m paper_2308_16370_b300.build` (no CPU fallback exists)")
+    lib = ctypes.CDLL(path)
+    P, I, I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+    PP = ctypes.POINTER(ctypes.c_void_p)
+    sig = {
+        "sj_create": [PP, I, P, P, P, P],
+        "sj_destroy": [P], "sj_sync": [P],
+        "sj_load_relation": [P, I, PP, I64, I, PP],
+        "sj_rel_info": [P, ctypes.POINTER(I64), ctypes.POINTER(I), PP],
+        "sj_free_rel": [P, P],
+        "sj_build_filter": [P, P, I, ctypes.POINTER(Pred), ctypes.POINTER(FilterParams), PP],
+        "sj_filter_info": [P, P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64), PP],
+        "sj_filter_probe": [P, P, P, I64, P],
+        "sj_free_filter": [P, P],
+        "sj_sieve": [P, P, I, ctypes.POINTER(ctypes.c_int), PP, ctypes.POINTER(Pred), PP,
+                     ctypes.POINTER(I64)],
+        "sj_sieve_path": [P, ctypes.POINTER(Path), ctypes.POINTER(SieveOpts), PP,
+                          ctypes.POINTER(SieveStats)],
+        "sj_join": [P, ctypes.POINTER(Path), PP, I, I, ctypes.POINTER(ColRef), ctypes.POINTER(Result)],
+        "sj_prof_enable": [P, I], "sj_prof_reset": [P],
+        "sj_prof_read": [P, I, ctypes.POINTER(I64), ctypes.POINTER(ctypes.c_double),
+                         ctypes.POINTER(ctypes.c_double)],
+        "sj_counters": [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64)],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    lib.sj_last_error.argtypes = [P]
+    lib.sj_last_error.restype = ctypes.c_char_p
+    lib.sj_status_str.argtypes = [ctypes.c_int]
+    lib.sj_status_str.restype = ctypes.c_char_p
+    lib.sj_version.argtypes = []
+    lib.sj_version.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+class _CudaArray:
+    """Zero-copy ``__cuda_array_interface__`` view of library-owned memory."""
+
+    def __init__(self, ptr: int, n: int, typestr: str = "<i4"):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr,
+                                         "data": (ptr, False), "version": 3, "strides": None}
+
+
+def _torch():
+    import torch
+    return torch
+
+
+# ----------------------------------------------------------------------------- handles
+class Relation:
+    """A columnar int32 relation on the device (library handle)."""
+
+    def __init__(self, ctx: "Context", handle: int, keep=None):
+        self.ctx = ctx
+        self.handle = ctypes.c_void_p(handle)
+        self._keep = keep  # borrowed tensors must outlive the handle
+        n = ctypes.c_int64()
+        nc = ctypes.c_int()
+        ptrs = (ctypes.c_void_p * MAX_COLS)()
+        ctx._check(ctx.lib.sj_rel_info(self.handle, ctypes.byref(n), ctypes.byref(nc), ptrs))
+        self.nrows = int(n.value)
+        self.ncols = int(nc.value)
+        self.col_ptrs = [int(ptrs[j] or 0) for j in range(self.ncols)]
+
+    def column(self, j: int):
+        """Zero-copy torch view of column j (valid while this handle lives)."""
+        torch = _torch()
+        if self.nrows == 0:
+            return torch.empty(0, dtype=torch.int32, device=f"cuda:{self.ctx.device}")
+        return torch.as_tensor(_CudaArray(self.col_ptrs[j], self.nrows),
+                               device=f"cuda:{self.ctx.device}")
+
+    def to_numpy(self):
+        self.ctx.sync()
+        return [self.column(j).cpu().numpy().copy() for j in range(self.ncols)]
+
+    def free(self):
+        if self.handle and self.ctx.ctx:
+            self.ctx.lib.sj_free_rel(self.ctx.ctx, self.handle)
+        self.handle = None
+        self._keep = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Filter:
+    def __init__(self, ctx: "Context", handle: int, params: FilterParams):
+        self.ctx = ctx
+        self.handle = ctypes.c_void_p(handle)
+        self.params = params
+
+    def info(self):
+        nb = ctypes.c_uint64()
+        ni = ctypes.c_uint64()
+        w = ctypes.c_void_p()
+        self.ctx._check(self.ctx.lib.sj_filter_info(self.ctx.ctx, self.handle, ctypes.byref(nb),
+                                                    ctypes.byref(ni), ctypes.byref(w)))
+        return int(nb.value), int(ni.value), int(w.value)
+
+    def words(self) -> np.ndarray:
+        """Copy of the filter words (nblocks * 8 uint32)."""
+        nb, _, ptr = self.info()
+        t = _torch().as_tensor(_CudaArray(ptr, nb * 8, "<i4"), device=f"cuda:{self.ctx.device}")
+        return t.cpu().numpy().view(np.uint32).copy()
+
+    def free(self):
+        if self.handle and self.ctx.ctx:
+            self.ctx.lib.sj_free_filter(self.ctx.ctx, self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def _params(bits_per_key=8, k=3, layout=BLOCKED256, seed=0) -> FilterParams:
+    return FilterParams(int(bits_per_key), int(k), int(layout), 0, int(seed) & ((1 << 64) - 1))
+
+
+def _pred(p):
+    if p is None:
+        return None
+    c, lo, hi = p
+    return Pred(int(c), int(lo), int(hi))
+
+
+class Context:
+    """One device + one stream.  ``stream`` is a torch.cuda.Stream (default:
+    the current stream).  With ``torch_allocator`` the library allocates
+    through PyTorch's caching allocator, else through cudaMallocAsync."""
+
+    def __init__(self, device: int = 0, stream=None, torch_allocator: bool = False):
+        torch = _torch()
+        if not torch.cuda.is_available():
+            raise RuntimeError("sievejoin needs a CUDA GPU; none is visible")
+        self.lib = load_library()
+        self.device = int(device)
+        torch.cuda.set_device(self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._cbs = None
+        alloc = free = None
+        if torch_allocator:
+            dev, st = self.device, self.stream
+
+            @ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+            def _alloc(nbytes, user):
+                try:
+                    return torch.cuda.caching_allocator_alloc(int(nbytes), dev, st)
+                except Exception:
+                    return None
+
+            @ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+            def _free(ptr, nbytes, user):
+                torch.cuda.caching_allocator_delete(ptr)
+
+            self._cbs = (_alloc, _free)
+            alloc = ctypes.cast(_alloc, ctypes.c_void_p)
+            free = ctypes.cast(_free, ctypes.c_void_p)
+        h = ctypes.c_void_p()
+        st = self.lib.sj_create(ctypes.byref(h), self.device, ctypes.c_void_p(self.stream.cuda_stream),
+                                alloc, free, None)
+        if st != 0:
+            raise SieveJoinError(st, "sj_create failed")
+        self.ctx = h
+
+    # --------------------------------------------------------------- plumbing
+    def _check(self, st: int):
+        if st != 0:
+            msg = self.lib.sj_last_error(self.ctx).decode() if self.ctx else ""
+            raise SieveJoinError(st, msg)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.sj_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def sync(self):
+        self._check(self.lib.sj_sync(self.ctx))
+
+    # --------------------------------------------------------------- relations
+    def load_relation(self, cols, where: str = "borrow") -> Relation:
+        """``cols``: torch int32 CUDA tensors (``borrow``/``copy``) or numpy /
+        CPU tensors (``host``; copied on the context stream)."""
+        torch = _torch()
+        mode = {"borrow": DEVICE_BORROW, "copy": DEVICE_COPY, "host": HOST_COPY}[where]
+        keep = []
+        ptrs = (ctypes.c_void_p * len(cols))()
+        n = None
+        for j, c in enumerate(cols):
+            if mode == HOST_COPY:
+                if isinstance(c, np.ndarray):
+                    c = np.ascontiguousarray(c, dtype=np.int32)
+                    ptrs[j] = c.ctypes.data
+                else:
+                    c = c.contiguous()
+                    assert c.dtype == torch.int32 and not c.is_cuda
+                    ptrs[j] = c.data_ptr()
+            else:
+                assert c.dtype == torch.int32 and c.is_cuda and c.is_contiguous()
+                ptrs[j] = c.data_ptr()
+            keep.append(c)
+            n = len(c) if n is None else n
+            if len(c) != n:
+                raise ValueError("columns differ in length")
+        h = ctypes.c_void_p()
+        self._check(self.lib.sj_load_relation(self.ctx, len(cols), ptrs, int(n or 0), mode,
+                                              ctypes.byref(h)))
+        if mode == HOST_COPY:
+            self.sync()  # host buffers may be released after this
+            keep = None
+        elif mode == DEVICE_COPY:
+            keep = None
+        return Relation(self, h.value, keep)
+
+    # --------------------------------------------------------------- filters
+    def build_filter(self, rel: Relation, key_col: int, pred=None, bits_per_key=8, k=3,
+                     layout=BLOCKED256, seed=0) -> Filter:
+        p = _params(bits_per_key, k, layout, seed)
+        pr = _pred(pred)
+        h = ctypes.c_void_p()
+        self._check(self.lib.sj_build_filter(self.ctx, rel.handle, int(key_col),
+                                             ctypes.byref(pr) if pr else None, ctypes.byref(p),
+                                             ctypes.byref(h)))
+        return Filter(self, h.value, p)
+
+    def filter_probe(self, f: Filter, keys):
+        torch = _torch()
+        out = torch.empty(len(keys), dtype=torch.uint8, device=keys.device)
+        self._check(self.lib.sj_filter_probe(self.ctx, f.handle, ctypes.c_void_p(keys.data_ptr()),
+                                             len(keys), ctypes.c_void_p(out.data_ptr())))
+        return out
+
+    def sieve(self, rel: Relation, key_cols=(), filters=(), pred=None) -> Relation:
+        kc = (ctypes.c_int * max(1, len(key_cols)))(*key_cols)
+        fs = (ctypes.c_void_p * max(1, len(filters)))(*[f.handle.value for f in filters])
+        pr = _pred(pred)
+        h = ctypes.c_void_p()
+        n = ctypes.c_int64()
+        self._check(self.lib.sj_sieve(self.ctx, rel.handle, len(key_cols), kc, fs,
+                                      ctypes.byref(pr) if pr else None, ctypes.byref(h),
+                                      ctypes.byref(n)))
+        return Relation(self, h.value)
+
+    # --------------------------------------------------------------- paths
+    def _path(self, rels, edges, preds, root):
+        n = len(rels)
+        hs = (ctypes.c_void_p * n)(*[r.handle.value for r in rels])
+        es = (Edge * max(1, len(edges)))(*[Edge(*map(int, e)) for e in edges])
+        ps = None
+        if preds is not None and any(p is not None for p in preds):
+            ps = (Pred * n)(*[_pred(p) if p is not None else Pred(-1, 0, 0) for p in preds])
+        path = Path(n, int(root), ctypes.cast(hs, ctypes.POINTER(ctypes.c_void_p)),
+                    ctypes.cast(es, ctypes.POINTER(Edge)),
+                    ctypes.cast(ps, ctypes.POINTER(Pred)) if ps is not None else None)
+        return path, (hs, es, ps)
+
+    def sieve_path(self, rels, edges, preds=None, root=-1, passes=FWD_BWD, bits_per_key=8, k=3,
+                   layout=BLOCKED256, seed=0):
+        """Pruning phase over a join tree.  Returns (sieved relations, stats)."""
+        path, keep = self._path(rels, edges, preds, root)
+        opts = SieveOpts(int(passes), 0, _params(bits_per_key, k, layout, seed))
+        outs = (ctypes.c_void_p * len(rels))()
+        stats = SieveStats()
+        self._check(self.lib.sj_sieve_path(self.ctx, ctypes.byref(path), ctypes.byref(opts), outs,
+                                           ctypes.byref(stats)))
+        sieved = [Relation(self, outs[i]) for i in range(len(rels))]
+        steps = [(("select", "fwd", "bwd")[stats.step[s].kind], stats.step[s].rel,
+                  stats.step[s].rows_in, stats.step[s].rows_out) for s in range(stats.nsteps)]
+        return sieved, {"steps": steps, "rows_final": [stats.rows_final[i] for i in range(len(rels))],
+                        "filter_bytes": int(stats.filter_bytes)}
+
+    def join(self, rels, edges, preds=None, root=-1, inputs=None, mode=COUNT_SUM, refs=()):
+        """Left-deep hash join.  ``refs`` = [(rel, col, wide), ...]: SUM terms
+        (COUNT_SUM) or projected columns (MATERIALIZE)."""
+        path, keep = self._path(rels, edges, preds, root)
+        ins = None
+        if inputs is not None:
+            ins = (ctypes.c_void_p * len(inputs))(*[r.handle.value for r in inputs])
+        rs = (ColRef * max(1, len(refs)))(*[ColRef(int(r[0]), int(r[1]), int(r[2]) if len(r) > 2 else 0, 0)
+                                            for r in refs])
+        res = Result()
+        self._check(self.lib.sj_join(self.ctx, ctypes.byref(path), ins, int(mode), len(refs), rs,
+                                     ctypes.byref(res)))
+        out = {"count": int(res.count), "sum": int(res.sum), "intermediate": int(res.intermediate),
+               "rows": None}
+        if res.rows:
+            out["rows"] = Relation(self, res.rows)
+        return out
+
+    # --------------------------------------------------------------- profiling
+    def prof_enable(self, on: bool = True):
+        self._check(self.lib.sj_prof_enable(self.ctx, 1 if on else 0))
+
+    def prof_reset(self):
+        self._check(self.lib.sj_prof_reset(self.ctx))
+
+    def prof_read(self, kind: str):
+        n = ctypes.c_int64()
+        ms = ctypes.c_double()
+        b = ctypes.c_double()
+        self._check(self.lib.sj_prof_read(self.ctx, KERNEL_KINDS[kind], ctypes.byref(n),
+                                          ctypes.byref(ms), ctypes.byref(b)))
+        return {"launches": int(n.value), "ms": float(ms.value), "bytes": float(b.value)}
+
+    def counters(self):
+        """Kernel launches, host-to-device and device-to-host bytes since the
+        last prof_reset."""
+        n, h2d, d2h = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        self._check(self.lib.sj_counters(self.ctx, ctypes.byref(n), ctypes.byref(h2d),
+                                         ctypes.byref(d2h)))
+        return {"launches": int(n.value), "h2d_bytes": int(h2d.value), "d2h_bytes": int(d2h.value)}
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def workload_path(ctx: Context, w: dict, where: str = "host"):
+    """Load a workload dict (see ``inputs``) into device relations."""
+    return [ctx.load_relation(r, where=where) for r in w["rels"]]

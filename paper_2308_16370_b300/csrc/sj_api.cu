@@ -1,0 +1,1344 @@
+// Host side of the C ABI declared in include/sievejoin.h: contexts, relation
+// and filter handles, the pruning-phase driver (Sec. 2.2, sj_sieve_path) and
+// the left-deep hash-join driver (Sec. 2.2 enumeration phase, sj_join).
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "sievejoin.h"
+#include "sj_kernels.cuh"
+
+using namespace sj;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t round_up(size_t x, size_t a = kAlign) { return (x + a - 1) / a * a; }
+
+// d_misc layout (uint64 words)
+constexpr int kMiscStatus = 0;   // uint32 status bits in the low half
+constexpr int kMiscResult = 1;   // [1..3] count lo, count hi, sum
+constexpr int kMiscTotals = 4;   // [4..5] matching probe rows, output tuples
+constexpr int kMiscNuniq = 6;    // uint32 distinct-key counter in the low half
+constexpr int kMiscSteps = 8;    // [8 .. 8 + kMaxSlots) per-step row counts
+constexpr int kMaxSlots = 120;
+constexpr int kMiscWords = kMiscSteps + kMaxSlots;
+
+struct ProfRec {
+  int kind;
+  cudaEvent_t e0, e1;
+  double bytes;       // fixed part
+  int slot_a, slot_b; // deferred parts: per_a * count[slot_a] + per_b * count[slot_b]
+  double per_a, per_b;
+};
+
+}  // namespace
+
+struct sj_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  sj_alloc_fn alloc = nullptr;
+  sj_free_fn free_ = nullptr;
+  void* user = nullptr;
+  int num_sms = 148;
+  std::string err;
+  uint64_t* d_misc = nullptr;
+  uint64_t* h_misc = nullptr;  // pinned
+  uint8_t* scratch = nullptr;
+  size_t scratch_bytes = 0;
+  int64_t launches = 0;
+  int64_t h2d_bytes = 0;
+  int64_t d2h_bytes = 0;
+  bool prof_on = false;
+  std::vector<ProfRec> prof;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  double prof_ms[SJ_K_COUNT] = {};
+  double prof_bytes[SJ_K_COUNT] = {};
+  int64_t prof_n[SJ_K_COUNT] = {};
+};
+
+struct sj_rel_s {
+  int ncols = 0;
+  int64_t nrows = 0;   // host row count (-1 while only the device knows it)
+  int64_t cap = 0;     // allocated rows
+  int32_t* cols[SJ_MAX_COLS] = {};
+  uint64_t* d_n = nullptr;  // device row count (compacted relations), else null
+  void* mem = nullptr;
+  size_t mem_bytes = 0;
+};
+
+struct sj_filter_s {
+  sj_filter_params p{};
+  uint64_t* hdr = nullptr;   // device: nblocks, rows inserted
+  uint32_t* words = nullptr;
+  uint64_t nblocks_cap = 0;
+  void* mem = nullptr;
+  size_t mem_bytes = 0;
+};
+
+namespace {
+
+sj_status fail(sj_ctx* c, sj_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+#define SJ_CUDA(c, call)                                                              \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess)                                                            \
+      return fail((c), SJ_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+#define SJ_TRY(expr)              \
+  do {                            \
+    sj_status s_ = (expr);        \
+    if (s_ != SJ_OK) return s_;   \
+  } while (0)
+
+void* dalloc(sj_ctx* c, size_t bytes) {
+  bytes = round_up(bytes ? bytes : 1);
+  void* p = nullptr;
+  if (c->alloc) {
+    p = c->alloc(bytes, c->user);
+  } else if (cudaMallocAsync(&p, bytes, c->stream) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  return p;
+}
+
+void dfree(sj_ctx* c, void* p, size_t bytes) {
+  if (!p) return;
+  bytes = round_up(bytes ? bytes : 1);
+  if (c->free_) c->free_(p, bytes, c->user);
+  else cudaFreeAsync(p, c->stream);
+}
+
+// Temporaries of one call, released (stream-ordered) when the call returns.
+struct Temps {
+  sj_ctx* c;
+  std::vector<std::pair<void*, size_t>> v;
+  explicit Temps(sj_ctx* cc) : c(cc) {}
+  ~Temps() {
+    for (auto& x : v) dfree(c, x.first, x.second);
+  }
+  template <class T>
+  T* get(size_t n_elems, sj_status* st) {
+    const size_t bytes = n_elems * sizeof(T);
+    void* p = dalloc(c, bytes);
+    if (!p) {
+      *st = SJ_ENOMEM;
+      return nullptr;
+    }
+    v.emplace_back(p, bytes);
+    return static_cast<T*>(p);
+  }
+};
+
+cudaEvent_t take_event(sj_ctx* c) {
+  if (c->ev_used == c->ev_pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    c->ev_pool.push_back(e);
+  }
+  return c->ev_pool[c->ev_used++];
+}
+
+// Bracket a kernel launch with profiling events when enabled.
+struct Launch {
+  sj_ctx* c;
+  ProfRec rec{};
+  bool on;
+  Launch(sj_ctx* cc, int kind, double bytes, int slot_a = -1, double per_a = 0, int slot_b = -1,
+         double per_b = 0)
+      : c(cc), on(cc->prof_on) {
+    c->launches++;
+    if (!on) return;
+    rec.kind = kind;
+    rec.bytes = bytes;
+    rec.slot_a = slot_a;
+    rec.per_a = per_a;
+    rec.slot_b = slot_b;
+    rec.per_b = per_b;
+    rec.e0 = take_event(c);
+    rec.e1 = take_event(c);
+    if (rec.e0) cudaEventRecord(rec.e0, c->stream);
+  }
+  ~Launch() {
+    if (!on || !rec.e0 || !rec.e1) return;
+    cudaEventRecord(rec.e1, c->stream);
+    c->prof.push_back(rec);
+  }
+};
+
+sj_status check_launch(sj_ctx* c, const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(c, SJ_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  return SJ_OK;
+}
+
+// Synchronise, read the misc block back and turn device status bits into errors.
+sj_status sync_read(sj_ctx* c) {
+  SJ_CUDA(c, cudaMemcpyAsync(c->h_misc, c->d_misc, kMiscWords * sizeof(uint64_t),
+                             cudaMemcpyDeviceToHost, c->stream));
+  c->d2h_bytes += kMiscWords * sizeof(uint64_t);
+  SJ_CUDA(c, cudaStreamSynchronize(c->stream));
+  const uint32_t st = (uint32_t)(c->h_misc[kMiscStatus] & 0xffffffffu);
+  if (st) {
+    SJ_CUDA(c, cudaMemsetAsync(c->d_misc + kMiscStatus, 0, sizeof(uint64_t), c->stream));
+    if (st & kErrTimeout) return fail(c, SJ_ETIMEOUT, "a bounded device wait timed out");
+    if (st & kErrTableFull) return fail(c, SJ_ETABLEFULL, "hash table probe chain exhausted");
+    return fail(c, SJ_ECUDA, "device status word set");
+  }
+  return SJ_OK;
+}
+
+uint32_t* status_ptr(sj_ctx* c) { return reinterpret_cast<uint32_t*>(c->d_misc + kMiscStatus); }
+
+// Scratch for one look-back scan: tile counter, flags, aggregates, prefixes.
+template <int NCH>
+sj_status scratch_for(sj_ctx* c, int64_t ntiles, uint32_t** counter, LookBack<NCH>* lb) {
+  if (ntiles < 1) ntiles = 1;
+  const size_t flags_bytes = round_up((size_t)ntiles * 4);
+  const size_t need = kAlign + flags_bytes + 2 * (size_t)ntiles * NCH * 8;
+  if (need > c->scratch_bytes) {
+    // the old scratch may still be used by enqueued work: stream-ordered free
+    dfree(c, c->scratch, c->scratch_bytes);
+    const size_t nb = round_up(std::max(need, c->scratch_bytes * 2));
+    c->scratch = static_cast<uint8_t*>(dalloc(c, nb));
+    c->scratch_bytes = c->scratch ? nb : 0;
+    if (!c->scratch) return fail(c, SJ_ENOMEM, "scratch allocation failed");
+  }
+  SJ_CUDA(c, cudaMemsetAsync(c->scratch, 0, kAlign + flags_bytes, c->stream));
+  *counter = reinterpret_cast<uint32_t*>(c->scratch);
+  lb->flags = reinterpret_cast<uint32_t*>(c->scratch + kAlign);
+  lb->agg = reinterpret_cast<uint64_t*>(c->scratch + kAlign + flags_bytes);
+  lb->inc = lb->agg + (size_t)ntiles * NCH;
+  lb->status = status_ptr(c);
+  return SJ_OK;
+}
+
+// --------------------------------------------------------------- relations
+sj_rel new_rel(sj_ctx* c, int ncols, int64_t cap) {
+  sj_rel r = new sj_rel_s();
+  const size_t colb = round_up((size_t)std::max<int64_t>(cap, 1) * 4);
+  r->mem_bytes = kAlign + colb * (size_t)ncols;
+  r->mem = dalloc(c, r->mem_bytes);
+  if (!r->mem) {
+    delete r;
+    return nullptr;
+  }
+  r->ncols = ncols;
+  r->cap = cap;
+  r->nrows = -1;
+  r->d_n = static_cast<uint64_t*>(r->mem);
+  uint8_t* p = static_cast<uint8_t*>(r->mem) + kAlign;
+  for (int j = 0; j < ncols; ++j) r->cols[j] = reinterpret_cast<int32_t*>(p + colb * j);
+  return r;
+}
+
+void free_rel(sj_ctx* c, sj_rel r) {
+  if (!r) return;
+  dfree(c, r->mem, r->mem_bytes);
+  delete r;
+}
+
+sj_rel view_of(const sj_rel_s* src) {
+  sj_rel r = new sj_rel_s(*src);
+  r->mem = nullptr;
+  r->mem_bytes = 0;
+  return r;
+}
+
+int64_t rel_cap(const sj_rel_s* r) { return r->d_n ? r->cap : r->nrows; }
+
+struct TestSpec {
+  int col;
+  bool is_pred;
+  int32_t lo, hi;
+  sj_filter f;
+};
+
+FilterView view(const sj_filter_s* f) {
+  FilterView v;
+  v.words = f->words;
+  v.hdr = f->hdr;
+  v.k = f->p.k;
+  v.layout = f->p.layout;
+  v.seed = f->p.seed;
+  return v;
+}
+
+// One sieve step without synchronising: kept rows of `in` into a new relation.
+// `slot` >= 0 also stores the kept-row count in the per-step statistics;
+// `slot_in` is the statistics slot of `in`'s own count (deferred profiling bytes).
+sj_status sieve_step_timed(sj_ctx* c, const sj_rel_s* in, const std::vector<TestSpec>& tests,
+                           int slot, int slot_in, sj_rel* out) {
+  const int64_t cap = rel_cap(in);
+  sj_rel r = new_rel(c, in->ncols, cap);
+  if (!r) return fail(c, SJ_ENOMEM, "sieve output allocation failed");
+  SieveArgs a;
+  memset(&a, 0, sizeof(a));
+  a.ntest = (int)tests.size();
+  for (size_t t = 0; t < tests.size(); ++t) {
+    a.test[t].col = in->cols[tests[t].col];
+    a.test[t].is_pred = tests[t].is_pred ? 1 : 0;
+    a.test[t].lo = tests[t].lo;
+    a.test[t].hi = tests[t].hi;
+    if (!tests[t].is_pred) a.test[t].f = view(tests[t].f);
+  }
+  a.nout = in->ncols;
+  for (int j = 0; j < in->ncols; ++j) {
+    a.in[j] = in->cols[j];
+    a.out[j] = r->cols[j];
+    a.out_is_vec[j] = (!tests.empty() && tests[0].col == j) ? 1 : 0;
+  }
+  a.n_host = in->d_n ? 0 : in->nrows;
+  a.n_dev = in->d_n;
+  a.out_n = r->d_n;
+  a.out_n2 = slot >= 0 ? c->d_misc + kMiscSteps + slot : nullptr;
+  const int64_t ntiles = (cap + kSieveTile - 1) / kSieveTile;
+  sj_status st = scratch_for<1>(c, ntiles, &a.tile_counter, &a.lb);
+  if (st != SJ_OK) {
+    free_rel(c, r);
+    return st;
+  }
+  // algorithmic bytes: the first tested column of every input row; each kept
+  // row's other columns read and all of its columns written
+  const int nvec = tests.empty() ? 0 : 1;
+  const double per_in = 4.0 * nvec;
+  const double per_out = 4.0 * (in->ncols - nvec) + 4.0 * in->ncols;
+  {
+    Launch L = in->d_n ? Launch(c, SJ_K_SIEVE, 0, slot_in, per_in, slot, per_out)
+                       : Launch(c, SJ_K_SIEVE, per_in * (double)in->nrows, slot, per_out);
+    launch_sieve(a, cap, c->stream);
+  }
+  st = check_launch(c, "k_sieve");
+  if (st != SJ_OK) {
+    free_rel(c, r);
+    return st;
+  }
+  *out = r;
+  return SJ_OK;
+}
+
+sj_filter_params norm_params(const sj_filter_params* p) {
+  sj_filter_params q{};
+  if (p) q = *p;
+  if (q.bits_per_key == 0) q.bits_per_key = 8;
+  if (q.k == 0) q.k = 3;
+  return q;
+}
+
+sj_status check_params(sj_ctx* c, const sj_filter_params& p) {
+  if (p.layout > SJ_CLASSIC) return fail(c, SJ_EINVAL, "unknown filter layout");
+  if (p.layout == SJ_BLOCKED256 && p.k > 4) return fail(c, SJ_EINVAL, "blocked filter needs k <= 4");
+  if (p.layout == SJ_CLASSIC && p.k > 8) return fail(c, SJ_EINVAL, "classic filter needs k <= 8");
+  if (p.bits_per_key > 1024) return fail(c, SJ_EINVAL, "bits_per_key must be <= 1024");
+  return SJ_OK;
+}
+
+// Build a filter over column `col` of `rel` without synchronising.
+sj_status build_filter_nosync(sj_ctx* c, const sj_rel_s* rel, int col, const sj_filter_params& p,
+                              int slot_in, sj_filter* out) {
+  const int64_t cap = rel_cap(rel);
+  sj_filter f = new sj_filter_s();
+  f->p = p;
+  uint64_t nbc = ((uint64_t)p.bits_per_key * (uint64_t)cap + 255) / 256;
+  if (nbc < 1) nbc = 1;
+  f->nblocks_cap = nbc;
+  f->mem_bytes = kAlign + nbc * 32;
+  f->mem = dalloc(c, f->mem_bytes);
+  if (!f->mem) {
+    delete f;
+    return fail(c, SJ_ENOMEM, "filter allocation failed");
+  }
+  f->hdr = static_cast<uint64_t*>(f->mem);
+  f->words = reinterpret_cast<uint32_t*>(static_cast<uint8_t*>(f->mem) + kAlign);
+  cudaError_t e = cudaMemsetAsync(f->words, 0, nbc * 32, c->stream);
+  if (e != cudaSuccess) {
+    dfree(c, f->mem, f->mem_bytes);
+    delete f;
+    return fail(c, SJ_ECUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
+  }
+  BloomBuildArgs a;
+  a.keys = rel->cols[col];
+  a.n_host = rel->d_n ? 0 : rel->nrows;
+  a.n_dev = rel->d_n;
+  a.hdr = f->hdr;
+  a.words = f->words;
+  a.nblocks_cap = nbc;
+  a.bits_per_key = p.bits_per_key;
+  a.k = p.k;
+  a.layout = p.layout;
+  a.seed = p.seed;
+  // algorithmic bytes: 4 per key read plus the filter's bits written once
+  const double per_key = 4.0 + p.bits_per_key / 8.0;
+  {
+    Launch L = rel->d_n ? Launch(c, SJ_K_BLOOM_BUILD, 0, slot_in, per_key)
+                        : Launch(c, SJ_K_BLOOM_BUILD, per_key * (double)rel->nrows);
+    launch_bloom_build(a, cap, c->num_sms, c->stream);
+  }
+  sj_status st = check_launch(c, "k_bloom_build");
+  if (st != SJ_OK) {
+    dfree(c, f->mem, f->mem_bytes);
+    delete f;
+    return st;
+  }
+  *out = f;
+  return SJ_OK;
+}
+
+void free_filter(sj_ctx* c, sj_filter f) {
+  if (!f) return;
+  dfree(c, f->mem, f->mem_bytes);
+  delete f;
+}
+
+// Resolve deferred algorithmic bytes of profiled launches from step counts.
+void prof_resolve(sj_ctx* c, size_t from) {
+  for (size_t i = from; i < c->prof.size(); ++i) {
+    ProfRec& r = c->prof[i];
+    if (r.slot_a >= 0) {
+      r.bytes += r.per_a * (double)c->h_misc[kMiscSteps + r.slot_a];
+      r.slot_a = -1;
+    }
+    if (r.slot_b >= 0) {
+      r.bytes += r.per_b * (double)c->h_misc[kMiscSteps + r.slot_b];
+      r.slot_b = -1;
+    }
+  }
+}
+
+// --------------------------------------------------------------- join tree
+struct Tree {
+  std::vector<int> parent, pedge, post, pre;
+  std::vector<std::vector<int>> children;
+};
+
+int edge_col(const sj_edge& e, int rel) { return e.rel_a == rel ? e.col_a : e.col_b; }
+
+sj_status validate_path(sj_ctx* c, const sj_path* p, const sj_rel* rels, Tree* tr) {
+  if (!p || p->nrel < 1 || p->nrel > SJ_MAX_REL) return fail(c, SJ_EINVAL, "nrel out of range");
+  const int n = p->nrel;
+  if (!rels) return fail(c, SJ_EINVAL, "null relations");
+  for (int i = 0; i < n; ++i)
+    if (!rels[i]) return fail(c, SJ_EINVAL, "null relation handle");
+  if (n > 1 && !p->edges) return fail(c, SJ_EINVAL, "null edges");
+  std::vector<std::vector<std::pair<int, int>>> adj(n);
+  for (int e = 0; e < n - 1; ++e) {
+    const sj_edge& E = p->edges[e];
+    if (E.rel_a < 0 || E.rel_a >= n || E.rel_b < 0 || E.rel_b >= n || E.rel_a == E.rel_b)
+      return fail(c, SJ_EINVAL, "edge relation out of range");
+    if (E.col_a < 0 || E.col_a >= rels[E.rel_a]->ncols || E.col_b < 0 ||
+        E.col_b >= rels[E.rel_b]->ncols)
+      return fail(c, SJ_EINVAL, "edge column out of range");
+    adj[E.rel_a].push_back({E.rel_b, e});
+    adj[E.rel_b].push_back({E.rel_a, e});
+  }
+  if (p->preds)
+    for (int i = 0; i < n; ++i)
+      if (p->preds[i].col >= rels[i]->ncols) return fail(c, SJ_EINVAL, "predicate column out of range");
+  const int root = p->root < 0 ? n - 1 : p->root;
+  if (root >= n) return fail(c, SJ_EINVAL, "root out of range");
+  tr->parent.assign(n, -1);
+  tr->pedge.assign(n, -1);
+  tr->children.assign(n, {});
+  std::vector<int> seen(n, 0), bfs{root};
+  seen[root] = 1;
+  for (size_t q = 0; q < bfs.size(); ++q) {
+    const int v = bfs[q];
+    for (auto& ue : adj[v]) {
+      if (seen[ue.first]) continue;
+      seen[ue.first] = 1;
+      tr->parent[ue.first] = v;
+      tr->pedge[ue.first] = ue.second;
+      tr->children[v].push_back(ue.first);
+      bfs.push_back(ue.first);
+    }
+  }
+  if ((int)bfs.size() != n) return fail(c, SJ_EINVAL, "join graph is not a connected tree");
+  // depth-first orders
+  std::vector<std::pair<int, size_t>> st{{root, 0}};
+  tr->pre.push_back(root);
+  while (!st.empty()) {
+    auto& top = st.back();
+    if (top.second < tr->children[top.first].size()) {
+      const int ch = tr->children[top.first][top.second++];
+      tr->pre.push_back(ch);
+      st.push_back({ch, 0});
+    } else {
+      tr->post.push_back(top.first);
+      st.pop_back();
+    }
+  }
+  return SJ_OK;
+}
+
+bool has_pred(const sj_path* p, int i) { return p->preds && p->preds[i].col >= 0; }
+
+}  // namespace
+
+// ======================================================================== C ABI
+extern "C" {
+
+const char* sj_version(void) { return "0.1.0"; }
+
+const char* sj_status_str(sj_status s) {
+  switch (s) {
+    case SJ_OK: return "ok";
+    case SJ_EINVAL: return "invalid argument";
+    case SJ_ENOMEM: return "out of device memory";
+    case SJ_ETABLEFULL: return "hash table full";
+    case SJ_ETIMEOUT: return "device wait timed out";
+    case SJ_EOVERFLOW: return "COUNT overflow";
+    case SJ_ECUDA: return "CUDA error";
+  }
+  return "unknown status";
+}
+
+const char* sj_last_error(const sj_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+sj_status sj_create(sj_ctx** out, int device, void* stream, sj_alloc_fn alloc, sj_free_fn free_,
+                    void* user) {
+  if (!out) return SJ_EINVAL;
+  if ((alloc == nullptr) != (free_ == nullptr)) return SJ_EINVAL;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return SJ_ECUDA;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) return SJ_ECUDA;
+  sj_ctx* c = new sj_ctx();
+  c->device = device;
+  c->stream = static_cast<cudaStream_t>(stream);
+  c->alloc = alloc;
+  c->free_ = free_;
+  c->user = user;
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (!alloc) {
+    // keep freed blocks in the device pool instead of returning them to the OS
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+      uint64_t thr = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+  }
+  c->d_misc = static_cast<uint64_t*>(dalloc(c, kMiscWords * sizeof(uint64_t)));
+  if (!c->d_misc || cudaMallocHost(&c->h_misc, kMiscWords * sizeof(uint64_t)) != cudaSuccess ||
+      cudaMemsetAsync(c->d_misc, 0, kMiscWords * sizeof(uint64_t), c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    cudaGetLastError();
+    if (c->d_misc) dfree(c, c->d_misc, kMiscWords * sizeof(uint64_t));
+    if (c->h_misc) cudaFreeHost(c->h_misc);
+    delete c;
+    return SJ_ENOMEM;
+  }
+  *out = c;
+  return SJ_OK;
+}
+
+sj_status sj_destroy(sj_ctx* c) {
+  if (!c) return SJ_EINVAL;
+  cudaStreamSynchronize(c->stream);
+  dfree(c, c->scratch, c->scratch_bytes);
+  dfree(c, c->d_misc, kMiscWords * sizeof(uint64_t));
+  cudaStreamSynchronize(c->stream);
+  cudaFreeHost(c->h_misc);
+  for (auto e : c->ev_pool) cudaEventDestroy(e);
+  delete c;
+  return SJ_OK;
+}
+
+sj_status sj_sync(sj_ctx* c) {
+  if (!c) return SJ_EINVAL;
+  return sync_read(c);
+}
+
+sj_status sj_load_relation(sj_ctx* c, int ncols, const int32_t* const* cols, int64_t nrows,
+                           int where, sj_rel* out) {
+  if (!c || !out || !cols) return fail(c, SJ_EINVAL, "null argument");
+  if (ncols < 1 || ncols > SJ_MAX_COLS) return fail(c, SJ_EINVAL, "ncols out of range");
+  if (nrows < 0 || nrows >= (int64_t(1) << 31)) return fail(c, SJ_EINVAL, "nrows out of range");
+  if (where < SJ_DEVICE_BORROW || where > SJ_HOST_COPY) return fail(c, SJ_EINVAL, "bad 'where'");
+  for (int j = 0; j < ncols; ++j) {
+    if (!cols[j] && nrows > 0) return fail(c, SJ_EINVAL, "null column pointer");
+    if (where != SJ_HOST_COPY && (reinterpret_cast<uintptr_t>(cols[j]) & 15))
+      return fail(c, SJ_EINVAL, "device columns must be 16-byte aligned");
+  }
+  if (where == SJ_DEVICE_BORROW) {
+    sj_rel r = new sj_rel_s();
+    r->ncols = ncols;
+    r->nrows = nrows;
+    r->cap = nrows;
+    for (int j = 0; j < ncols; ++j) r->cols[j] = const_cast<int32_t*>(cols[j]);
+    *out = r;
+    return SJ_OK;
+  }
+  sj_rel r = new_rel(c, ncols, nrows);
+  if (!r) return fail(c, SJ_ENOMEM, "relation allocation failed");
+  r->d_n = nullptr;  // host-known count
+  r->nrows = nrows;
+  const cudaMemcpyKind kind = where == SJ_HOST_COPY ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  for (int j = 0; j < ncols; ++j) {
+    if (nrows == 0) break;
+    cudaError_t e = cudaMemcpyAsync(r->cols[j], cols[j], (size_t)nrows * 4, kind, c->stream);
+    if (e != cudaSuccess) {
+      free_rel(c, r);
+      return fail(c, SJ_ECUDA, std::string("cudaMemcpyAsync: ") + cudaGetErrorString(e));
+    }
+    if (kind == cudaMemcpyHostToDevice) c->h2d_bytes += nrows * 4;
+  }
+  *out = r;
+  return SJ_OK;
+}
+
+sj_status sj_rel_info(sj_rel r, int64_t* nrows, int* ncols, const int32_t** cols) {
+  if (!r) return SJ_EINVAL;
+  if (nrows) *nrows = r->nrows;
+  if (ncols) *ncols = r->ncols;
+  if (cols)
+    for (int j = 0; j < SJ_MAX_COLS; ++j) cols[j] = j < r->ncols ? r->cols[j] : nullptr;
+  return SJ_OK;
+}
+
+sj_status sj_free_rel(sj_ctx* c, sj_rel r) {
+  if (!c || !r) return SJ_EINVAL;
+  free_rel(c, r);
+  return SJ_OK;
+}
+
+sj_status sj_build_filter(sj_ctx* c, sj_rel rel, int key_col, const sj_pred* pred,
+                          const sj_filter_params* params, sj_filter* out) {
+  if (!c || !rel || !out) return fail(c, SJ_EINVAL, "null argument");
+  if (rel->nrows < 0) return fail(c, SJ_EINVAL, "relation row count unknown");
+  if (key_col < 0 || key_col >= rel->ncols) return fail(c, SJ_EINVAL, "key column out of range");
+  const sj_filter_params p = norm_params(params);
+  SJ_TRY(check_params(c, p));
+  if (pred && pred->col >= 0) {
+    if (pred->col >= rel->ncols) return fail(c, SJ_EINVAL, "predicate column out of range");
+    // select the rows passing the predicate, then size the filter by them
+    std::vector<TestSpec> t{{pred->col, true, pred->lo, pred->hi, nullptr}};
+    sj_rel sel = nullptr;
+    SJ_TRY(sieve_step_timed(c, rel, t, 0, -1, &sel));
+    sj_status st = sync_read(c);
+    if (st == SJ_OK) {
+      sel->nrows = (int64_t)c->h_misc[kMiscSteps + 0];
+      sel->d_n = nullptr;
+      prof_resolve(c, 0);
+      st = build_filter_nosync(c, sel, key_col, p, -1, out);
+    }
+    free_rel(c, sel);
+    return st;
+  }
+  return build_filter_nosync(c, rel, key_col, p, -1, out);
+}
+
+sj_status sj_filter_info(sj_ctx* c, sj_filter f, uint64_t* nblocks, uint64_t* n_inserted,
+                         const uint32_t** words) {
+  if (!c || !f) return fail(c, SJ_EINVAL, "null argument");
+  uint64_t h[2];
+  SJ_CUDA(c, cudaMemcpyAsync(h, f->hdr, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  c->d2h_bytes += sizeof(h);
+  SJ_TRY(sync_read(c));
+  if (nblocks) *nblocks = h[0];
+  if (n_inserted) *n_inserted = h[1];
+  if (words) *words = f->words;
+  return SJ_OK;
+}
+
+sj_status sj_filter_probe(sj_ctx* c, sj_filter f, const int32_t* keys, int64_t n, uint8_t* out) {
+  if (!c || !f || (n > 0 && (!keys || !out)) || n < 0) return fail(c, SJ_EINVAL, "bad argument");
+  if (n == 0) return SJ_OK;
+  BloomProbeArgs a;
+  a.f = view(f);
+  a.keys = keys;
+  a.n = n;
+  a.out = out;
+  {
+    Launch L(c, SJ_K_OTHER, 5.0 * (double)n);
+    launch_bloom_probe(a, c->num_sms, c->stream);
+  }
+  return check_launch(c, "k_bloom_probe");
+}
+
+sj_status sj_free_filter(sj_ctx* c, sj_filter f) {
+  if (!c || !f) return SJ_EINVAL;
+  free_filter(c, f);
+  return SJ_OK;
+}
+
+sj_status sj_sieve(sj_ctx* c, sj_rel rel, int nprobe, const int* key_cols, const sj_filter* filters,
+                   const sj_pred* pred, sj_rel* out, int64_t* nrows_out) {
+  if (!c || !rel || !out) return fail(c, SJ_EINVAL, "null argument");
+  if (rel->nrows < 0) return fail(c, SJ_EINVAL, "relation row count unknown");
+  if (nprobe < 0 || nprobe > SJ_MAX_PROBES || (nprobe > 0 && (!key_cols || !filters)))
+    return fail(c, SJ_EINVAL, "bad probe list");
+  std::vector<TestSpec> t;
+  if (pred && pred->col >= 0) {
+    if (pred->col >= rel->ncols) return fail(c, SJ_EINVAL, "predicate column out of range");
+    t.push_back({pred->col, true, pred->lo, pred->hi, nullptr});
+  }
+  for (int j = 0; j < nprobe; ++j) {
+    if (key_cols[j] < 0 || key_cols[j] >= rel->ncols || !filters[j])
+      return fail(c, SJ_EINVAL, "bad probe column or filter");
+    t.push_back({key_cols[j], false, 0, 0, filters[j]});
+  }
+  sj_rel r = nullptr;
+  const size_t p0 = c->prof.size();
+  SJ_TRY(sieve_step_timed(c, rel, t, 0, -1, &r));
+  sj_status st = sync_read(c);
+  if (st != SJ_OK) {
+    free_rel(c, r);
+    return st;
+  }
+  prof_resolve(c, p0);
+  r->nrows = (int64_t)c->h_misc[kMiscSteps + 0];
+  if (nrows_out) *nrows_out = r->nrows;
+  *out = r;
+  return SJ_OK;
+}
+
+sj_status sj_sieve_path(sj_ctx* c, const sj_path* path, const sj_sieve_opts* opts, sj_rel* out_sieved,
+                        sj_sieve_stats* stats) {
+  if (!c || !path || !out_sieved) return fail(c, SJ_EINVAL, "null argument");
+  Tree tr;
+  SJ_TRY(validate_path(c, path, path->rels, &tr));
+  const int n = path->nrel;
+  for (int i = 0; i < n; ++i)
+    if (path->rels[i]->nrows < 0) return fail(c, SJ_EINVAL, "relation row count unknown");
+  sj_sieve_opts o{};
+  if (opts) o = *opts;
+  const sj_filter_params fp = norm_params(&o.filter);
+  SJ_TRY(check_params(c, fp));
+  if (o.passes < SJ_FWD_BWD || o.passes > SJ_NO_SIEVE) return fail(c, SJ_EINVAL, "bad passes");
+
+  const size_t p0 = c->prof.size();
+  std::vector<sj_rel> cur(n, nullptr);   // owned temporaries (null = the input itself)
+  std::vector<int> last_slot(n, -1);     // step slot holding the relation's current count
+  std::vector<sj_filter> filters;
+  struct StepRec { int kind, rel, slot_in, slot_out; int64_t rows_in_host; };
+  std::vector<StepRec> steps;
+  int slot = 0;
+  uint64_t filter_bytes = 0;
+
+  auto cleanup = [&]() {
+    for (auto f : filters) free_filter(c, f);
+    filters.clear();
+    for (int i = 0; i < n; ++i) {
+      free_rel(c, cur[i]);
+      cur[i] = nullptr;
+    }
+  };
+  auto rel_of = [&](int i) -> const sj_rel_s* { return cur[i] ? cur[i] : path->rels[i]; };
+  auto do_step = [&](int i, int kind, const std::vector<TestSpec>& t) -> sj_status {
+    if (slot >= kMaxSlots || (int)steps.size() >= SJ_MAX_STEPS)
+      return fail(c, SJ_EINVAL, "too many sieve steps");
+    sj_rel r = nullptr;
+    const sj_rel_s* in = rel_of(i);
+    SJ_TRY(sieve_step_timed(c, in, t, slot, last_slot[i], &r));
+    steps.push_back({kind, i, last_slot[i], slot, in->d_n ? -1 : in->nrows});
+    free_rel(c, cur[i]);
+    cur[i] = r;
+    last_slot[i] = slot++;
+    return SJ_OK;
+  };
+  auto do_build = [&](int i, int col, sj_filter* f) -> sj_status {
+    SJ_TRY(build_filter_nosync(c, rel_of(i), col, fp, last_slot[i], f));
+    filters.push_back(*f);
+    filter_bytes += (*f)->nblocks_cap * 32;
+    return SJ_OK;
+  };
+
+  sj_status st = SJ_OK;
+  for (int i = 0; i < n && st == SJ_OK; ++i)
+    if (has_pred(path, i))
+      st = do_step(i, 0, {{path->preds[i].col, true, path->preds[i].lo, path->preds[i].hi, nullptr}});
+  if (st == SJ_OK && o.passes != SJ_NO_SIEVE && n > 1) {
+    std::vector<sj_filter> up(n, nullptr), down(n, nullptr);
+    if (o.passes == SJ_FWD_BWD) {
+      for (int v : tr.post) {
+        if (st != SJ_OK) break;
+        if (!tr.children[v].empty()) {
+          std::vector<TestSpec> t;
+          for (int ch : tr.children[v])
+            t.push_back({edge_col(path->edges[tr.pedge[ch]], v), false, 0, 0, up[ch]});
+          if ((int)t.size() > SJ_MAX_PROBES) {
+            st = fail(c, SJ_EINVAL, "a relation has more than 4 children");
+            break;
+          }
+          st = do_step(v, 1, t);
+        }
+        if (st == SJ_OK && tr.parent[v] >= 0)
+          st = do_build(v, edge_col(path->edges[tr.pedge[v]], v), &up[v]);
+      }
+    }
+    for (int v : tr.pre) {
+      if (st != SJ_OK) break;
+      if (tr.parent[v] >= 0)
+        st = do_step(v, 2, {{edge_col(path->edges[tr.pedge[v]], v), false, 0, 0, down[v]}});
+      for (int ch : tr.children[v]) {
+        if (st != SJ_OK) break;
+        st = do_build(v, edge_col(path->edges[tr.pedge[ch]], v), &down[ch]);
+      }
+    }
+  }
+  if (st == SJ_OK) st = sync_read(c);
+  if (st != SJ_OK) {
+    cleanup();
+    return st;
+  }
+  prof_resolve(c, p0);
+  for (auto f : filters) free_filter(c, f);
+  filters.clear();
+  for (int i = 0; i < n; ++i) {
+    if (cur[i]) {
+      cur[i]->nrows = (int64_t)c->h_misc[kMiscSteps + last_slot[i]];
+      out_sieved[i] = cur[i];
+    } else {
+      out_sieved[i] = view_of(path->rels[i]);
+    }
+  }
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    stats->nsteps = (int)steps.size();
+    for (size_t s = 0; s < steps.size(); ++s) {
+      stats->step[s].kind = steps[s].kind;
+      stats->step[s].rel = steps[s].rel;
+      stats->step[s].rows_in = steps[s].slot_in >= 0
+                                   ? (int64_t)c->h_misc[kMiscSteps + steps[s].slot_in]
+                                   : steps[s].rows_in_host;
+      stats->step[s].rows_out = (int64_t)c->h_misc[kMiscSteps + steps[s].slot_out];
+    }
+    for (int i = 0; i < n; ++i) stats->rows_final[i] = out_sieved[i]->nrows;
+    stats->filter_bytes = filter_bytes;
+  }
+  return SJ_OK;
+}
+
+}  // extern "C"
+
+// ======================================================================== join
+namespace {
+
+struct LevelPlan {
+  int rel, rel_col;       // relation added at this level and its key column
+  int probe_rel, probe_col;  // already-joined column it is equal to
+};
+
+// Left-deep order: start at relation 0, then repeatedly the lowest-index
+// relation adjacent to the joined set.
+std::vector<LevelPlan> join_order(const sj_path* p) {
+  std::vector<LevelPlan> plan;
+  std::vector<int> in(p->nrel, 0);
+  in[0] = 1;
+  for (int added = 1; added < p->nrel; ++added) {
+    LevelPlan best{-1, 0, 0, 0};
+    for (int e = 0; e < p->nrel - 1; ++e) {
+      const sj_edge& E = p->edges[e];
+      for (int side = 0; side < 2; ++side) {
+        const int x = side ? E.rel_b : E.rel_a, cx = side ? E.col_b : E.col_a;
+        const int y = side ? E.rel_a : E.rel_b, cy = side ? E.col_a : E.col_b;
+        if (in[x] && !in[y] && (best.rel < 0 || y < best.rel)) best = {y, cy, x, cx};
+      }
+    }
+    in[best.rel] = 1;
+    plan.push_back(best);
+  }
+  return plan;
+}
+
+Terms terms_of(const sj_rel_s* r, int rel, int nrefs, const sj_colref* refs) {
+  Terms t;
+  memset(&t, 0, sizeof(t));
+  for (int k = 0; k < nrefs; ++k) {
+    if (refs[k].rel != rel) continue;
+    t.col[t.n] = r->cols[refs[k].col];
+    t.col_hi[t.n] = refs[k].wide ? r->cols[refs[k].col + 1] : nullptr;
+    t.n++;
+  }
+  return t;
+}
+
+uint64_t pow2_at_least(uint64_t x) {
+  uint64_t p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+using ColKey = std::pair<int, int>;
+
+struct Inter {
+  std::map<ColKey, const int32_t*> cols;
+  int64_t n = 0;
+  uint64_t* psum = nullptr;
+  bool base = true;  // still relation 0 itself
+  std::vector<std::pair<void*, size_t>> mem;
+};
+
+void free_inter(sj_ctx* c, Inter& in) {
+  for (auto& m : in.mem) dfree(c, m.first, m.second);
+  in.mem.clear();
+}
+
+struct Table2 {
+  Table t;
+  uint64_t nslots;
+};
+
+sj_status make_table(sj_ctx* c, Temps& tmp, int64_t nrows, Table2* out) {
+  sj_status st = SJ_OK;
+  const uint64_t nslots = pow2_at_least(std::max<uint64_t>(64, 2 * (uint64_t)nrows));
+  unsigned long long* slots = tmp.get<unsigned long long>(nslots, &st);
+  if (!slots) return fail(c, st, "hash table allocation failed");
+  SJ_CUDA(c, cudaMemsetAsync(slots, 0, nslots * 8, c->stream));
+  out->t.slots = slots;
+  out->t.bucket_mask = (uint32_t)(nslots / 4 - 1);
+  out->nslots = nslots;
+  return SJ_OK;
+}
+
+}  // namespace
+
+extern "C" sj_status sj_join(sj_ctx* c, const sj_path* path, const sj_rel* inputs, int mode,
+                             int nrefs, const sj_colref* refs, sj_result* result) {
+  if (!c || !path || !result) return fail(c, SJ_EINVAL, "null argument");
+  Tree tr;
+  SJ_TRY(validate_path(c, path, path->rels, &tr));
+  const int n = path->nrel;
+  if (mode != SJ_COUNT_SUM && mode != SJ_MATERIALIZE) return fail(c, SJ_EINVAL, "bad mode");
+  if (nrefs < 0 || nrefs > SJ_MAX_TERMS || (nrefs > 0 && !refs))
+    return fail(c, SJ_EINVAL, "bad column references");
+  if (mode == SJ_MATERIALIZE && nrefs < 1) return fail(c, SJ_EINVAL, "MATERIALIZE needs refs");
+  std::vector<const sj_rel_s*> rels(n);
+  for (int i = 0; i < n; ++i) {
+    rels[i] = inputs ? inputs[i] : path->rels[i];
+    if (!rels[i]) return fail(c, SJ_EINVAL, "null input relation");
+    if (rels[i]->ncols != path->rels[i]->ncols) return fail(c, SJ_EINVAL, "input column count differs");
+    if (rels[i]->nrows < 0) return fail(c, SJ_EINVAL, "relation row count unknown");
+  }
+  for (int k = 0; k < nrefs; ++k) {
+    const sj_colref& r = refs[k];
+    if (r.rel < 0 || r.rel >= n || r.col < 0 || r.col + (r.wide ? 1 : 0) >= rels[r.rel]->ncols)
+      return fail(c, SJ_EINVAL, "column reference out of range");
+    if (mode == SJ_MATERIALIZE && r.wide) return fail(c, SJ_EINVAL, "MATERIALIZE takes int32 refs");
+  }
+
+  // predicates of raw inputs
+  std::vector<sj_rel> sel(n, nullptr);
+  struct SelGuard {
+    sj_ctx* c;
+    std::vector<sj_rel>* v;
+    ~SelGuard() {
+      for (auto r : *v) free_rel(c, r);
+    }
+  } sel_guard{c, &sel};
+  if (!inputs && path->preds) {
+    bool any = false;
+    const size_t p0 = c->prof.size();
+    for (int i = 0; i < n; ++i) {
+      if (!has_pred(path, i)) continue;
+      std::vector<TestSpec> t{{path->preds[i].col, true, path->preds[i].lo, path->preds[i].hi, nullptr}};
+      SJ_TRY(sieve_step_timed(c, rels[i], t, i, -1, &sel[i]));
+      any = true;
+    }
+    if (any) {
+      SJ_TRY(sync_read(c));
+      prof_resolve(c, p0);
+      for (int i = 0; i < n; ++i)
+        if (sel[i]) {
+          sel[i]->nrows = (int64_t)c->h_misc[kMiscSteps + i];
+          rels[i] = sel[i];
+        }
+    }
+  }
+
+  memset(result, 0, sizeof(*result));
+  const bool want_sum = mode == SJ_COUNT_SUM && nrefs > 0;
+  const int nsm = c->num_sms;
+
+  if (n == 1) {
+    const sj_rel_s* r0 = rels[0];
+    if (mode == SJ_COUNT_SUM) {
+      result->count = (uint64_t)r0->nrows;
+      if (want_sum && r0->nrows > 0) {
+        SJ_CUDA(c, cudaMemsetAsync(c->d_misc + kMiscResult, 0, 3 * 8, c->stream));
+        SumTermsArgs a;
+        a.n = r0->nrows;
+        a.terms = terms_of(r0, 0, nrefs, refs);
+        a.result = reinterpret_cast<unsigned long long*>(c->d_misc + kMiscResult);
+        {
+          Launch L(c, SJ_K_AGG, 4.0 * a.terms.n * (double)a.n);
+          launch_sum_terms(a, nsm, c->stream);
+        }
+        SJ_TRY(check_launch(c, "k_sum_terms"));
+        SJ_TRY(sync_read(c));
+        result->sum = c->h_misc[kMiscResult + 2];
+      }
+      return SJ_OK;
+    }
+    sj_rel out = new_rel(c, nrefs, r0->nrows);
+    if (!out) return fail(c, SJ_ENOMEM, "result allocation failed");
+    out->d_n = nullptr;
+    out->nrows = r0->nrows;
+    for (int k = 0; k < nrefs && r0->nrows > 0; ++k) {
+      cudaError_t e = cudaMemcpyAsync(out->cols[k], r0->cols[refs[k].col], (size_t)r0->nrows * 4,
+                                      cudaMemcpyDeviceToDevice, c->stream);
+      if (e != cudaSuccess) {
+        free_rel(c, out);
+        return fail(c, SJ_ECUDA, std::string("cudaMemcpyAsync: ") + cudaGetErrorString(e));
+      }
+    }
+    sj_status st = sync_read(c);
+    if (st != SJ_OK) {
+      free_rel(c, out);
+      return st;
+    }
+    result->count = (uint64_t)out->nrows;
+    result->rows = out;
+    return SJ_OK;
+  }
+
+  const std::vector<LevelPlan> plan = join_order(path);
+  Inter in;
+  in.n = rels[0]->nrows;
+  for (int col = 0; col < rels[0]->ncols; ++col) in.cols[{0, col}] = rels[0]->cols[col];
+  std::vector<int> joined(n, 0);
+  joined[0] = 1;
+  uint64_t intermediate = 0;
+  sj_rel out_rel = nullptr;
+  sj_status st = SJ_OK;
+
+  for (size_t L = 0; L < plan.size() && st == SJ_OK; ++L) {
+    const LevelPlan& lp = plan[L];
+    const sj_rel_s* B = rels[lp.rel];
+    const int64_t nb = B->nrows;
+    const int64_t np = in.n;
+    const bool last = L + 1 == plan.size();
+    joined[lp.rel] = 1;
+    const int32_t* pk = in.cols.at({lp.probe_rel, lp.probe_col});
+    Temps tmp(c);
+
+    if (last && mode == SJ_COUNT_SUM) {
+      if (np == 0 || nb == 0) break;  // empty join
+      Table2 tb;
+      if ((st = make_table(c, tmp, nb, &tb)) != SJ_OK) break;
+      unsigned long long* cnt = tmp.get<unsigned long long>(tb.nslots, &st);
+      unsigned long long* sum = tmp.get<unsigned long long>(tb.nslots, &st);
+      if (st != SJ_OK) {
+        fail(c, st, "aggregate table allocation failed");
+        break;
+      }
+      cudaMemsetAsync(cnt, 0, tb.nslots * 8, c->stream);
+      cudaMemsetAsync(sum, 0, tb.nslots * 8, c->stream);
+      cudaMemsetAsync(c->d_misc + kMiscResult, 0, 3 * 8, c->stream);
+      AggInsertArgs ai;
+      ai.keys = B->cols[lp.rel_col];
+      ai.n = nb;
+      ai.t = tb.t;
+      ai.terms = want_sum ? terms_of(B, lp.rel, nrefs, refs) : Terms{};
+      if (!want_sum) memset(&ai.terms, 0, sizeof(ai.terms));
+      ai.cnt = cnt;
+      ai.sum = sum;
+      ai.status = status_ptr(c);
+      {
+        Launch Lk(c, SJ_K_AGG, (4.0 + 4.0 * ai.terms.n) * (double)nb);
+        launch_agg_insert(ai, nsm, c->stream);
+      }
+      if ((st = check_launch(c, "k_agg_insert")) != SJ_OK) break;
+      AggProbeArgs ap;
+      ap.keys = pk;
+      ap.n = np;
+      ap.t = tb.t;
+      ap.cnt = cnt;
+      ap.sum = sum;
+      memset(&ap.probe_terms, 0, sizeof(ap.probe_terms));
+      ap.psum_in = nullptr;
+      if (want_sum) {
+        if (in.base) ap.probe_terms = terms_of(rels[0], 0, nrefs, refs);
+        else ap.psum_in = in.psum;
+      }
+      ap.result = reinterpret_cast<unsigned long long*>(c->d_misc + kMiscResult);
+      ap.status = status_ptr(c);
+      {
+        const double per = 4.0 + (ap.psum_in ? 8.0 : 4.0 * ap.probe_terms.n);
+        Launch Lk(c, SJ_K_AGG, per * (double)np);
+        launch_agg_probe(ap, nsm, c->stream);
+      }
+      if ((st = check_launch(c, "k_agg_probe")) != SJ_OK) break;
+      if ((st = sync_read(c)) != SJ_OK) break;
+      const uint64_t lo = c->h_misc[kMiscResult], hi = c->h_misc[kMiscResult + 1];
+      if (hi != 0 || lo >= (1ull << 63)) {
+        st = fail(c, SJ_EOVERFLOW, "COUNT(*) reached 2^63");
+        break;
+      }
+      result->count = lo;
+      result->sum = c->h_misc[kMiscResult + 2];
+      break;
+    }
+
+    // ---- multimap level: build on B, probe with the intermediate, expand
+    // columns that must survive this level
+    std::vector<ColKey> carried;
+    if (last) {
+      for (int k = 0; k < nrefs; ++k) carried.push_back({refs[k].rel, refs[k].col});
+    } else {
+      std::map<ColKey, int> need;
+      for (size_t L2 = L + 1; L2 < plan.size(); ++L2)
+        if (joined[plan[L2].probe_rel]) need[{plan[L2].probe_rel, plan[L2].probe_col}] = 1;
+      if (mode == SJ_MATERIALIZE)
+        for (int k = 0; k < nrefs; ++k)
+          if (joined[refs[k].rel]) need[{refs[k].rel, refs[k].col}] = 1;
+      for (auto& kv : need) carried.push_back(kv.first);
+    }
+    const bool carry_sum = want_sum && !last;
+
+    uint64_t Q = 0, T = 0;
+    Table2 tb{};
+    int32_t* rows = nullptr;
+    uint64_t* off = nullptr;
+    int32_t *prow = nullptr, *pid = nullptr;
+    uint64_t* o = nullptr;
+    if (np > 0 && nb > 0) {
+      if ((st = make_table(c, tmp, nb, &tb)) != SJ_OK) break;
+      uint32_t* cnt = tmp.get<uint32_t>(nb, &st);
+      uint32_t* rid = tmp.get<uint32_t>(nb, &st);
+      uint32_t* rank = tmp.get<uint32_t>(nb, &st);
+      off = tmp.get<uint64_t>(nb, &st);
+      rows = tmp.get<int32_t>(nb, &st);
+      prow = tmp.get<int32_t>(np, &st);
+      pid = tmp.get<int32_t>(np, &st);
+      o = tmp.get<uint64_t>(np, &st);
+      if (st != SJ_OK) {
+        fail(c, st, "join level allocation failed");
+        break;
+      }
+      cudaMemsetAsync(cnt, 0, (size_t)nb * 4, c->stream);
+      cudaMemsetAsync(c->d_misc + kMiscNuniq, 0, 8, c->stream);
+      uint32_t* nuniq = reinterpret_cast<uint32_t*>(c->d_misc + kMiscNuniq);
+      MMInsertArgs mi{B->cols[lp.rel_col], nb, tb.t, nuniq, cnt, rid, rank, status_ptr(c)};
+      {
+        Launch Lk(c, SJ_K_HT_BUILD, 12.0 * (double)nb);
+        launch_mm_insert(mi, nsm, c->stream);
+      }
+      if ((st = check_launch(c, "k_mm_insert")) != SJ_OK) break;
+      ScanArgs sa;
+      sa.in = cnt;
+      sa.out = off;
+      sa.n_host = 0;
+      sa.n_dev = nuniq;
+      sa.total = nullptr;
+      if ((st = scratch_for<1>(c, (nb + kScanTile - 1) / kScanTile, &sa.tile_counter, &sa.lb)) != SJ_OK)
+        break;
+      {
+        Launch Lk(c, SJ_K_HT_BUILD, 12.0 * (double)nb);
+        launch_scan_u32(sa, nb, c->stream);
+      }
+      if ((st = check_launch(c, "k_scan_u32")) != SJ_OK) break;
+      MMScatterArgs ms{rid, rank, off, nb, rows};
+      {
+        Launch Lk(c, SJ_K_HT_BUILD, 20.0 * (double)nb);
+        launch_mm_scatter(ms, nsm, c->stream);
+      }
+      if ((st = check_launch(c, "k_mm_scatter")) != SJ_OK) break;
+      MMProbeArgs mp;
+      mp.keys = pk;
+      mp.n = np;
+      mp.t = tb.t;
+      mp.cnt = cnt;
+      mp.prow = prow;
+      mp.pid = pid;
+      mp.o = o;
+      mp.totals = c->d_misc + kMiscTotals;
+      if ((st = scratch_for<2>(c, (np + kProbeTile - 1) / kProbeTile, &mp.tile_counter, &mp.lb)) !=
+          SJ_OK)
+        break;
+      {
+        Launch Lk(c, SJ_K_HT_PROBE, 4.0 * (double)np);
+        launch_mm_probe(mp, c->stream);
+      }
+      if ((st = check_launch(c, "k_mm_probe")) != SJ_OK) break;
+      if ((st = sync_read(c)) != SJ_OK) break;
+      Q = c->h_misc[kMiscTotals];
+      T = c->h_misc[kMiscTotals + 1];
+      if (c->prof_on && !c->prof.empty()) c->prof.back().bytes += 16.0 * (double)Q;
+    }
+    if (!last) intermediate += T;
+    if (T >= (uint64_t(1) << 31) * 16) {
+      st = fail(c, SJ_ENOMEM, "intermediate result too large");
+      break;
+    }
+
+    // outputs of this level
+    Inter nx;
+    nx.n = (int64_t)T;
+    nx.base = false;
+    std::vector<int32_t*> outs;
+    if (last) {
+      out_rel = new_rel(c, nrefs, (int64_t)T);
+      if (!out_rel) {
+        st = fail(c, SJ_ENOMEM, "result allocation failed");
+        break;
+      }
+      out_rel->d_n = nullptr;
+      out_rel->nrows = (int64_t)T;
+      for (int k = 0; k < nrefs; ++k) outs.push_back(out_rel->cols[k]);
+    } else {
+      for (auto& ck : carried) {
+        void* p = dalloc(c, std::max<uint64_t>(T, 1) * 4);
+        if (!p) {
+          st = SJ_ENOMEM;
+          break;
+        }
+        nx.mem.push_back({p, std::max<uint64_t>(T, 1) * 4});
+        nx.cols[ck] = static_cast<int32_t*>(p);
+        outs.push_back(static_cast<int32_t*>(p));
+      }
+      if (st == SJ_OK && carry_sum) {
+        void* p = dalloc(c, std::max<uint64_t>(T, 1) * 8);
+        if (!p) st = SJ_ENOMEM;
+        else {
+          nx.mem.push_back({p, std::max<uint64_t>(T, 1) * 8});
+          nx.psum = static_cast<uint64_t*>(p);
+        }
+      }
+      if (st != SJ_OK) {
+        free_inter(c, nx);
+        fail(c, st, "intermediate allocation failed");
+        break;
+      }
+    }
+    if (T > 0) {
+      // one expand launch per group of at most kMaxCols output columns
+      const size_t ncar = carried.size();
+      for (size_t c0 = 0; c0 < std::max<size_t>(ncar, 1) && st == SJ_OK; c0 += kMaxCols) {
+        MMExpandArgs ex;
+        memset(&ex, 0, sizeof(ex));
+        ex.T = T;
+        ex.Q = Q;
+        ex.o = o;
+        ex.prow = prow;
+        ex.pid = pid;
+        ex.off = off;
+        ex.rows = rows;
+        const size_t c1 = std::min(ncar, c0 + kMaxCols);
+        for (size_t k = c0; k < c1; ++k) {
+          const ColKey ck = carried[k];
+          const int slot = (int)(k - c0);
+          ex.src_build[slot] = ck.first == lp.rel ? 1 : 0;
+          ex.src[slot] = ck.first == lp.rel ? B->cols[ck.second] : in.cols.at(ck);
+          ex.out[slot] = outs[k];
+        }
+        ex.nout = (int)(c1 - c0);
+        if (c0 == 0 && carry_sum) {
+          ex.psum_out = nx.psum;
+          if (in.base) ex.probe_terms = terms_of(rels[0], 0, nrefs, refs);
+          else ex.psum_in = in.psum;
+          ex.build_terms = terms_of(B, lp.rel, nrefs, refs);
+        }
+        {
+          const double per = 8.0 * ex.nout + (ex.psum_out ? 16.0 : 0.0) + 12.0;
+          Launch Lk(c, SJ_K_HT_EXPAND, per * (double)T);
+          launch_mm_expand(ex, c->stream);
+        }
+        st = check_launch(c, "k_mm_expand");
+      }
+    }
+    if (st != SJ_OK) {
+      free_inter(c, nx);
+      break;
+    }
+    free_inter(c, in);
+    in = std::move(nx);
+    if (last) {
+      result->count = T;
+      st = sync_read(c);
+    }
+  }
+  free_inter(c, in);
+  if (st != SJ_OK) {
+    free_rel(c, out_rel);
+    return st;
+  }
+  if (mode == SJ_MATERIALIZE) {
+    if (!out_rel) {  // an empty level before the last
+      out_rel = new_rel(c, nrefs, 0);
+      if (!out_rel) return fail(c, SJ_ENOMEM, "result allocation failed");
+      out_rel->d_n = nullptr;
+      out_rel->nrows = 0;
+    }
+    result->rows = out_rel;
+    result->count = (uint64_t)out_rel->nrows;
+  }
+  result->intermediate = intermediate;
+  return SJ_OK;
+}
+
+// ======================================================================== profiling
+extern "C" {
+
+sj_status sj_prof_enable(sj_ctx* c, int on) {
+  if (!c) return SJ_EINVAL;
+  c->prof_on = on != 0;
+  return SJ_OK;
+}
+
+static sj_status prof_collect(sj_ctx* c) {
+  SJ_CUDA(c, cudaStreamSynchronize(c->stream));
+  for (const ProfRec& r : c->prof) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.e0, r.e1) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    c->prof_ms[r.kind] += ms;
+    c->prof_bytes[r.kind] += (r.slot_a < 0 && r.slot_b < 0) ? r.bytes : r.bytes;
+    c->prof_n[r.kind] += 1;
+  }
+  c->prof.clear();
+  c->ev_used = 0;
+  return SJ_OK;
+}
+
+sj_status sj_prof_reset(sj_ctx* c) {
+  if (!c) return SJ_EINVAL;
+  SJ_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->prof.clear();
+  c->ev_used = 0;
+  for (int k = 0; k < SJ_K_COUNT; ++k) {
+    c->prof_ms[k] = 0;
+    c->prof_bytes[k] = 0;
+    c->prof_n[k] = 0;
+  }
+  c->launches = 0;
+  c->h2d_bytes = 0;
+  c->d2h_bytes = 0;
+  return SJ_OK;
+}
+
+sj_status sj_prof_read(sj_ctx* c, int kind, int64_t* launches, double* ms, double* bytes) {
+  if (!c || kind < 0 || kind >= SJ_K_COUNT) return fail(c, SJ_EINVAL, "bad profiling kind");
+  SJ_TRY(prof_collect(c));
+  if (launches) *launches = c->prof_n[kind];
+  if (ms) *ms = c->prof_ms[kind];
+  if (bytes) *bytes = c->prof_bytes[kind];
+  return SJ_OK;
+}
+
+sj_status sj_counters(sj_ctx* c, int64_t* launches, int64_t* h2d_bytes, int64_t* d2h_bytes) {
+  if (!c) return SJ_EINVAL;
+  if (launches) *launches = c->launches;
+  if (h2d_bytes) *h2d_bytes = c->h2d_bytes;
+  if (d2h_bytes) *d2h_bytes = c->d2h_bytes;
+  return SJ_OK;
+}
+
+}  // extern "C"

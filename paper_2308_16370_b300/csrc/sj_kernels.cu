@@ -1,0 +1,743 @@
+// sm_103a kernels of the sieved multi-way join.
+//
+//   k_bloom_build  -- Bloom filter build (Sec. 2.1 step 1): read-before-OR
+//                     atomics into an L2-resident filter
+//   k_bloom_probe  -- membership test (Sec. 2.1 step 3)
+//   k_sieve        -- one pruning step (Sec. 2.2): vectorised key loads, filter
+//                     probes, order-preserving stream compaction with a
+//                     decoupled look-back
+//   k_scan_u32     -- exclusive prefix sum (hash-table offsets)
+//   k_mm_*         -- multimap hash join level (Sec. 2.2 enumeration phase)
+//   k_agg_*        -- last join level folded into COUNT(*) / SUM
+//
+// Nothing here is a dense contraction, so there are no tensor-core paths: all
+// kernels are bound by HBM bandwidth or by L2 latency of random accesses.
+#include "sj_kernels.cuh"
+
+namespace sj {
+
+namespace {
+
+constexpr uint64_t kTableSeed = 0x9e3779b97f4a7c15ull;
+
+__device__ __forceinline__ uint32_t table_bucket(int32_t key, uint32_t mask) {
+  return (uint32_t)fmix64((uint64_t)(uint32_t)key ^ kTableSeed) & mask;
+}
+
+// Sum of the SUM terms of one row, int64 arithmetic mod 2^64.  The loop has a
+// constant trip count so the kernel-parameter arrays are indexed statically.
+__device__ __forceinline__ uint64_t term_sum(const Terms& t, int64_t row) {
+  uint64_t v = 0;
+#pragma unroll
+  for (int i = 0; i < kMaxTerms; ++i) {
+    if (i < t.n) {
+      if (t.col_hi[i]) {
+        const uint64_t lo = (uint32_t)__ldg(t.col[i] + row);
+        const uint64_t hi = (uint32_t)__ldg(t.col_hi[i] + row);
+        v += lo | (hi << 32);
+      } else {
+        v += (uint64_t)(int64_t)__ldg(t.col[i] + row);
+      }
+    }
+  }
+  return v;
+}
+
+// ---------------------------------------------------------------- Bloom build
+__device__ __forceinline__ void or_bits(uint32_t* p, uint32_t mask) {
+  // Read first: under skew most repeated keys find their bits already set and
+  // skip the atomic entirely (L2-coherent load, bypassing L1).
+  if ((__ldcg(p) & mask) != mask) atomicOr(p, mask);
+}
+
+__device__ __forceinline__ void bloom_insert(const BloomBuildArgs& a, uint64_t nb, int32_t key) {
+  const uint64_t h = key_hash(key, a.seed);
+  if (a.layout == 0) {
+    uint32_t* base = a.words + (((h >> 32) * nb) >> 32) * 8;
+#pragma unroll
+    for (uint32_t i = 0; i < 4; ++i) {
+      if (i < a.k) {
+        const uint32_t bit = (uint32_t)(h >> (8 * i)) & 255u;
+        or_bits(base + (bit >> 5), 1u << (bit & 31));
+      }
+    }
+  } else {
+    const uint64_t m = nb * 256ull;
+    const uint64_t h1 = h & 0xffffffffull;
+    const uint64_t h2 = (h >> 32) | 1ull;
+    for (uint32_t i = 0; i < a.k; ++i) {
+      const uint64_t g = (h1 + (uint64_t)i * h2) % m;
+      or_bits(a.words + (g >> 5), 1u << (g & 31));
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_bloom_build(BloomBuildArgs a) {
+  const int64_t n = a.n_dev ? (int64_t)(*a.n_dev) : a.n_host;
+  uint64_t nb = ((uint64_t)a.bits_per_key * (uint64_t)n + 255ull) / 256ull;
+  if (nb < 1) nb = 1;
+  if (nb > a.nblocks_cap) nb = a.nblocks_cap;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.hdr[0] = nb;
+    a.hdr[1] = (uint64_t)n;
+  }
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nvec = n >> 2;
+  const int4* kv = reinterpret_cast<const int4*>(a.keys);
+  for (int64_t i = gid; i < nvec; i += stride) {
+    const int4 v = __ldcs(kv + i);
+    bloom_insert(a, nb, v.x);
+    bloom_insert(a, nb, v.y);
+    bloom_insert(a, nb, v.z);
+    bloom_insert(a, nb, v.w);
+  }
+  for (int64_t r = (nvec << 2) + gid; r < n; r += stride) bloom_insert(a, nb, __ldcs(a.keys + r));
+}
+
+__global__ void __launch_bounds__(kBlock) k_bloom_probe(BloomProbeArgs a) {
+  const uint64_t nb = __ldg(a.f.hdr);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride)
+    a.out[i] = filter_contains(a.f, nb, __ldg(a.keys + i)) ? 1 : 0;
+}
+
+// ---------------------------------------------------------------- sieve
+__device__ __forceinline__ bool run_test(const SieveTest& t, uint64_t nb, int32_t v) {
+  return t.is_pred ? (v >= t.lo && v < t.hi) : filter_contains(t.f, nb, v);
+}
+
+__global__ void __launch_bounds__(kBlock) k_sieve(SieveArgs a) {
+  __shared__ uint32_t s_tile;
+  __shared__ Vec<1> s_warp[kBlock / 32];
+  __shared__ uint64_t s_prefix;
+  const int tid = threadIdx.x;
+  if (tid == 0) s_tile = atomicAdd(a.tile_counter, 1u);
+  __syncthreads();
+  const uint32_t tile = s_tile;
+  const int64_t n = a.n_dev ? (int64_t)(*a.n_dev) : a.n_host;
+  const int64_t ntiles = (n + kSieveTile - 1) / kSieveTile;
+  if ((int64_t)tile >= ntiles) {
+    if (tile == 0 && tid == 0) {
+      *a.out_n = 0;
+      if (a.out_n2) *a.out_n2 = 0;
+    }
+    return;
+  }
+  const int64_t base = (int64_t)tile * kSieveTile;
+  const int32_t* vcol = a.ntest > 0 ? a.test[0].col : nullptr;
+
+  // 1. first test column: 4 coalesced 16-byte loads per thread
+  int32_t key[16];
+  uint32_t alive = 0;
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const int64_t r0 = base + (int64_t)(v * kBlock + tid) * 4;
+    if (r0 + 4 <= n) {
+      if (vcol) {
+        const int4 x = __ldcs(reinterpret_cast<const int4*>(vcol + r0));
+        key[4 * v + 0] = x.x;
+        key[4 * v + 1] = x.y;
+        key[4 * v + 2] = x.z;
+        key[4 * v + 3] = x.w;
+      }
+      alive |= 0xfu << (4 * v);
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        key[4 * v + e] = 0;
+        if (r0 + e < n) {
+          if (vcol) key[4 * v + e] = __ldcs(vcol + r0 + e);
+          alive |= 1u << (4 * v + e);
+        }
+      }
+    }
+  }
+
+  // 2. tests; later tests only load the rows still alive
+  if (a.ntest > 0) {
+    const uint64_t nb = a.test[0].is_pred ? 0 : __ldg(a.test[0].f.hdr);
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+      if ((alive >> i) & 1u)
+        if (!run_test(a.test[0], nb, key[i])) alive &= ~(1u << i);
+  }
+#pragma unroll
+  for (int t = 1; t < kMaxTests; ++t) {
+    if (t < a.ntest) {
+      const SieveTest& tt = a.test[t];
+      const uint64_t nb = tt.is_pred ? 0 : __ldg(tt.f.hdr);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        if ((alive >> i) & 1u) {
+          const int64_t row = base + (int64_t)((i >> 2) * kBlock + tid) * 4 + (i & 3);
+          if (!run_test(tt, nb, __ldcs(tt.col + row))) alive &= ~(1u << i);
+        }
+      }
+    }
+  }
+
+  // 3. block scan of the survivor counts of the 4 chunks (16 bits each)
+  Vec<1> cnt;
+  cnt.v[0] = 0;
+#pragma unroll
+  for (int v = 0; v < 4; ++v) cnt.v[0] |= (uint64_t)__popc((alive >> (4 * v)) & 0xfu) << (16 * v);
+  Vec<1> tot;
+  const Vec<1> ex = block_exclusive_scan<1>(cnt, &tot, s_warp);
+  uint64_t chunk_off[4];
+  uint64_t tile_total = 0;
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    chunk_off[v] = tile_total;
+    tile_total += (tot.v[0] >> (16 * v)) & 0xffffull;
+  }
+
+  // 4. decoupled look-back for the tile's global offset
+  if (tid < 32) {
+    Vec<1> aggv;
+    aggv.v[0] = tile_total;
+    if (tile == 0) {
+      if (tid == 0) {
+        lb_publish<1>(a.lb, 0, 2, aggv);
+        s_prefix = 0;
+      }
+    } else {
+      if (tid == 0) lb_publish<1>(a.lb, tile, 1, aggv);
+      const Vec<1> e = lb_exclusive<1>(a.lb, tile);
+      if (tid == 0) {
+        Vec<1> incv;
+        incv.v[0] = e.v[0] + tile_total;
+        lb_publish<1>(a.lb, tile, 2, incv);
+        s_prefix = e.v[0];
+      }
+    }
+  }
+  __syncthreads();
+  const uint64_t prefix = s_prefix;
+  if ((int64_t)tile == ntiles - 1 && tid == 0) {
+    *a.out_n = prefix + tile_total;
+    if (a.out_n2) *a.out_n2 = prefix + tile_total;
+  }
+
+  // 5. write the survivors of every output column, in input order
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const uint32_t bits = (alive >> (4 * v)) & 0xfu;
+    if (!bits) continue;
+    const uint64_t pos0 = prefix + chunk_off[v] + ((ex.v[0] >> (16 * v)) & 0xffffull);
+    const int64_t r0 = base + (int64_t)(v * kBlock + tid) * 4;
+#pragma unroll
+    for (int j = 0; j < kMaxCols; ++j) {
+      if (j >= a.nout) break;
+      int32_t val[4];
+      if (a.out_is_vec[j]) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) val[e] = key[4 * v + e];
+      } else if (r0 + 4 <= n) {
+        const int4 x = __ldcs(reinterpret_cast<const int4*>(a.in[j] + r0));
+        val[0] = x.x;
+        val[1] = x.y;
+        val[2] = x.z;
+        val[3] = x.w;
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) val[e] = ((bits >> e) & 1u) ? __ldcs(a.in[j] + r0 + e) : 0;
+      }
+      int32_t* dst = a.out[j] + pos0;
+      int k = 0;
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        if ((bits >> e) & 1u) dst[k++] = val[e];
+    }
+  }
+}
+
+// ---------------------------------------------------------------- scan
+__global__ void __launch_bounds__(kBlock) k_scan_u32(ScanArgs a) {
+  __shared__ uint32_t s_tile;
+  __shared__ Vec<2> s_warp[kBlock / 32];
+  __shared__ uint64_t s_prefix;
+  const int tid = threadIdx.x;
+  if (tid == 0) s_tile = atomicAdd(a.tile_counter, 1u);
+  __syncthreads();
+  const uint32_t tile = s_tile;
+  const int64_t n = a.n_dev ? (int64_t)(*a.n_dev) : a.n_host;
+  const int64_t ntiles = (n + kScanTile - 1) / kScanTile;
+  if ((int64_t)tile >= ntiles) {
+    if (tile == 0 && tid == 0 && a.total) *a.total = 0;
+    return;
+  }
+  const int64_t base = (int64_t)tile * kScanTile;
+  uint32_t x[8];
+#pragma unroll
+  for (int v = 0; v < 2; ++v) {
+    const int64_t r0 = base + (int64_t)(v * kBlock + tid) * 4;
+    if (r0 + 4 <= n) {
+      const uint4 q = __ldg(reinterpret_cast<const uint4*>(a.in + r0));
+      x[4 * v] = q.x;
+      x[4 * v + 1] = q.y;
+      x[4 * v + 2] = q.z;
+      x[4 * v + 3] = q.w;
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) x[4 * v + e] = (r0 + e < n) ? __ldg(a.in + r0 + e) : 0u;
+    }
+  }
+  Vec<2> s;
+  s.v[0] = (uint64_t)x[0] + x[1] + x[2] + x[3];
+  s.v[1] = (uint64_t)x[4] + x[5] + x[6] + x[7];
+  Vec<2> tot;
+  const Vec<2> ex = block_exclusive_scan<2>(s, &tot, s_warp);
+  const uint64_t tile_total = tot.v[0] + tot.v[1];
+  if (tid < 32) {
+    Vec<1> aggv;
+    aggv.v[0] = tile_total;
+    if (tile == 0) {
+      if (tid == 0) {
+        lb_publish<1>(a.lb, 0, 2, aggv);
+        s_prefix = 0;
+      }
+    } else {
+      if (tid == 0) lb_publish<1>(a.lb, tile, 1, aggv);
+      const Vec<1> e = lb_exclusive<1>(a.lb, tile);
+      if (tid == 0) {
+        Vec<1> incv;
+        incv.v[0] = e.v[0] + tile_total;
+        lb_publish<1>(a.lb, tile, 2, incv);
+        s_prefix = e.v[0];
+      }
+    }
+  }
+  __syncthreads();
+  const uint64_t prefix = s_prefix;
+  if ((int64_t)tile == ntiles - 1 && tid == 0 && a.total) *a.total = prefix + tile_total;
+#pragma unroll
+  for (int v = 0; v < 2; ++v) {
+    uint64_t run = prefix + (v ? tot.v[0] : 0) + ex.v[v];
+    const int64_t r0 = base + (int64_t)(v * kBlock + tid) * 4;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      if (r0 + e < n) a.out[r0 + e] = run;
+      run += x[4 * v + e];
+    }
+  }
+}
+
+// ---------------------------------------------------------------- hash tables
+// Find the slot holding `key`; insert it if absent.  Multimap variant: the
+// inserting thread assigns the key a dense id (published in the slot's high
+// word, id + 1; 0xffffffff marks "id pending").  Returns the id, or -1 with
+// kErrTableFull when the probe sequence is exhausted.
+__device__ __forceinline__ int32_t mm_find_or_insert(const Table& t, int32_t key, uint32_t* nuniq,
+                                                     uint32_t* status) {
+  uint32_t b = table_bucket(key, t.bucket_mask);
+  const uint64_t lo = (uint32_t)key;
+  for (uint32_t step = 0; step <= t.bucket_mask; ++step) {
+    unsigned long long* bk = t.slots + (uint64_t)b * 4;
+#pragma unroll 1
+    for (int s = 0; s < 4; ++s) {
+      uint64_t v = ld_volatile_u64(reinterpret_cast<const uint64_t*>(bk + s));
+      if (v == 0) {
+        const unsigned long long pend = (0xffffffffull << 32) | lo;
+        const unsigned long long old = atomicCAS(bk + s, 0ull, pend);
+        if (old == 0) {
+          const uint32_t id = atomicAdd(nuniq, 1u);
+          st_volatile_u64(reinterpret_cast<uint64_t*>(bk + s), ((uint64_t)(id + 1) << 32) | lo);
+          return (int32_t)id;
+        }
+        v = old;
+      }
+      if ((v & 0xffffffffull) == lo) {
+        uint32_t spins = 0;
+        while ((v >> 32) == 0xffffffffull) {
+          if (++spins > kSpinLimit) {
+            atomicOr(status, kErrTimeout);
+            return -1;
+          }
+          __nanosleep(32);
+          v = ld_volatile_u64(reinterpret_cast<const uint64_t*>(bk + s));
+        }
+        return (int32_t)((v >> 32) - 1);
+      }
+    }
+    b = (b + 1) & t.bucket_mask;
+  }
+  atomicOr(status, kErrTableFull);
+  return -1;
+}
+
+// Read-only lookup after the build finished: slot index of `key`, or -1.
+__device__ __forceinline__ int64_t table_find(const Table& t, int32_t key) {
+  uint32_t b = table_bucket(key, t.bucket_mask);
+  const uint64_t lo = (uint32_t)key;
+  for (uint32_t step = 0; step <= t.bucket_mask; ++step) {
+    const ulonglong2* p = reinterpret_cast<const ulonglong2*>(t.slots + (uint64_t)b * 4);
+    const ulonglong2 q0 = __ldg(p);
+    const ulonglong2 q1 = __ldg(p + 1);
+    const uint64_t sl[4] = {q0.x, q0.y, q1.x, q1.y};
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      if (sl[s] == 0) return -1;
+      if ((sl[s] & 0xffffffffull) == lo) return (int64_t)b * 4 + s;
+    }
+    b = (b + 1) & t.bucket_mask;
+  }
+  return -1;
+}
+
+__global__ void __launch_bounds__(kBlock) k_mm_insert(MMInsertArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  // every lane of a warp runs the same number of iterations (warp-collective match)
+  const int64_t first = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31);
+  for (int64_t w0 = first; w0 < a.n; w0 += stride) {
+    const int64_t row = w0 + lane;
+    const bool active = row < a.n;
+    int32_t id = -1;
+    if (active) id = mm_find_or_insert(a.t, __ldcs(a.keys + row), a.nuniq, a.status);
+    const int32_t gkey = (active && id >= 0) ? id : -2 - lane;
+    const uint32_t group = __match_any_sync(0xffffffffu, gkey);
+    const int leader = __ffs(group) - 1;
+    uint32_t base = 0;
+    if (lane == leader && gkey >= 0) base = atomicAdd(a.cnt + gkey, (uint32_t)__popc(group));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (active && id >= 0) {
+      a.rid[row] = (uint32_t)id;
+      a.rank[row] = base + __popc(group & ((1u << lane) - 1u));
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_mm_scatter(MMScatterArgs a) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride)
+    a.rows[__ldg(a.off + __ldg(a.rid + i)) + __ldg(a.rank + i)] = (int32_t)i;
+}
+
+__global__ void __launch_bounds__(kBlock) k_mm_probe(MMProbeArgs a) {
+  __shared__ uint32_t s_tile;
+  __shared__ Vec<3> s_warp[kBlock / 32];
+  __shared__ uint64_t s_prefix[2];
+  const int tid = threadIdx.x;
+  if (tid == 0) s_tile = atomicAdd(a.tile_counter, 1u);
+  __syncthreads();
+  const uint32_t tile = s_tile;
+  const int64_t n = a.n;
+  const int64_t ntiles = (n + kProbeTile - 1) / kProbeTile;
+  if ((int64_t)tile >= ntiles) return;
+  const int64_t base = (int64_t)tile * kProbeTile;
+  int32_t id[8];
+  uint32_t m[8];
+#pragma unroll
+  for (int v = 0; v < 2; ++v) {
+    const int64_t r0 = base + (int64_t)(v * kBlock + tid) * 4;
+    int32_t k4[4];
+    bool ok4[4];
+    if (r0 + 4 <= n) {
+      const int4 x = __ldcs(reinterpret_cast<const int4*>(a.keys + r0));
+      k4[0] = x.x; k4[1] = x.y; k4[2] = x.z; k4[3] = x.w;
+      ok4[0] = ok4[1] = ok4[2] = ok4[3] = true;
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        ok4[e] = r0 + e < n;
+        k4[e] = ok4[e] ? __ldcs(a.keys + r0 + e) : 0;
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      id[4 * v + e] = -1;
+      m[4 * v + e] = 0;
+      if (ok4[e]) {
+        const int64_t s = table_find(a.t, k4[e]);
+        if (s >= 0) {
+          const uint32_t kid = (uint32_t)(__ldg(a.t.slots + s) >> 32) - 1u;
+          id[4 * v + e] = (int32_t)kid;
+          m[4 * v + e] = __ldg(a.cnt + kid);
+        }
+      }
+    }
+  }
+  // scan channels: [0] hit counts of chunks 0 and 1 packed (32 bits each),
+  // [1] output tuples of chunk 0, [2] output tuples of chunk 1
+  Vec<3> c;
+  uint32_t hits[2] = {0, 0};
+  uint64_t msum[2] = {0, 0};
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    hits[i >> 2] += m[i] ? 1u : 0u;
+    msum[i >> 2] += m[i];
+  }
+  c.v[0] = (uint64_t)hits[0] | ((uint64_t)hits[1] << 32);
+  c.v[1] = msum[0];
+  c.v[2] = msum[1];
+  Vec<3> tot;
+  const Vec<3> ex = block_exclusive_scan<3>(c, &tot, s_warp);
+  const uint64_t hits0 = tot.v[0] & 0xffffffffull, hits1 = tot.v[0] >> 32;
+  const uint64_t tile_hits = hits0 + hits1;
+  const uint64_t tile_tuples = tot.v[1] + tot.v[2];
+  if (tid < 32) {
+    Vec<2> aggv;
+    aggv.v[0] = tile_hits;
+    aggv.v[1] = tile_tuples;
+    if (tile == 0) {
+      if (tid == 0) {
+        lb_publish<2>(a.lb, 0, 2, aggv);
+        s_prefix[0] = 0;
+        s_prefix[1] = 0;
+      }
+    } else {
+      if (tid == 0) lb_publish<2>(a.lb, tile, 1, aggv);
+      const Vec<2> e = lb_exclusive<2>(a.lb, tile);
+      if (tid == 0) {
+        Vec<2> incv;
+        incv.v[0] = e.v[0] + tile_hits;
+        incv.v[1] = e.v[1] + tile_tuples;
+        lb_publish<2>(a.lb, tile, 2, incv);
+        s_prefix[0] = e.v[0];
+        s_prefix[1] = e.v[1];
+      }
+    }
+  }
+  __syncthreads();
+  const uint64_t p_hits = s_prefix[0], p_tuples = s_prefix[1];
+  if ((int64_t)tile == ntiles - 1 && tid == 0) {
+    a.totals[0] = p_hits + tile_hits;
+    a.totals[1] = p_tuples + tile_tuples;
+  }
+#pragma unroll
+  for (int v = 0; v < 2; ++v) {
+    uint64_t q = p_hits + (v ? hits0 : 0) + ((ex.v[0] >> (32 * v)) & 0xffffffffull);
+    uint64_t o = p_tuples + (v ? tot.v[1] : 0) + ex.v[1 + v];
+    const int64_t r0 = base + (int64_t)(v * kBlock + tid) * 4;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      if (m[4 * v + e]) {
+        a.prow[q] = (int32_t)(r0 + e);
+        a.pid[q] = id[4 * v + e];
+        a.o[q] = o;
+        ++q;
+        o += m[4 * v + e];
+      }
+    }
+  }
+}
+
+// Largest q in [lo, hi] with o[q] <= j (o strictly increasing, o[lo] <= j).
+__device__ __forceinline__ uint64_t upper_q(const uint64_t* o, uint64_t lo, uint64_t hi,
+                                            uint64_t j) {
+  while (lo < hi) {
+    const uint64_t mid = (lo + hi + 1) >> 1;
+    if (__ldg(o + mid) <= j) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(kBlock) k_mm_expand(MMExpandArgs a) {
+  __shared__ uint64_t s_q[2];
+  const uint64_t span = (uint64_t)kBlock * kExpandItems;
+  const uint64_t j0 = (uint64_t)blockIdx.x * span;
+  if (j0 >= a.T) return;
+  const uint64_t j1 = (j0 + span < a.T ? j0 + span : a.T) - 1;
+  if (threadIdx.x == 0) s_q[0] = upper_q(a.o, 0, a.Q - 1, j0);
+  if (threadIdx.x == 32) s_q[1] = upper_q(a.o, 0, a.Q - 1, j1);
+  __syncthreads();
+  const uint64_t qlo = s_q[0], qhi = s_q[1];
+#pragma unroll 2
+  for (int it = 0; it < kExpandItems; ++it) {
+    const uint64_t j = j0 + (uint64_t)it * kBlock + threadIdx.x;
+    if (j > j1) break;
+    const uint64_t q = upper_q(a.o, qlo, qhi, j);
+    const uint64_t t = j - __ldg(a.o + q);
+    const int32_t prow = __ldg(a.prow + q);
+    const int32_t brow = __ldg(a.rows + __ldg(a.off + __ldg(a.pid + q)) + t);
+#pragma unroll
+    for (int c = 0; c < kMaxCols; ++c)
+      if (c < a.nout) a.out[c][j] = __ldg(a.src[c] + (a.src_build[c] ? brow : prow));
+    if (a.psum_out) {
+      const uint64_t ps = a.psum_in ? __ldg(a.psum_in + prow) : term_sum(a.probe_terms, prow);
+      a.psum_out[j] = ps + term_sum(a.build_terms, brow);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- aggregate level
+__device__ __forceinline__ int64_t agg_find_or_insert(const Table& t, int32_t key,
+                                                      uint32_t* status) {
+  uint32_t b = table_bucket(key, t.bucket_mask);
+  const unsigned long long want = (1ull << 32) | (uint32_t)key;
+  for (uint32_t step = 0; step <= t.bucket_mask; ++step) {
+    unsigned long long* bk = t.slots + (uint64_t)b * 4;
+#pragma unroll 1
+    for (int s = 0; s < 4; ++s) {
+      unsigned long long v = ld_volatile_u64(reinterpret_cast<const uint64_t*>(bk + s));
+      if (v == 0) {
+        v = atomicCAS(bk + s, 0ull, want);
+        if (v == 0) return (int64_t)b * 4 + s;
+      }
+      if (v == want) return (int64_t)b * 4 + s;
+    }
+    b = (b + 1) & t.bucket_mask;
+  }
+  atomicOr(status, kErrTableFull);
+  return -1;
+}
+
+__global__ void __launch_bounds__(kBlock) k_agg_insert(AggInsertArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t first = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31);
+  for (int64_t w0 = first; w0 < a.n; w0 += stride) {
+    const int64_t row = w0 + lane;
+    const bool active = row < a.n;
+    int64_t s = -1;
+    uint64_t val = 0;
+    if (active) {
+      s = agg_find_or_insert(a.t, __ldcs(a.keys + row), a.status);
+      val = term_sum(a.terms, row);
+    }
+    // combine rows of the same key within the warp, then one atomic pair per key
+    const long long gk = (s >= 0) ? s : (-2 - lane);
+    const uint32_t group = __match_any_sync(0xffffffffu, gk);
+    uint64_t gsum = 0;
+    if (__any_sync(0xffffffffu, __popc(group) > 1)) {
+#pragma unroll 4
+      for (int l = 0; l < 32; ++l) {
+        const uint64_t x = __shfl_sync(0xffffffffu, val, l);
+        if ((group >> l) & 1u) gsum += x;
+      }
+    } else {
+      gsum = val;
+    }
+    if (s >= 0 && lane == __ffs(group) - 1) {
+      atomicAdd(a.cnt + s, (unsigned long long)__popc(group));
+      if (a.terms.n) atomicAdd(a.sum + s, (unsigned long long)gsum);
+    }
+  }
+}
+
+struct U128 {
+  uint64_t lo, hi;
+};
+__device__ __forceinline__ void add128(U128& x, uint64_t lo, uint64_t hi) {
+  const uint64_t nl = x.lo + lo;
+  x.hi += hi + (nl < x.lo ? 1ull : 0ull);
+  x.lo = nl;
+}
+
+__global__ void __launch_bounds__(kBlock) k_agg_probe(AggProbeArgs a) {
+  __shared__ uint64_t s_red[3][kBlock / 32];
+  U128 cnt = {0, 0};
+  uint64_t sum = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+    const int64_t s = table_find(a.t, __ldcs(a.keys + i));
+    if (s < 0) continue;
+    const uint64_t c = __ldg(a.cnt + s);
+    const uint64_t ps = a.psum_in ? __ldg(a.psum_in + i) : term_sum(a.probe_terms, i);
+    add128(cnt, c, 0);
+    sum += ps * c + __ldg(a.sum + s);
+  }
+  // block reduction of (count lo, count hi, sum)
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) {
+    const uint64_t lo = __shfl_xor_sync(0xffffffffu, cnt.lo, d);
+    const uint64_t hi = __shfl_xor_sync(0xffffffffu, cnt.hi, d);
+    add128(cnt, lo, hi);
+    sum += __shfl_xor_sync(0xffffffffu, sum, d);
+  }
+  if (lane == 0) {
+    s_red[0][warp] = cnt.lo;
+    s_red[1][warp] = cnt.hi;
+    s_red[2][warp] = sum;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    U128 c = {0, 0};
+    uint64_t sm = 0;
+    for (int w = 0; w < kBlock / 32; ++w) {
+      add128(c, s_red[0][w], s_red[1][w]);
+      sm += s_red[2][w];
+    }
+    const unsigned long long old = atomicAdd(a.result + 0, (unsigned long long)c.lo);
+    const uint64_t carry = (old + c.lo < old) ? 1ull : 0ull;
+    if (c.hi + carry) atomicAdd(a.result + 1, (unsigned long long)(c.hi + carry));
+    atomicAdd(a.result + 2, (unsigned long long)sm);
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_sum_terms(SumTermsArgs a) {
+  __shared__ uint64_t s_red[kBlock / 32];
+  uint64_t sum = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride)
+    sum += term_sum(a.terms, i);
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, d);
+  if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = sum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint64_t sm = 0;
+    for (int w = 0; w < kBlock / 32; ++w) sm += s_red[w];
+    atomicAdd(a.result + 2, (unsigned long long)sm);
+  }
+}
+
+int host_grid(int64_t work, int per_block, int cap) {
+  int64_t g = (work + per_block - 1) / per_block;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return (int)g;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- launchers
+void launch_bloom_build(const BloomBuildArgs& a, int64_t n_upper, int num_sms, cudaStream_t s) {
+  k_bloom_build<<<host_grid(n_upper, kBlock * 4, num_sms * 8), kBlock, 0, s>>>(a);
+}
+
+void launch_bloom_probe(const BloomProbeArgs& a, int num_sms, cudaStream_t s) {
+  k_bloom_probe<<<host_grid(a.n, kBlock * 4, num_sms * 8), kBlock, 0, s>>>(a);
+}
+
+void launch_sieve(const SieveArgs& a, int64_t n_upper, cudaStream_t s) {
+  k_sieve<<<host_grid(n_upper, kSieveTile, 1 << 30), kBlock, 0, s>>>(a);
+}
+
+void launch_scan_u32(const ScanArgs& a, int64_t n_upper, cudaStream_t s) {
+  k_scan_u32<<<host_grid(n_upper, kScanTile, 1 << 30), kBlock, 0, s>>>(a);
+}
+
+void launch_mm_insert(const MMInsertArgs& a, int num_sms, cudaStream_t s) {
+  k_mm_insert<<<host_grid(a.n, kBlock, num_sms * 8), kBlock, 0, s>>>(a);
+}
+
+void launch_mm_scatter(const MMScatterArgs& a, int num_sms, cudaStream_t s) {
+  k_mm_scatter<<<host_grid(a.n, kBlock, num_sms * 8), kBlock, 0, s>>>(a);
+}
+
+void launch_mm_probe(const MMProbeArgs& a, cudaStream_t s) {
+  k_mm_probe<<<host_grid(a.n, kProbeTile, 1 << 30), kBlock, 0, s>>>(a);
+}
+
+void launch_mm_expand(const MMExpandArgs& a, cudaStream_t s) {
+  const int64_t span = (int64_t)kBlock * kExpandItems;
+  k_mm_expand<<<host_grid((int64_t)a.T, (int)span, 1 << 30), kBlock, 0, s>>>(a);
+}
+
+void launch_agg_insert(const AggInsertArgs& a, int num_sms, cudaStream_t s) {
+  k_agg_insert<<<host_grid(a.n, kBlock, num_sms * 8), kBlock, 0, s>>>(a);
+}
+
+void launch_agg_probe(const AggProbeArgs& a, int num_sms, cudaStream_t s) {
+  k_agg_probe<<<host_grid(a.n, kBlock, num_sms * 8), kBlock, 0, s>>>(a);
+}
+
+void launch_sum_terms(const SumTermsArgs& a, int num_sms, cudaStream_t s) {
+  k_sum_terms<<<host_grid(a.n, kBlock, num_sms * 8), kBlock, 0, s>>>(a);
+}
+
+}  // namespace sj

@@ -1,0 +1,177 @@
+// Kernel argument blocks and host-side launchers of the sieved-join kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sj_device.cuh"
+
+namespace sj {
+
+constexpr int kMaxCols = 8;
+constexpr int kMaxTests = 5;   // one range predicate + up to four filters
+constexpr int kMaxTerms = 8;
+
+// ------------------------------------------------------------------ Bloom build
+struct BloomBuildArgs {
+  const int32_t* keys;
+  int64_t n_host;          // used when n_dev is null
+  const uint64_t* n_dev;   // device row count of a compacted relation, or null
+  uint64_t* hdr;           // hdr[0] = nblocks, hdr[1] = rows inserted (written)
+  uint32_t* words;         // zeroed, nblocks_cap * 8 words
+  uint64_t nblocks_cap;
+  uint32_t bits_per_key, k, layout;
+  uint64_t seed;
+};
+void launch_bloom_build(const BloomBuildArgs& a, int64_t n_upper, int num_sms, cudaStream_t s);
+
+struct BloomProbeArgs {
+  FilterView f;
+  const int32_t* keys;
+  int64_t n;
+  uint8_t* out;
+};
+void launch_bloom_probe(const BloomProbeArgs& a, int num_sms, cudaStream_t s);
+
+// ------------------------------------------------------------------ sieve
+// One test of a sieve step: a range predicate (lo <= v < hi) or a filter probe.
+struct SieveTest {
+  const int32_t* col;
+  int32_t is_pred;
+  int32_t lo, hi;
+  FilterView f;
+};
+
+struct SieveArgs {
+  const int32_t* in[kMaxCols];
+  int32_t* out[kMaxCols];
+  int32_t out_is_vec[kMaxCols];  // out column j is the first test's column
+  int nout;
+  int ntest;
+  SieveTest test[kMaxTests];
+  int64_t n_host;
+  const uint64_t* n_dev;
+  uint64_t* out_n;        // kept rows (written by the last tile)
+  uint64_t* out_n2;       // optional second copy (per-step statistics), or null
+  uint32_t* tile_counter; // zeroed
+  LookBack<1> lb;         // flags zeroed
+};
+// Tiles of 4096 rows: 256 threads x 4 vectors x 4 int32.
+constexpr int kSieveTile = kBlock * 16;
+void launch_sieve(const SieveArgs& a, int64_t n_upper, cudaStream_t s);
+
+// ------------------------------------------------------------------ scans
+struct ScanArgs {
+  const uint32_t* in;
+  uint64_t* out;          // exclusive prefix, uint64
+  int64_t n_host;
+  const uint32_t* n_dev;  // device count (uint32), or null
+  uint64_t* total;        // optional
+  uint32_t* tile_counter;
+  LookBack<1> lb;
+};
+constexpr int kScanTile = kBlock * 8;
+void launch_scan_u32(const ScanArgs& a, int64_t n_upper, cudaStream_t s);
+
+// ------------------------------------------------------------------ hash tables
+// Open addressing, linear probing over buckets of four 8-byte slots (one
+// 32-byte sector).  A slot is 0 when empty, else (tag << 32) | uint32(key).
+struct Table {
+  unsigned long long* slots;
+  uint32_t bucket_mask;  // nbuckets - 1, nbuckets a power of two
+};
+
+struct MMInsertArgs {       // multimap build, pass 1: distinct keys and per-row rank
+  const int32_t* keys;
+  int64_t n;
+  Table t;
+  uint32_t* nuniq;
+  uint32_t* cnt;            // [n] zeroed
+  uint32_t* rid;            // [n] row -> key id
+  uint32_t* rank;           // [n] row -> rank among rows of its key
+  uint32_t* status;
+};
+void launch_mm_insert(const MMInsertArgs& a, int num_sms, cudaStream_t s);
+
+struct MMScatterArgs {      // multimap build, pass 2: rows grouped by key id
+  const uint32_t* rid;
+  const uint32_t* rank;
+  const uint64_t* off;
+  int64_t n;
+  int32_t* rows;
+};
+void launch_mm_scatter(const MMScatterArgs& a, int num_sms, cudaStream_t s);
+
+struct MMProbeArgs {        // probe + compaction of matching probe rows
+  const int32_t* keys;
+  int64_t n;
+  Table t;
+  const uint32_t* cnt;
+  int32_t* prow;            // matching probe row
+  int32_t* pid;             // its key id
+  uint64_t* o;              // exclusive prefix of match counts
+  uint64_t* totals;         // [0] = matching rows, [1] = output tuples
+  uint32_t* tile_counter;
+  LookBack<2> lb;
+};
+constexpr int kProbeTile = kBlock * 8;
+void launch_mm_probe(const MMProbeArgs& a, cudaStream_t s);
+
+struct Terms {              // SUM terms read from one side's columns
+  const int32_t* col[kMaxTerms];     // int32 term, or low word of an int64 term
+  const int32_t* col_hi[kMaxTerms];  // high word of an int64 term, else null
+  int n;
+};
+
+struct MMExpandArgs {       // one output tuple per (matching probe row, build row)
+  uint64_t T;
+  uint64_t Q;
+  const uint64_t* o;
+  const int32_t* prow;
+  const int32_t* pid;
+  const uint64_t* off;
+  const int32_t* rows;
+  const int32_t* src[kMaxCols];  // source column of each output column
+  int32_t src_build[kMaxCols];   // 1 = indexed by build row, 0 = by probe row
+  int32_t* out[kMaxCols];
+  int nout;
+  const uint64_t* psum_in;       // null: use probe_terms
+  Terms probe_terms;
+  Terms build_terms;
+  uint64_t* psum_out;            // null: no SUM carried
+};
+constexpr int kExpandItems = 8;
+void launch_mm_expand(const MMExpandArgs& a, cudaStream_t s);
+
+struct AggInsertArgs {
+  const int32_t* keys;
+  int64_t n;
+  Table t;
+  Terms terms;
+  unsigned long long* cnt;  // [nslots] zeroed
+  unsigned long long* sum;  // [nslots] zeroed
+  uint32_t* status;
+};
+void launch_agg_insert(const AggInsertArgs& a, int num_sms, cudaStream_t s);
+
+struct AggProbeArgs {
+  const int32_t* keys;
+  int64_t n;
+  Table t;
+  const unsigned long long* cnt;
+  const unsigned long long* sum;
+  const uint64_t* psum_in;
+  Terms probe_terms;
+  unsigned long long* result;  // [0] count lo, [1] count hi, [2] sum; zeroed
+  uint32_t* status;
+};
+void launch_agg_probe(const AggProbeArgs& a, int num_sms, cudaStream_t s);
+
+struct SumTermsArgs {
+  int64_t n;
+  Terms terms;
+  unsigned long long* result;  // [2] += sum
+};
+void launch_sum_terms(const SumTermsArgs& a, int num_sms, cudaStream_t s);
+
+}  // namespace sj
