@@ -173,6 +173,43 @@ SJ_API sj_status sj_sieve(sj_ctx *ctx, sj_rel rel, int nprobe, const int *key_co
                    const sj_filter *filters, const sj_pred *pred, sj_rel *out,
                    int64_t *nrows_out);
 
+/*
+ * Allocation-free sieve step.  The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory where they sieve --
+ * code running inside a custom allocator or memory manager, or a runtime that
+ * only hands out buffers it reserved up front and forbids cudaMalloc on its
+ * hot path.  It needs no context, calls no cudaMalloc, cudaFree or other
+ * allocating routine, and does the same work as sj_sieve with one filter and
+ * no predicate: the rows of the relation (ncols device columns in_cols, nrows
+ * rows) whose column key_col passes the filter are written, in input order,
+ * to out_cols (ncols device columns with room for nrows rows each), and the
+ * kept-row count to the device uint64 *out_count.  The filter is given by its
+ * word array (nblocks * 8 uint32, the layout sj_filter_params describes; the
+ * words of a filter built by sj_build_filter are reported by sj_filter_info)
+ * and its params (k, layout and seed; bits_per_key is not used).  All
+ * pointers are device pointers, 16-byte aligned.  `status` is NULL or a
+ * device uint32 that receives SJ_ETIMEOUT-style bits (1 = a bounded wait gave
+ * up) and is not cleared by the call.  The work is enqueued on cuda_stream
+ * (NULL = legacy default stream) of the current device; nothing is
+ * synchronised.
+ *
+ * Its scratch is one fixed device array of about 640 KiB inside this library
+ * (held by every GPU that loads the library until the process exits), sized
+ * for SJ_NOALLOC_MAX_ROWS rows; larger relations are rejected with SJ_EINVAL.
+ * Every call shares that array and clears what must start at zero, so calls
+ * that overlap on the GPU (other streams, other host threads) race: serialise
+ * them.  The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  On failure *err (when err is not NULL) points to a
+ * static message.  Errors: SJ_EINVAL, SJ_ECUDA.
+ */
+#define SJ_NOALLOC_MAX_ROWS (1ll << 27)
+SJ_API sj_status sj_sieve_noalloc(void *cuda_stream, int ncols, const int32_t *const *in_cols,
+                                  int64_t nrows, int key_col, const uint32_t *filter_words,
+                                  uint64_t nblocks, const sj_filter_params *params,
+                                  int32_t *const *out_cols, uint64_t *out_count, uint32_t *status,
+                                  const char **err);
+
 /* ---------------------------------------------------------------- join path */
 
 /* Equality rel_a.col_a = rel_b.col_b. */

@@ -35,7 +35,7 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "out of device memory", 3: "hash ta
 EXPORTS = ["sj_create", "sj_destroy", "sj_sync", "sj_last_error", "sj_status_str", "sj_version",
            "sj_load_relation", "sj_rel_info", "sj_free_rel", "sj_build_filter", "sj_filter_info",
            "sj_filter_probe", "sj_free_filter", "sj_sieve", "sj_sieve_path", "sj_join",
-           "sj_prof_enable", "sj_prof_reset", "sj_prof_read", "sj_counters"]
+           "sj_prof_enable", "sj_prof_reset", "sj_prof_read", "sj_counters", "sj_sieve_noalloc"]
 
 
 class SieveJoinError(RuntimeError):
@@ -125,6 +125,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "sj_prof_read": [P, I, ctypes.POINTER(I64), ctypes.POINTER(ctypes.c_double),
                          ctypes.POINTER(ctypes.c_double)],
         "sj_counters": [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64)],
+        "sj_sieve_noalloc": [P, I, PP, I64, I, P, ctypes.c_uint64, ctypes.POINTER(FilterParams),
+                             PP, P, P, ctypes.POINTER(ctypes.c_char_p)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
