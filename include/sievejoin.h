@@ -114,20 +114,23 @@ SJ_API sj_status sj_free_rel(sj_ctx *ctx, sj_rel rel);
 
 /* ------------------------------------------------------------ Bloom filters */
 
-enum { SJ_BLOCKED256 = 0, SJ_CLASSIC = 1 };
+enum { SJ_REGBLOCKED32 = 0, SJ_BLOCKED256 = 1, SJ_CLASSIC = 2 };
 
 /*
  * Filter parameters.  The paper sizes Bloomjoin's filter at one bit per tuple
- * (Sec. 2.1 step 2) and leaves the hash family open (Sec. 1 cites Kirsch and
- * Mitzenmacher).  Here: h = fmix64(uint32(key) xor seed) (MurmurHash3's
- * finaliser); m = 256 * max(1, ceil(bits_per_key * n / 256)) bits for n
- * inserted rows.
- *   SJ_BLOCKED256: block b = ((h >> 32) * nblocks) >> 32; bits (h >> 8i) & 255,
- *                  i < k, inside the 256-bit block (eight uint32 words); k <= 4.
+ * (Sec. 2.1 step 2) and leaves the hash family and layout open (Sec. 1 cites
+ * Kirsch and Mitzenmacher).  Here: h = fmix64(uint32(key) xor seed)
+ * (MurmurHash3's finaliser); m = 256 * max(1, ceil(bits_per_key * n / 256))
+ * bits for n inserted rows, stored as m / 32 uint32 words; word w holds bits
+ * 32w..32w+31, least significant bit first.
+ *   SJ_REGBLOCKED32 (default): all k bits of a key in one 32-bit word,
+ *                  word = ((h >> 32) * (m / 32)) >> 32, bit i = (h >> 5i) & 31,
+ *                  k <= 6.  One load per probe, one atomicOr per insert.
+ *   SJ_BLOCKED256: block b = ((h >> 32) * (m / 256)) >> 32; bits (h >> 8i) & 255,
+ *                  i < k, inside that 256-bit block (eight words); k <= 4.
  *   SJ_CLASSIC:    bits (h1 + i*h2) mod m, h1 = h & 0xffffffff,
  *                  h2 = (h >> 32) | 1; k <= 8.
- * Word w of the filter holds bits 32w..32w+31, least significant bit first.
- * Defaults (a zeroed struct is read as): bits_per_key 8, k 3, BLOCKED256, seed 0.
+ * A zeroed struct reads as: bits_per_key 8, k 3, SJ_REGBLOCKED32, seed 0.
  */
 typedef struct {
     uint32_t bits_per_key;
@@ -193,7 +196,7 @@ SJ_API sj_status sj_sieve(sj_ctx *ctx, sj_rel rel, int nprobe, const int *key_co
  * (NULL = legacy default stream) of the current device; nothing is
  * synchronised.
  *
- * Its scratch is one fixed device array of about 640 KiB inside this library
+ * Its scratch is one fixed device array of about 256 KiB inside this library
  * (held by every GPU that loads the library until the process exits), sized
  * for SJ_NOALLOC_MAX_ROWS rows; larger relations are rejected with SJ_EINVAL.
  * Every call shares that array and clears what must start at zero, so calls

@@ -36,8 +36,9 @@ _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _SRC_PATH = os.path.join(_HERE, "sj_oracle.c")
 _lib = None
 
-BLOCKED256 = 0
-CLASSIC = 1
+REG32 = 0
+BLOCKED256 = 1
+CLASSIC = 2
 COUNT_SUM = 0
 MATERIALIZE = 1
 FWD_BWD = 0
@@ -120,6 +121,9 @@ def bloom_nblocks(n_inserted: int, bits_per_key: int) -> int:
 def bloom_positions(h: np.ndarray, nblocks: int, k: int, layout: int):
     """(word index, bit mask) arrays, one pair per hash function i < k.
 
+    REG32 (register-blocked): all k bits of a key fall in one 32-bit word,
+    word = ((h >> 32) * nwords) >> 32 with nwords = 8 * nblocks, and bit
+    i = (h >> 5i) & 31.
     BLOCKED256: the key's block is ((h >> 32) * nblocks) >> 32 and its bits are
     the bytes (h >> 8i) & 255 inside that 256-bit block (eight uint32 words).
     CLASSIC: bit g_i = (h1 + i*h2) mod m over the whole m = 256*nblocks bits,
@@ -127,7 +131,12 @@ def bloom_positions(h: np.ndarray, nblocks: int, k: int, layout: int):
     hashing of Kirsch and Mitzenmacher, cited in Sec. 1).
     """
     out = []
-    if layout == BLOCKED256:
+    if layout == REG32:
+        word = ((h >> _U64(32)) * _U64(8 * nblocks)) >> _U64(32)
+        for i in range(k):
+            bit = (h >> _U64(5 * i)) & _U64(31)
+            out.append((word.astype(np.int64), (_U64(1) << bit).astype(np.uint32)))
+    elif layout == BLOCKED256:
         blk = ((h >> _U64(32)) * _U64(nblocks)) >> _U64(32)
         for i in range(k):
             bit = (h >> _U64(8 * i)) & _U64(255)
@@ -146,7 +155,7 @@ def bloom_positions(h: np.ndarray, nblocks: int, k: int, layout: int):
 
 
 def bloom_build(keys: np.ndarray, bits_per_key: int = 8, k: int = 3,
-                layout: int = BLOCKED256, seed: int = 0) -> dict:
+                layout: int = REG32, seed: int = 0) -> dict:
     """Build a filter: set every hash position of every key (Sec. 2.1 step 1)."""
     keys = np.asarray(keys, dtype=np.int32)
     nblocks = bloom_nblocks(len(keys), bits_per_key)
@@ -243,7 +252,7 @@ def edge_col(edges, e, rel):
 
 
 def sieve_path(w: dict, passes: int = FWD_BWD, bits_per_key: int = 8, k: int = 3,
-               layout: int = BLOCKED256, seed: int = 0):
+               layout: int = REG32, seed: int = 0):
     """The pruning phase of Sec. 2.2 over a tree-shaped join.
 
     Predicates are applied first.  Pass 1 ("forward", R1 -> Rn for a chain

@@ -16,12 +16,12 @@ import os
 import numpy as np
 
 __all__ = ["Context", "Relation", "Filter", "SieveJoinError", "load_library", "LIB_PATH",
-           "BLOCKED256", "CLASSIC", "FWD_BWD", "BWD_ONLY", "NO_SIEVE", "COUNT_SUM",
+           "REGBLOCKED32", "BLOCKED256", "CLASSIC", "FWD_BWD", "BWD_ONLY", "NO_SIEVE", "COUNT_SUM",
            "MATERIALIZE", "KERNEL_KINDS"]
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libsievejoin.so")
 
-BLOCKED256, CLASSIC = 0, 1
+REGBLOCKED32, BLOCKED256, CLASSIC = 0, 1, 2
 FWD_BWD, BWD_ONLY, NO_SIEVE = 0, 1, 2
 COUNT_SUM, MATERIALIZE = 0, 1
 DEVICE_BORROW, DEVICE_COPY, HOST_COPY = 0, 1, 2
@@ -228,7 +228,7 @@ class Filter:
             pass
 
 
-def _params(bits_per_key=8, k=3, layout=BLOCKED256, seed=0) -> FilterParams:
+def _params(bits_per_key=8, k=3, layout=REGBLOCKED32, seed=0) -> FilterParams:
     return FilterParams(int(bits_per_key), int(k), int(layout), 0, int(seed) & ((1 << 64) - 1))
 
 
@@ -335,7 +335,7 @@ class Context:
 
     # --------------------------------------------------------------- filters
     def build_filter(self, rel: Relation, key_col: int, pred=None, bits_per_key=8, k=3,
-                     layout=BLOCKED256, seed=0) -> Filter:
+                     layout=REGBLOCKED32, seed=0) -> Filter:
         p = _params(bits_per_key, k, layout, seed)
         pr = _pred(pred)
         h = ctypes.c_void_p()
@@ -376,7 +376,7 @@ class Context:
         return path, (hs, es, ps)
 
     def sieve_path(self, rels, edges, preds=None, root=-1, passes=FWD_BWD, bits_per_key=8, k=3,
-                   layout=BLOCKED256, seed=0):
+                   layout=REGBLOCKED32, seed=0):
         """Pruning phase over a join tree.  Returns (sieved relations, stats)."""
         path, keep = self._path(rels, edges, preds, root)
         opts = SieveOpts(int(passes), 0, _params(bits_per_key, k, layout, seed))

@@ -52,6 +52,7 @@ struct sj_ctx {
   uint64_t* h_misc = nullptr;  // pinned
   uint8_t* scratch = nullptr;
   size_t scratch_bytes = 0;
+  uint32_t epoch = 0;  // look-back flag epoch of the last scan launch
   int64_t launches = 0;
   int64_t h2d_bytes = 0;
   int64_t d2h_bytes = 0;
@@ -203,12 +204,14 @@ sj_status sync_read(sj_ctx* c) {
 
 uint32_t* status_ptr(sj_ctx* c) { return reinterpret_cast<uint32_t*>(c->d_misc + kMiscStatus); }
 
-// Scratch for one look-back scan: tile counter, flags, aggregates, prefixes.
+// Scratch for one look-back scan: the tile ticket counter and NCH packed state
+// words per tile.  States carry a per-launch epoch and the kernel resets the
+// ticket counter, so the area is zeroed only when (re)allocated or when the
+// 16-bit epoch wraps.
 template <int NCH>
 sj_status scratch_for(sj_ctx* c, int64_t ntiles, uint32_t** counter, LookBack<NCH>* lb) {
   if (ntiles < 1) ntiles = 1;
-  const size_t flags_bytes = round_up((size_t)ntiles * 4);
-  const size_t need = kAlign + flags_bytes + 2 * (size_t)ntiles * NCH * 8;
+  const size_t need = kAlign + (size_t)ntiles * NCH * 8;
   if (need > c->scratch_bytes) {
     // the old scratch may still be used by enqueued work: stream-ordered free
     dfree(c, c->scratch, c->scratch_bytes);
@@ -216,13 +219,17 @@ sj_status scratch_for(sj_ctx* c, int64_t ntiles, uint32_t** counter, LookBack<NC
     c->scratch = static_cast<uint8_t*>(dalloc(c, nb));
     c->scratch_bytes = c->scratch ? nb : 0;
     if (!c->scratch) return fail(c, SJ_ENOMEM, "scratch allocation failed");
+    SJ_CUDA(c, cudaMemsetAsync(c->scratch, 0, nb, c->stream));
+    c->epoch = 0;
   }
-  SJ_CUDA(c, cudaMemsetAsync(c->scratch, 0, kAlign + flags_bytes, c->stream));
+  if (++c->epoch >= (1u << 16)) {
+    SJ_CUDA(c, cudaMemsetAsync(c->scratch, 0, c->scratch_bytes, c->stream));
+    c->epoch = 1;
+  }
   *counter = reinterpret_cast<uint32_t*>(c->scratch);
-  lb->flags = reinterpret_cast<uint32_t*>(c->scratch + kAlign);
-  lb->agg = reinterpret_cast<uint64_t*>(c->scratch + kAlign + flags_bytes);
-  lb->inc = lb->agg + (size_t)ntiles * NCH;
+  lb->st = reinterpret_cast<uint64_t*>(c->scratch + kAlign);
   lb->status = status_ptr(c);
+  lb->epoch = c->epoch;
   return SJ_OK;
 }
 
@@ -340,6 +347,8 @@ sj_filter_params norm_params(const sj_filter_params* p) {
 
 sj_status check_params(sj_ctx* c, const sj_filter_params& p) {
   if (p.layout > SJ_CLASSIC) return fail(c, SJ_EINVAL, "unknown filter layout");
+  if (p.layout == SJ_REGBLOCKED32 && p.k > 6)
+    return fail(c, SJ_EINVAL, "register-blocked filter needs k <= 6");
   if (p.layout == SJ_BLOCKED256 && p.k > 4) return fail(c, SJ_EINVAL, "blocked filter needs k <= 4");
   if (p.layout == SJ_CLASSIC && p.k > 8) return fail(c, SJ_EINVAL, "classic filter needs k <= 8");
   if (p.bits_per_key > 1024) return fail(c, SJ_EINVAL, "bits_per_key must be <= 1024");

@@ -40,9 +40,23 @@ struct FilterView {
   const uint32_t* words;
   const uint64_t* hdr;  // hdr[0] = nblocks, hdr[1] = rows inserted
   uint32_t k;
-  uint32_t layout;      // 0 = blocked 256-bit, 1 = classic
+  uint32_t layout;      // 0 = register-blocked 32-bit word, 1 = blocked 256-bit, 2 = classic
   uint64_t seed;
 };
+
+// Register-blocked layout: the word holding all k bits of a key and the mask
+// of those bits (bit i = (h >> 5i) & 31).  nwords = 8 * nblocks < 2^35; the
+// multiply-shift range reduction takes the high half of h.
+__device__ __forceinline__ uint64_t reg32_word(uint64_t h, uint64_t nwords) {
+  return ((h >> 32) * nwords) >> 32;
+}
+__device__ __forceinline__ uint32_t reg32_mask(uint32_t hlo, uint32_t k) {
+  uint32_t m = 0;
+#pragma unroll
+  for (uint32_t i = 0; i < 6; ++i)
+    if (i < k) m |= 1u << ((hlo >> (5 * i)) & 31u);
+  return m;
+}
 
 __device__ __forceinline__ bool bit_of4(uint64_t q0, uint64_t q1, uint64_t q2, uint64_t q3,
                                         uint32_t bit) {
@@ -59,6 +73,10 @@ __device__ __forceinline__ bool filter_contains(const FilterView& f, uint64_t nb
                                                 int32_t key) {
   const uint64_t h = key_hash(key, f.seed);
   if (f.layout == 0) {
+    const uint32_t m = reg32_mask((uint32_t)h, f.k);
+    return (__ldg(f.words + reg32_word(h, nblocks * 8)) & m) == m;
+  }
+  if (f.layout == 1) {
     const uint64_t blk = ((h >> 32) * nblocks) >> 32;
     const ulonglong2* p = reinterpret_cast<const ulonglong2*>(f.words + blk * 8);
     const ulonglong2 a = __ldg(p);
@@ -138,25 +156,54 @@ __device__ __forceinline__ Vec<NCH> block_exclusive_scan(Vec<NCH> x, Vec<NCH>* t
 }
 
 // ------------------------------------------------------------------ look-back
-// Tile states for a decoupled look-back scan (Merrill and Garland, 2016):
-// flag 0 = not ready, 1 = aggregate published, 2 = inclusive prefix published.
-// Values are written before their flag, with a fence in between.
+// Tile states for a decoupled look-back scan (Merrill and Garland, 2016).  Each
+// channel of a tile is ONE 64-bit word: epoch (16 bits) | state (2 bits) |
+// value (46 bits), state 0 = not ready, 1 = tile aggregate, 2 = inclusive
+// prefix.  Flag and value travel in one single-copy-atomic store, so neither
+// side needs a fence.  A word whose epoch differs from this launch's reads as
+// "not ready": the states need no clearing between launches as long as every
+// launch on the same scratch uses a new epoch (or the words are zeroed and
+// epoch 0 is used).  With two channels a reader retries until both words show
+// the same state.
+constexpr int kValueBits = 46;
+constexpr uint64_t kValueMask = (1ull << kValueBits) - 1;
+
 template <int NCH>
 struct LookBack {
-  uint32_t* flags;  // [ntiles], zeroed before the launch
-  uint64_t* agg;    // [ntiles * NCH]
-  uint64_t* inc;    // [ntiles * NCH]
+  uint64_t* st;      // [ntiles * NCH]
   uint32_t* status;
+  uint32_t epoch;    // < 2^16
 };
 
 template <int NCH>
-__device__ __forceinline__ void lb_publish(const LookBack<NCH>& lb, uint32_t tile, uint32_t flag,
+__device__ __forceinline__ void lb_publish(const LookBack<NCH>& lb, uint32_t tile, uint32_t state,
                                            const Vec<NCH>& v) {
-  uint64_t* dst = (flag == 2 ? lb.inc : lb.agg) + (uint64_t)tile * NCH;
+  const uint64_t tag = ((uint64_t)lb.epoch << 48) | ((uint64_t)state << kValueBits);
 #pragma unroll
-  for (int c = 0; c < NCH; ++c) st_volatile_u64(dst + c, v.v[c]);
-  __threadfence();
-  st_volatile_u32(lb.flags + tile, flag);
+  for (int c = 0; c < NCH; ++c)
+    st_volatile_u64(lb.st + (uint64_t)tile * NCH + c, tag | (v.v[c] & kValueMask));
+}
+
+// State of a packed word under this launch's epoch.
+template <int NCH>
+__device__ __forceinline__ uint32_t lb_state(const LookBack<NCH>& lb, uint64_t w) {
+  return (uint32_t)(w >> 48) == lb.epoch ? (uint32_t)(w >> kValueBits) & 3u : 0u;
+}
+
+// Read the NCH words of one tile; returns their common state (0 if not ready
+// or inconsistent) and the values.
+template <int NCH>
+__device__ __forceinline__ uint32_t lb_read(const LookBack<NCH>& lb, int64_t idx, Vec<NCH>* v) {
+  uint32_t s0 = 0;
+#pragma unroll
+  for (int c = 0; c < NCH; ++c) {
+    const uint64_t w = ld_volatile_u64(lb.st + (uint64_t)idx * NCH + c);
+    const uint32_t s = lb_state(lb, w);
+    if (c == 0) s0 = s;
+    else if (s != s0) s0 = 0;
+    v->v[c] = w & kValueMask;
+  }
+  return s0;
 }
 
 // Called by warp 0 of a tile > 0.  Returns the exclusive prefix of `tile`
@@ -177,22 +224,19 @@ __device__ __forceinline__ Vec<NCH> lb_exclusive(const LookBack<NCH>& lb, uint32
 #pragma unroll
     for (int c = 0; c < NCH; ++c) v.v[c] = 0;
     if (idx >= 0) {
-      f = ld_volatile_u32(lb.flags + idx);
+      f = lb_read(lb, idx, &v);
       uint32_t spins = 0, ns = 8;
       while (f == 0) {
         if (++spins > kSpinLimit) break;
         __nanosleep(ns);
         if (ns < 256) ns <<= 1;
-        f = ld_volatile_u32(lb.flags + idx);
+        f = lb_read(lb, idx, &v);
       }
       if (f == 0) {
         atomicOr(lb.status, kErrTimeout);
         f = 2;
-      } else {
-        __threadfence();
-        const uint64_t* src = (f == 2 ? lb.inc : lb.agg) + (uint64_t)idx * NCH;
 #pragma unroll
-        for (int c = 0; c < NCH; ++c) v.v[c] = ld_volatile_u64(src + c);
+        for (int c = 0; c < NCH; ++c) v.v[c] = 0;
       }
     }
     const uint32_t pmask = __ballot_sync(0xffffffffu, f == 2);
@@ -208,6 +252,43 @@ __device__ __forceinline__ Vec<NCH> lb_exclusive(const LookBack<NCH>& lb, uint32
     j -= 32;
   }
   return excl;
+}
+
+// 4-byte asynchronous global -> shared copy (cached in L1).  Landing probe
+// words in shared memory instead of registers lets one thread keep dozens of
+// filter reads in flight.
+__device__ __forceinline__ void cp_async4(uint32_t* smem_dst, const uint32_t* gsrc) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// One 32-byte filter block in a single request (256-bit vector load).  The
+// read-only variant is for filters no kernel writes while it runs; the
+// L1-cacheable variant is for the build, where a stale copy only costs a
+// redundant atomicOr.
+__device__ __forceinline__ void ld_block32_nc(const uint32_t* p, uint64_t& q0, uint64_t& q1,
+                                              uint64_t& q2, uint64_t& q3) {
+  asm("ld.global.nc.v4.u64 {%0, %1, %2, %3}, [%4];"
+      : "=l"(q0), "=l"(q1), "=l"(q2), "=l"(q3)
+      : "l"(p));
+}
+__device__ __forceinline__ void ld_block32_ca(const uint32_t* p, uint64_t& q0, uint64_t& q1,
+                                              uint64_t& q2, uint64_t& q3) {
+  asm volatile("ld.global.ca.v4.u64 {%0, %1, %2, %3}, [%4];"
+               : "=l"(q0), "=l"(q1), "=l"(q2), "=l"(q3)
+               : "l"(p));
+}
+
+// Draw this CTA's tile ticket.  The CTA that draws the last ticket of the grid
+// resets the counter, so the next launch on the same scratch starts at 0
+// without a memset (every ticket of this launch has been drawn by then).
+__device__ __forceinline__ uint32_t draw_ticket(uint32_t* counter) {
+  const uint32_t t = atomicAdd(counter, 1u);
+  if (t == gridDim.x - 1) atomicExch(counter, 0u);
+  return t;
 }
 
 }  // namespace sj

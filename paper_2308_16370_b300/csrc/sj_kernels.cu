@@ -50,29 +50,66 @@ __device__ __forceinline__ void or_bits(uint32_t* p, uint32_t mask) {
   if ((__ldcg(p) & mask) != mask) atomicOr(p, mask);
 }
 
-__device__ __forceinline__ void bloom_insert(const BloomBuildArgs& a, uint64_t nb, int32_t key) {
+__device__ __forceinline__ void bloom_insert_classic(const BloomBuildArgs& a, uint64_t nb,
+                                                     int32_t key) {
   const uint64_t h = key_hash(key, a.seed);
-  if (a.layout == 0) {
-    uint32_t* base = a.words + (((h >> 32) * nb) >> 32) * 8;
+  const uint64_t m = nb * 256ull;
+  const uint64_t h1 = h & 0xffffffffull;
+  const uint64_t h2 = (h >> 32) | 1ull;
+  for (uint32_t i = 0; i < a.k; ++i) {
+    const uint64_t g = (h1 + (uint64_t)i * h2) % m;
+    or_bits(a.words + (g >> 5), 1u << (g & 31));
+  }
+}
+
+// Blocked layout, four keys at a time: the four 32-byte blocks are loaded
+// first (L1-cacheable, so repeated hot keys hit L1 instead of one L2 slice),
+// then an atomicOr is issued only for bits that are still clear.  A stale L1
+// copy can only cause a redundant OR, never a lost bit.
+__device__ __forceinline__ void bloom_insert_blocked4(const BloomBuildArgs& a, uint64_t nb,
+                                                      const int32_t (&key)[4], uint32_t live) {
+  uint64_t h[4];
+  uint32_t* base[4];
+  uint64_t q[4][4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    h[j] = key_hash(key[j], a.seed);
+    base[j] = a.words + (((h[j] >> 32) * nb) >> 32) * 8;
+    ld_block32_ca(base[j], q[j][0], q[j][1], q[j][2], q[j][3]);
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    if (!((live >> j) & 1u)) continue;
 #pragma unroll
     for (uint32_t i = 0; i < 4; ++i) {
       if (i < a.k) {
-        const uint32_t bit = (uint32_t)(h >> (8 * i)) & 255u;
-        or_bits(base + (bit >> 5), 1u << (bit & 31));
+        const uint32_t bit = (uint32_t)(h[j] >> (8 * i)) & 255u;
+        if (!bit_of4(q[j][0], q[j][1], q[j][2], q[j][3], bit))
+          atomicOr(base[j] + (bit >> 5), 1u << (bit & 31));
       }
-    }
-  } else {
-    const uint64_t m = nb * 256ull;
-    const uint64_t h1 = h & 0xffffffffull;
-    const uint64_t h2 = (h >> 32) | 1ull;
-    for (uint32_t i = 0; i < a.k; ++i) {
-      const uint64_t g = (h1 + (uint64_t)i * h2) % m;
-      or_bits(a.words + (g >> 5), 1u << (g & 31));
     }
   }
 }
 
-__global__ void __launch_bounds__(kBlock) k_bloom_build(BloomBuildArgs a) {
+// Register-blocked layout, four keys at a time: load the four words first
+// (L1-cacheable), then one atomicOr per key whose bits are not all set yet.
+__device__ __forceinline__ void bloom_insert_reg4(const BloomBuildArgs& a, uint64_t nb,
+                                                  const int32_t (&key)[4], uint32_t live) {
+  uint32_t* p[4];
+  uint32_t m[4], cur[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const uint64_t h = key_hash(key[j], a.seed);
+    p[j] = a.words + reg32_word(h, nb * 8);
+    m[j] = reg32_mask((uint32_t)h, a.k);
+    cur[j] = __ldca(p[j]);
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+    if (((live >> j) & 1u) && (cur[j] & m[j]) != m[j]) atomicOr(p[j], m[j]);
+}
+
+__global__ void __launch_bounds__(kBlock, 3) k_bloom_build(BloomBuildArgs a) {
   const int64_t n = a.n_dev ? (int64_t)(*a.n_dev) : a.n_host;
   uint64_t nb = ((uint64_t)a.bits_per_key * (uint64_t)n + 255ull) / 256ull;
   if (nb < 1) nb = 1;
@@ -83,16 +120,38 @@ __global__ void __launch_bounds__(kBlock) k_bloom_build(BloomBuildArgs a) {
   }
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t nvec = n >> 2;
+  const int64_t nvec = (n + 3) >> 2;
   const int4* kv = reinterpret_cast<const int4*>(a.keys);
   for (int64_t i = gid; i < nvec; i += stride) {
-    const int4 v = __ldcs(kv + i);
-    bloom_insert(a, nb, v.x);
-    bloom_insert(a, nb, v.y);
-    bloom_insert(a, nb, v.z);
-    bloom_insert(a, nb, v.w);
+    int32_t k4[4];
+    uint32_t live = 0xfu;
+    if ((i << 2) + 4 <= n) {
+      const int4 v = __ldcs(kv + i);
+      k4[0] = v.x;
+      k4[1] = v.y;
+      k4[2] = v.z;
+      k4[3] = v.w;
+    } else {
+      live = 0;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        k4[e] = 0;
+        if ((i << 2) + e < n) {
+          k4[e] = __ldcs(a.keys + (i << 2) + e);
+          live |= 1u << e;
+        }
+      }
+    }
+    if (a.layout == 0) {
+      bloom_insert_reg4(a, nb, k4, live);
+    } else if (a.layout == 1) {
+      bloom_insert_blocked4(a, nb, k4, live);
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        if ((live >> e) & 1u) bloom_insert_classic(a, nb, k4[e]);
+    }
   }
-  for (int64_t r = (nvec << 2) + gid; r < n; r += stride) bloom_insert(a, nb, __ldcs(a.keys + r));
 }
 
 __global__ void __launch_bounds__(kBlock) k_bloom_probe(BloomProbeArgs a) {
@@ -103,16 +162,98 @@ __global__ void __launch_bounds__(kBlock) k_bloom_probe(BloomProbeArgs a) {
 }
 
 // ---------------------------------------------------------------- sieve
-__device__ __forceinline__ bool run_test(const SieveTest& t, uint64_t nb, int32_t v) {
-  return t.is_pred ? (v >= t.lo && v < t.hi) : filter_contains(t.f, nb, v);
+// Test NK keys against one filter or predicate; returns the passing subset
+// of `live`.  For the blocked layout all loads are issued before any bit is
+// tested, so one thread keeps up to 4 * NK filter-word loads in flight.
+// Tests of NK keys against one predicate or filter; each returns the passing
+// subset of `live`.  All filter loads of the NK keys are issued before any bit
+// is tested so they are in flight together; dead keys read word 0 (an L1 hit)
+// instead of branching.  One function per layout keeps register use per call
+// site to what that layout needs.
+template <int NK>
+__device__ __forceinline__ uint32_t test_pred(const SieveTest& t, const int32_t* key, uint32_t live) {
+  uint32_t pass = 0;
+#pragma unroll
+  for (int j = 0; j < NK; ++j) pass |= (key[j] >= t.lo && key[j] < t.hi) ? (1u << j) : 0u;
+  return pass & live;
 }
 
-__global__ void __launch_bounds__(kBlock) k_sieve(SieveArgs a) {
+template <int NK>
+__device__ __forceinline__ uint32_t test_reg32(const SieveTest& t, uint64_t nb, const int32_t* key,
+                                               uint32_t live) {
+  uint32_t hlo[NK], w[NK];
+#pragma unroll
+  for (int j = 0; j < NK; ++j) {
+    const uint64_t h = key_hash(key[j], t.f.seed);
+    hlo[j] = (uint32_t)h;
+    w[j] = __ldg(t.f.words + (((live >> j) & 1u) ? reg32_word(h, nb * 8) : 0));
+  }
+  uint32_t pass = 0;
+#pragma unroll
+  for (int j = 0; j < NK; ++j) {
+    const uint32_t m = reg32_mask(hlo[j], t.f.k);
+    pass |= ((w[j] & m) == m) ? (1u << j) : 0u;
+  }
+  return pass & live;
+}
+
+template <int NK>
+__device__ __forceinline__ uint32_t test_blocked(const SieveTest& t, uint64_t nb, const int32_t* key,
+                                                 uint32_t live) {
+  uint64_t h[NK];
+  uint64_t q[NK][4];
+#pragma unroll
+  for (int j = 0; j < NK; ++j) {
+    h[j] = key_hash(key[j], t.f.seed);
+    const uint32_t* base =
+        ((live >> j) & 1u) ? t.f.words + (((h[j] >> 32) * nb) >> 32) * 8 : t.f.words;
+    ld_block32_nc(base, q[j][0], q[j][1], q[j][2], q[j][3]);
+  }
+  uint32_t pass = 0;
+#pragma unroll
+  for (int j = 0; j < NK; ++j) {
+    bool ok = true;
+#pragma unroll
+    for (uint32_t i = 0; i < 4; ++i)
+      if (i < t.f.k)
+        ok &= bit_of4(q[j][0], q[j][1], q[j][2], q[j][3], (uint32_t)(h[j] >> (8 * i)) & 255u);
+    pass |= ok ? (1u << j) : 0u;
+  }
+  return pass & live;
+}
+
+__device__ __forceinline__ uint32_t test_classic(const SieveTest& t, uint64_t nb, const int32_t* key,
+                                                 uint32_t live) {
+  uint32_t pass = 0;
+#pragma unroll
+  for (int j = 0; j < 16; ++j)
+    if ((live >> j) & 1u) pass |= filter_contains(t.f, nb, key[j]) ? (1u << j) : 0u;
+  return pass;
+}
+
+// All 16 keys of a thread against one test.
+__device__ __forceinline__ uint32_t test16(const SieveTest& t, const int32_t* key, uint32_t live) {
+  if (t.is_pred) return test_pred<16>(t, key, live);
+  const uint64_t nb = __ldg(t.f.hdr);
+  if (t.f.layout == 0) {
+    return test_reg32<8>(t, nb, key, live & 0xffu) | (test_reg32<8>(t, nb, key + 8, live >> 8) << 8);
+  }
+  if (t.f.layout == 1) {
+    uint32_t pass = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      pass |= test_blocked<2>(t, nb, key + 2 * q, (live >> (2 * q)) & 0x3u) << (2 * q);
+    return pass;
+  }
+  return test_classic(t, nb, key, live);
+}
+
+__global__ void __launch_bounds__(kBlock, 4) k_sieve(SieveArgs a) {
   __shared__ uint32_t s_tile;
   __shared__ Vec<1> s_warp[kBlock / 32];
   __shared__ uint64_t s_prefix;
   const int tid = threadIdx.x;
-  if (tid == 0) s_tile = atomicAdd(a.tile_counter, 1u);
+  if (tid == 0) s_tile = draw_ticket(a.tile_counter);
   __syncthreads();
   const uint32_t tile = s_tile;
   const int64_t n = a.n_dev ? (int64_t)(*a.n_dev) : a.n_host;
@@ -155,27 +296,20 @@ __global__ void __launch_bounds__(kBlock) k_sieve(SieveArgs a) {
   }
 
   // 2. tests; later tests only load the rows still alive
-  if (a.ntest > 0) {
-    const uint64_t nb = a.test[0].is_pred ? 0 : __ldg(a.test[0].f.hdr);
-#pragma unroll
-    for (int i = 0; i < 16; ++i)
-      if ((alive >> i) & 1u)
-        if (!run_test(a.test[0], nb, key[i])) alive &= ~(1u << i);
-  }
+  if (a.ntest > 0) alive = test16(a.test[0], key, alive);
 #pragma unroll
   for (int t = 1; t < kMaxTests; ++t) {
-    if (t < a.ntest) {
-      const SieveTest& tt = a.test[t];
-      const uint64_t nb = tt.is_pred ? 0 : __ldg(tt.f.hdr);
+    if (t < a.ntest && alive) {
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
-        if ((alive >> i) & 1u) {
-          const int64_t row = base + (int64_t)((i >> 2) * kBlock + tid) * 4 + (i & 3);
-          if (!run_test(tt, nb, __ldcs(tt.col + row))) alive &= ~(1u << i);
-        }
+        const int64_t row = base + (int64_t)((i >> 2) * kBlock + tid) * 4 + (i & 3);
+        key[i] = ((alive >> i) & 1u) ? __ldcs(a.test[t].col + row) : 0;
       }
+      alive = test16(a.test[t], key, alive);
     }
   }
+  // the first test column's values are reloaded for output if tests overwrote them
+  const bool keys_valid = a.ntest <= 1;
 
   // 3. block scan of the survivor counts of the 4 chunks (16 bits each)
   Vec<1> cnt;
@@ -230,7 +364,7 @@ __global__ void __launch_bounds__(kBlock) k_sieve(SieveArgs a) {
     for (int j = 0; j < kMaxCols; ++j) {
       if (j >= a.nout) break;
       int32_t val[4];
-      if (a.out_is_vec[j]) {
+      if (a.out_is_vec[j] && keys_valid) {
 #pragma unroll
         for (int e = 0; e < 4; ++e) val[e] = key[4 * v + e];
       } else if (r0 + 4 <= n) {
@@ -258,7 +392,7 @@ __global__ void __launch_bounds__(kBlock) k_scan_u32(ScanArgs a) {
   __shared__ Vec<2> s_warp[kBlock / 32];
   __shared__ uint64_t s_prefix;
   const int tid = threadIdx.x;
-  if (tid == 0) s_tile = atomicAdd(a.tile_counter, 1u);
+  if (tid == 0) s_tile = draw_ticket(a.tile_counter);
   __syncthreads();
   const uint32_t tile = s_tile;
   const int64_t n = a.n_dev ? (int64_t)(*a.n_dev) : a.n_host;
@@ -419,7 +553,7 @@ __global__ void __launch_bounds__(kBlock) k_mm_probe(MMProbeArgs a) {
   __shared__ Vec<3> s_warp[kBlock / 32];
   __shared__ uint64_t s_prefix[2];
   const int tid = threadIdx.x;
-  if (tid == 0) s_tile = atomicAdd(a.tile_counter, 1u);
+  if (tid == 0) s_tile = draw_ticket(a.tile_counter);
   __syncthreads();
   const uint32_t tile = s_tile;
   const int64_t n = a.n;
@@ -696,7 +830,7 @@ int host_grid(int64_t work, int per_block, int cap) {
 
 // ---------------------------------------------------------------- launchers
 void launch_bloom_build(const BloomBuildArgs& a, int64_t n_upper, int num_sms, cudaStream_t s) {
-  k_bloom_build<<<host_grid(n_upper, kBlock * 4, num_sms * 8), kBlock, 0, s>>>(a);
+  k_bloom_build<<<host_grid(n_upper, kBlock * 4, num_sms * 3), kBlock, 0, s>>>(a);
 }
 
 void launch_bloom_probe(const BloomProbeArgs& a, int num_sms, cudaStream_t s) {

@@ -53,8 +53,8 @@ struct SieveArgs {
   const uint64_t* n_dev;
   uint64_t* out_n;        // kept rows (written by the last tile)
   uint64_t* out_n2;       // optional second copy (per-step statistics), or null
-  uint32_t* tile_counter; // zeroed
-  LookBack<1> lb;         // flags zeroed
+  uint32_t* tile_counter; // 0 at launch (reset by the kernel for the next one)
+  LookBack<1> lb;
 };
 // Tiles of 4096 rows: 256 threads x 4 vectors x 4 int32.
 constexpr int kSieveTile = kBlock * 16;

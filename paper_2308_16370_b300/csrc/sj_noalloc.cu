@@ -24,10 +24,8 @@ constexpr int64_t kMaxTiles = (kMaxRows + sj::kSieveTile - 1) / sj::kSieveTile;
 constexpr size_t kOffCounter = 0;    // uint32 tile ticket
 constexpr size_t kOffStatus = 64;    // uint32 status word (when the caller passes none)
 constexpr size_t kOffHdr = 128;      // uint64 nblocks, uint64 rows inserted
-constexpr size_t kOffFlags = 256;
-constexpr size_t kOffAgg = kOffFlags + 4 * kMaxTiles;
-constexpr size_t kOffInc = kOffAgg + 8 * kMaxTiles;
-constexpr size_t kScratchBytes = kOffInc + 8 * kMaxTiles;  // 640 KiB + 256 B
+constexpr size_t kOffStates = 256;   // one packed look-back word per tile
+constexpr size_t kScratchBytes = kOffStates + 8 * kMaxTiles;  // 256 KiB + 256 B
 
 static __device__ __align__(256) unsigned char g_sieve_scratch[kScratchBytes];
 
@@ -42,8 +40,8 @@ __global__ void k_noalloc_prepare(uint64_t nblocks, uint32_t ntiles, int clear_s
     hdr[0] = nblocks;
     hdr[1] = 0;
   }
-  uint32_t* flags = reinterpret_cast<uint32_t*>(g_sieve_scratch + kOffFlags);
-  for (uint32_t t = i; t < ntiles; t += gridDim.x * blockDim.x) flags[t] = 0u;
+  uint64_t* states = reinterpret_cast<uint64_t*>(g_sieve_scratch + kOffStates);
+  for (uint32_t t = i; t < ntiles; t += gridDim.x * blockDim.x) states[t] = 0ull;
 }
 
 // Host code must not use g_sieve_scratch as an address: in host code the name
@@ -86,7 +84,8 @@ extern "C" sj_status sj_sieve_noalloc(void* cuda_stream, int ncols, const int32_
     return bad("null argument");
   if (nblocks < 1 || nblocks >= (uint64_t(1) << 32)) return bad("nblocks must be in 1..2^32-1");
   if (params->layout > SJ_CLASSIC) return bad("unknown filter layout");
-  if ((params->layout == SJ_BLOCKED256 && (params->k < 1 || params->k > 4)) ||
+  if ((params->layout == SJ_REGBLOCKED32 && (params->k < 1 || params->k > 6)) ||
+      (params->layout == SJ_BLOCKED256 && (params->k < 1 || params->k > 4)) ||
       (params->layout == SJ_CLASSIC && (params->k < 1 || params->k > 8)))
     return bad("k out of range for the layout");
   if (reinterpret_cast<uintptr_t>(filter_words) & 15) return bad("filter words must be 16-byte aligned");
@@ -130,10 +129,9 @@ extern "C" sj_status sj_sieve_noalloc(void* cuda_stream, int ncols, const int32_
   a.out_n = out_count;
   a.out_n2 = nullptr;
   a.tile_counter = reinterpret_cast<uint32_t*>(base + kOffCounter);
-  a.lb.flags = reinterpret_cast<uint32_t*>(base + kOffFlags);
-  a.lb.agg = reinterpret_cast<uint64_t*>(base + kOffAgg);
-  a.lb.inc = reinterpret_cast<uint64_t*>(base + kOffInc);
+  a.lb.st = reinterpret_cast<uint64_t*>(base + kOffStates);
   a.lb.status = status ? status : reinterpret_cast<uint32_t*>(base + kOffStatus);
+  a.lb.epoch = 0;  // the states are zeroed by k_noalloc_prepare
   sj::launch_sieve(a, nrows, stream);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {

@@ -172,7 +172,7 @@ def test_fmix64_avalanche():
 
 
 # ------------------------------------------------------------------ Bloom filter
-@pytest.mark.parametrize("layout", [oracle.BLOCKED256, oracle.CLASSIC])
+@pytest.mark.parametrize("layout", [oracle.REG32, oracle.BLOCKED256, oracle.CLASSIC])
 @pytest.mark.parametrize("k", [1, 2, 3, 4])
 def test_bloom_no_false_negatives(layout, k):
     g = np.random.default_rng(k)
@@ -200,15 +200,24 @@ def test_bloom_classic_k1_is_a_hashed_bitset():
 
 
 def test_bloom_blocked_bits_stay_in_one_block():
-    """Each key sets 1..k bits, all inside one aligned 256-bit block."""
+    """Each key sets 1..k bits, all inside one aligned 256-bit block
+    (BLOCKED256) or one 32-bit word (REG32); the block / word index is
+    spread evenly (chi-square over 64 bins)."""
     g = np.random.default_rng(10)
-    for key in g.integers(-(1 << 31), (1 << 31) - 1, 50, dtype=np.int64).astype(np.int32):
-        f = oracle.bloom_build(np.array([key] * 1 + [], dtype=np.int32), 8 * 256 * 4, 3,
-                               oracle.BLOCKED256, seed=1)
-        nz = np.nonzero(f["words"])[0]
-        assert len(set(nz // 8)) == 1
-        bits = np.unpackbits(f["words"].view(np.uint8)).sum()
-        assert 1 <= bits <= 3
+    for layout, span in ((oracle.BLOCKED256, 8), (oracle.REG32, 1)):
+        for key in g.integers(-(1 << 31), (1 << 31) - 1, 50, dtype=np.int64).astype(np.int32):
+            f = oracle.bloom_build(np.array([key], dtype=np.int32), 8 * 256 * 4, 3, layout, seed=1)
+            nz = np.nonzero(f["words"])[0]
+            assert len(set(nz // span)) == 1
+            bits = np.unpackbits(f["words"].view(np.uint8)).sum()
+            assert 1 <= bits <= 3
+        keys = g.integers(-(1 << 31), (1 << 31) - 1, 64_000, dtype=np.int64).astype(np.int32)
+        nblocks = 64 if layout == oracle.BLOCKED256 else 8  # 64 blocks or 64 words
+        word, _ = oracle.bloom_positions(oracle.key_hash(keys, 3), nblocks, 1, layout)[0]
+        bins = np.bincount(word // span, minlength=64)
+        assert len(bins) == 64
+        chi2 = ((bins - 1000.0) ** 2 / 1000.0).sum()
+        assert chi2 < 120, chi2  # 63 degrees of freedom
 
 
 def _poisson_mix(lam, fn, jmax=None):
@@ -229,15 +238,16 @@ def test_eq3_expected_set_bits(k):
     g = np.random.default_rng(20 + k)
     D = 200_000
     keys = g.choice(1 << 30, D, replace=False).astype(np.int32)
-    for layout in (oracle.CLASSIC, oracle.BLOCKED256):
+    for layout in (oracle.CLASSIC, oracle.BLOCKED256, oracle.REG32):
         f = oracle.bloom_build(keys, 8, k, layout, seed=77)
         m = 256 * f["nblocks"]
         got = int(np.unpackbits(f["words"].view(np.uint8)).sum())
         if layout == oracle.CLASSIC:
             exp = m * (1 - math.exp(-k * D / m))
         else:
-            lam = D / f["nblocks"]
-            exp = f["nblocks"] * _poisson_mix(lam, lambda j: 256 * (1 - (1 - 1 / 256) ** (k * j)))
+            w = 256 if layout == oracle.BLOCKED256 else 32
+            nb = m // w
+            exp = nb * _poisson_mix(D / nb, lambda j: w * (1 - (1 - 1 / w) ** (k * j)))
         assert abs(got - exp) / exp < 0.01, (layout, got, exp)
 
 
@@ -250,15 +260,15 @@ def test_false_positive_rate(bpk, k):
     n = 100_000
     keys = g.choice(1 << 29, n, replace=False).astype(np.int32)
     neg = (g.choice(1 << 29, 1_000_000, replace=False) + (1 << 29)).astype(np.int32)
-    for layout in (oracle.CLASSIC, oracle.BLOCKED256):
+    for layout in (oracle.CLASSIC, oracle.BLOCKED256, oracle.REG32):
         f = oracle.bloom_build(keys, bpk, k, layout, seed=99)
         m = 256 * f["nblocks"]
         fpr = oracle.bloom_contains(f, neg).mean()
         if layout == oracle.CLASSIC:
             exp = (1 - math.exp(-k * n / m)) ** k
         else:
-            lam = n / f["nblocks"]
-            exp = _poisson_mix(lam, lambda j: (1 - (1 - 1 / 256) ** (k * j)) ** k)
+            w = 256 if layout == oracle.BLOCKED256 else 32
+            exp = _poisson_mix(n * w / m, lambda j: (1 - (1 - 1 / w) ** (k * j)) ** k)
         sig = math.sqrt(exp * (1 - exp) / len(neg))
         assert abs(fpr - exp) <= 4 * sig + 0.04 * exp, (layout, fpr, exp)
 
