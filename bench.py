@@ -56,7 +56,7 @@ WORKLOADS = {
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="sievejoin", choices=["sievejoin", "reference"])
     ap.add_argument("--workload", default="chain4_zipf", choices=sorted(WORKLOADS))
@@ -108,15 +108,20 @@ class ClockSampler:
         self.device = device
         self.proc = None
         self.lines = []
+        self.skip = 0
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.th = threading.Thread(target=self._read, daemon=True)
             self.th.start()
+            t0 = time.time()
+            while not self.lines and time.time() - t0 < 5.0:  # first sample before timing
+                time.sleep(0.02)
+            self.skip = len(self.lines)
         except Exception:
             self.proc = None
         return self
@@ -137,7 +142,7 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in self.lines[self.skip:]:
             p = [x.strip() for x in ln.split(",")]
             if len(p) < 8:
                 continue
@@ -205,18 +210,32 @@ def load_peaks():
     return 6400.0, "fallback"
 
 
+def kernel_source_digest() -> str:
+    """Digest of the kernel sources, to tell whether a profile is current."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("sj_kernels.cu", "sj_device.cuh", "sj_kernels.cuh"):
+        with open(os.path.join(ROOT, "paper_2308_16370_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def profiled_traffic(kernel: str, workload: str):
-    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if any."""
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, or None
+    if there is none or the kernels changed since it was captured."""
     p = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
     if not os.path.exists(p):
         return None
+    digest, traffic = None, None
     for ln in open(p):
+        if ln.startswith("kernel_source_sha256_16:"):
+            digest = ln.split(":", 1)[1].strip()
         if ln.startswith("traffic_bytes_per_launch:"):
             try:
-                return float(ln.split(":", 1)[1].strip())
+                traffic = float(ln.split(":", 1)[1].strip())
             except ValueError:
-                return None
-    return None
+                traffic = None
+    return traffic if digest == kernel_source_digest() else None
 
 
 # ----------------------------------------------------------------------------- CPU oracle
