@@ -63,6 +63,11 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving run")
+    ap.add_argument("--serve-queries", type=int, default=2000)
+    ap.add_argument("--serve-max-rows", type=int, default=5_000_000,
+                    help="largest pool relation (50M in the full-size serving workload)")
+    ap.add_argument("--serve-slots", type=int, default=8)
     return ap.parse_args()
 
 
@@ -238,6 +243,78 @@ def profiled_traffic(kernel: str, workload: str):
     return traffic if digest == kernel_source_digest() else None
 
 
+# ----------------------------------------------------------------------------- serving
+def serving_run(args, torch, sj):
+    """Poisson stream of chain queries (2-6 relations) over a resident pool of
+    40 relations with Zipf(0.8) keys over 2^22; first a closed loop (all
+    queries at once) for capacity, then an open loop at 0.7x that rate."""
+    from paper_2308_16370_b300 import inputs
+    import oracle
+    domain = 1 << 22
+    pool = inputs.serving_pool(nrel=40, min_rows=10_000, max_rows=args.serve_max_rows,
+                               domain=domain, seed=5)
+    dev = [[torch.from_numpy(c).cuda() for c in r] for r in pool]
+    sizes = [len(r[0]) for r in pool]
+    qs = inputs.serving_queries(sizes, args.serve_queries, domain=domain, seed=6)
+
+    def run(rate):
+        with sj.Server(nslots=args.serve_slots) as srv:
+            ids = [srv.add_relation(c) for c in dev]
+            warm = srv.submit([ids[r] for r in qs[0]["rels"]], qs[0]["edges"], qs[0]["preds"],
+                              qs[0]["sum"], qs[0]["root"])
+            srv.poll(1, wait_ms=60_000)
+            done = {}
+            g = np.random.default_rng(7)
+            # absolute Poisson arrival times, so host sleep overshoot does not lower the rate
+            arrive = np.cumsum(g.exponential(1.0 / rate, len(qs))) if rate else np.zeros(len(qs))
+            t0 = time.perf_counter()
+            tickets = []
+            for q, ta in zip(qs, arrive):
+                while True:
+                    lag = ta - (time.perf_counter() - t0)
+                    if lag <= 0:
+                        break
+                    time.sleep(lag if lag > 2e-3 else 0)
+                tickets.append(srv.submit([ids[r] for r in q["rels"]], q["edges"], q["preds"],
+                                          q["sum"], q["root"]))
+                for c in srv.poll(4096, 0):
+                    done[c["ticket"]] = c
+            while len(done) < len(tickets):
+                for c in srv.poll(4096, wait_ms=60_000):
+                    done[c["ticket"]] = c
+            span = time.perf_counter() - t0
+            st = srv.stats()
+        res = [done[t] for t in tickets]
+        return res, span, st
+
+    closed, span_c, _ = run(None)
+    qps_closed = len(qs) / span_c
+    lam = 0.7 * qps_closed
+    opened, span_o, st = run(lam)
+    lat = np.array([c["done_ms"] - c["submit_ms"] for c in opened])
+    same = all((a["count"], a["sum"]) == (b["count"], b["sum"]) for a, b in zip(closed, opened))
+    # oracle check on a bounded sample of the served queries
+    g = np.random.default_rng(8)
+    sample = [int(i) for i in g.choice(len(qs), min(8, len(qs)), replace=False)]
+    ok = 0
+    for i in sample:
+        q = qs[i]
+        w = {"rels": [pool[r] for r in q["rels"]], "edges": q["edges"], "preds": q["preds"],
+             "root": q["root"], "sum": q["sum"]}
+        e = oracle.agg_propagation(w)
+        ok += int((e["count"], e["sum"]) == (opened[i]["count"], opened[i]["sum"]))
+    return {"queries": len(qs), "slots": args.serve_slots, "arrival": "Poisson",
+            "rate_qps": lam, "qps": len(qs) / span_o, "closed_loop_qps": qps_closed,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "failed": int(sum(c["status"] != 0 for c in opened)),
+            "mix_equals_closed_loop": bool(same), "oracle_checked": len(sample),
+            "oracle_agree": ok, "filter_cache_hits": st["cache_hits"],
+            "filter_cache_misses": st["cache_misses"], "peak_concurrency": st["peak_concurrency"],
+            "pool": f"40 relations (x, y), log-uniform 1e4..{args.serve_max_rows:.0e} rows, "
+                    f"Zipf(0.8) keys over 2^22; chains of 2-6, predicate on the first relation "
+                    f"from 8 templates; COUNT and SUM"}
+
+
 # ----------------------------------------------------------------------------- CPU oracle
 def cpu_oracle_run(spec, reps_seconds=10.0, max_reps=20):
     """Time the CPU oracle (plain hash join) on the bounded sample."""
@@ -350,6 +427,10 @@ def main():
                "h2d_bytes_per_step": ec["h2d_bytes"] // (esteps + 1),
                "d2h_bytes_per_step": ec["d2h_bytes"] // (esteps + 1)}
 
+    serving = None
+    if not args.no_serve:
+        serving = serving_run(args, torch, sj)
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_oracle_run(spec)
@@ -385,6 +466,7 @@ def main():
         "kernels": {k: {"launches": v["launches"], "ms": v["ms"],
                         "GBps": (v["bytes"] / (v["ms"] / 1000.0) / 1e9) if v["ms"] > 0 else None}
                     for k, v in kstats.items() if v["launches"]},
+        "serving": serving,
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)

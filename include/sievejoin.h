@@ -242,10 +242,19 @@ enum {
     SJ_NO_SIEVE = 2  /* apply the predicates only */
 };
 
+/*
+ * leaf_filters (NULL, or one entry per relation) hands in reusable filters
+ * (Sec. 2.3): for a leaf v of the join tree, a non-NULL leaf_filters[v] is
+ * used in pass 1 instead of building the filter v sends to its parent.  It
+ * must have been built (sj_build_filter) over the column of v on that edge,
+ * from v's rows passing v's predicate, with the same filter parameters;
+ * entries of non-leaves are ignored.  Handed-in filters are not freed.
+ */
 typedef struct {
     int32_t passes;
     int32_t reserved;
     sj_filter_params filter;
+    const sj_filter *leaf_filters;
 } sj_sieve_opts;
 
 #define SJ_MAX_STEPS 32
@@ -311,6 +320,77 @@ typedef struct {
  */
 SJ_API sj_status sj_join(sj_ctx *ctx, const sj_path *path, const sj_rel *inputs, int mode, int nrefs,
                   const sj_colref *refs, sj_result *result);
+
+/* ---------------------------------------------------------------- serving */
+
+/*
+ * A query server over resident relations.  Queries (tree-shaped equi-joins
+ * over registered relations, returning COUNT(*) and SUM) are queued and run
+ * by `nslots` workers, each with its own context and CUDA stream, so queries
+ * that arrive while others run are admitted as soon as a slot and enough of
+ * the device-memory budget are free, and their kernels overlap on the GPU
+ * (continuous batching).  With cache_filters the server keeps the reusable
+ * leaf filters of pass 1 (Sec. 2.3: filters pre-built for one query serve
+ * later queries that contain the same relation, column and predicate), keyed
+ * by (relation, column, predicate), on the device until it is destroyed.
+ * Results are identical to running each query alone.
+ */
+typedef struct sj_server sj_server;
+
+typedef struct {
+    int32_t device;
+    int32_t nslots;          /* concurrent queries (workers); default 4 */
+    uint64_t hbm_budget;     /* bytes in-flight queries may use; 0 = half the free memory */
+    int32_t passes;          /* sieve schedule (SJ_FWD_BWD, ...) */
+    int32_t cache_filters;   /* 1 = reuse leaf filters across queries */
+    sj_filter_params filter; /* parameters of every filter the server builds */
+} sj_server_opts;
+
+typedef struct {
+    int32_t nrel;
+    int32_t root;                      /* as in sj_path; -1 = last relation */
+    int32_t rel[SJ_MAX_REL];           /* registered relation ids */
+    sj_edge edges[SJ_MAX_REL - 1];     /* rel_a / rel_b are positions 0..nrel-1 */
+    sj_pred preds[SJ_MAX_REL];         /* col < 0 for none */
+    int32_t nterms;
+    sj_colref terms[SJ_MAX_TERMS];     /* SUM terms; rel is a position */
+} sj_query;
+
+typedef struct {
+    uint64_t ticket;
+    sj_status status;
+    int32_t cache_hits;      /* leaf filters taken from the cache */
+    uint64_t count;
+    uint64_t sum;
+    double submit_ms;        /* host clock, ms since server creation */
+    double start_ms;         /* admitted to a slot */
+    double done_ms;          /* result on the host */
+} sj_completion;
+
+typedef struct {
+    uint64_t submitted, completed, failed;
+    uint64_t cache_hits, cache_misses, cached_filters;
+    uint64_t peak_inflight_bytes;
+    int32_t peak_concurrency;
+    int32_t reserved;
+} sj_server_stats;
+
+/* Create a server (starts its workers).  Errors: SJ_EINVAL, SJ_ECUDA, SJ_ENOMEM. */
+SJ_API sj_status sj_server_create(sj_server **out, const sj_server_opts *opts);
+/* Register a resident relation: `ncols` device columns of `nrows` rows,
+ * 16-byte aligned, borrowed (they must outlive the server).  Returns its id.
+ * Register relations before submitting the queries that use them; this call
+ * must not run concurrently with sj_server_submit. */
+SJ_API sj_status sj_server_add_relation(sj_server *srv, int ncols, const int32_t *const *dev_cols,
+                                        int64_t nrows, int32_t *rel_id);
+/* Queue a query (copied); returns at once with its ticket.  SJ_EINVAL if the
+ * query names an unknown relation or column or is not a tree. */
+SJ_API sj_status sj_server_submit(sj_server *srv, const sj_query *q, uint64_t *ticket);
+/* Take up to `max` finished queries; wait up to `wait_ms` for the first one. */
+SJ_API sj_status sj_server_poll(sj_server *srv, sj_completion *out, int max, int *n, int wait_ms);
+SJ_API sj_status sj_server_stats_get(sj_server *srv, sj_server_stats *stats);
+/* Finish queued queries, stop the workers and free cached filters. */
+SJ_API sj_status sj_server_destroy(sj_server *srv);
 
 /* ---------------------------------------------------------------- profiling */
 

@@ -35,7 +35,9 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "out of device memory", 3: "hash ta
 EXPORTS = ["sj_create", "sj_destroy", "sj_sync", "sj_last_error", "sj_status_str", "sj_version",
            "sj_load_relation", "sj_rel_info", "sj_free_rel", "sj_build_filter", "sj_filter_info",
            "sj_filter_probe", "sj_free_filter", "sj_sieve", "sj_sieve_path", "sj_join",
-           "sj_prof_enable", "sj_prof_reset", "sj_prof_read", "sj_counters", "sj_sieve_noalloc"]
+           "sj_prof_enable", "sj_prof_reset", "sj_prof_read", "sj_counters", "sj_sieve_noalloc",
+           "sj_server_create", "sj_server_add_relation", "sj_server_submit", "sj_server_poll",
+           "sj_server_stats_get", "sj_server_destroy"]
 
 
 class SieveJoinError(RuntimeError):
@@ -68,7 +70,7 @@ class Path(ctypes.Structure):
 
 class SieveOpts(ctypes.Structure):
     _fields_ = [("passes", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("filter", FilterParams)]
+                ("filter", FilterParams), ("leaf_filters", ctypes.POINTER(ctypes.c_void_p))]
 
 
 class StepStat(ctypes.Structure):
@@ -84,6 +86,34 @@ class SieveStats(ctypes.Structure):
 
 class ColRef(ctypes.Structure):
     _fields_ = [("rel", ctypes.c_int32), ("col", ctypes.c_int32), ("wide", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("nslots", ctypes.c_int32),
+                ("hbm_budget", ctypes.c_uint64), ("passes", ctypes.c_int32),
+                ("cache_filters", ctypes.c_int32), ("filter", FilterParams)]
+
+
+class Query(ctypes.Structure):
+    _fields_ = [("nrel", ctypes.c_int32), ("root", ctypes.c_int32),
+                ("rel", ctypes.c_int32 * MAX_REL), ("edges", Edge * (MAX_REL - 1)),
+                ("preds", Pred * MAX_REL), ("nterms", ctypes.c_int32),
+                ("terms", ColRef * MAX_TERMS)]
+
+
+class Completion(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_uint64), ("status", ctypes.c_int32),
+                ("cache_hits", ctypes.c_int32), ("count", ctypes.c_uint64),
+                ("sum", ctypes.c_uint64), ("submit_ms", ctypes.c_double),
+                ("start_ms", ctypes.c_double), ("done_ms", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("failed", ctypes.c_uint64), ("cache_hits", ctypes.c_uint64),
+                ("cache_misses", ctypes.c_uint64), ("cached_filters", ctypes.c_uint64),
+                ("peak_inflight_bytes", ctypes.c_uint64), ("peak_concurrency", ctypes.c_int32),
                 ("reserved", ctypes.c_int32)]
 
 
@@ -127,6 +157,12 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "sj_counters": [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64)],
         "sj_sieve_noalloc": [P, I, PP, I64, I, P, ctypes.c_uint64, ctypes.POINTER(FilterParams),
                              PP, P, P, ctypes.POINTER(ctypes.c_char_p)],
+        "sj_server_create": [PP, ctypes.POINTER(ServerOpts)],
+        "sj_server_add_relation": [P, I, PP, I64, ctypes.POINTER(ctypes.c_int32)],
+        "sj_server_submit": [P, ctypes.POINTER(Query), ctypes.POINTER(ctypes.c_uint64)],
+        "sj_server_poll": [P, ctypes.POINTER(Completion), I, ctypes.POINTER(I), I],
+        "sj_server_stats_get": [P, ctypes.POINTER(ServerStats)],
+        "sj_server_destroy": [P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -376,10 +412,18 @@ class Context:
         return path, (hs, es, ps)
 
     def sieve_path(self, rels, edges, preds=None, root=-1, passes=FWD_BWD, bits_per_key=8, k=3,
-                   layout=REGBLOCKED32, seed=0):
-        """Pruning phase over a join tree.  Returns (sieved relations, stats)."""
+                   layout=REGBLOCKED32, seed=0, leaf_filters=None):
+        """Pruning phase over a join tree.  Returns (sieved relations, stats).
+
+        ``leaf_filters``: None or one Filter / None per relation, reused for
+        leaves in pass 1 instead of being rebuilt (Sec. 2.3)."""
         path, keep = self._path(rels, edges, preds, root)
-        opts = SieveOpts(int(passes), 0, _params(bits_per_key, k, layout, seed))
+        lf = None
+        if leaf_filters is not None:
+            lf = (ctypes.c_void_p * len(rels))(*[(f.handle.value if f is not None else None)
+                                                 for f in leaf_filters])
+        opts = SieveOpts(int(passes), 0, _params(bits_per_key, k, layout, seed),
+                         ctypes.cast(lf, ctypes.POINTER(ctypes.c_void_p)) if lf is not None else None)
         outs = (ctypes.c_void_p * len(rels))()
         stats = SieveStats()
         self._check(self.lib.sj_sieve_path(self.ctx, ctypes.byref(path), ctypes.byref(opts), outs,
@@ -430,6 +474,91 @@ class Context:
         self._check(self.lib.sj_counters(self.ctx, ctypes.byref(n), ctypes.byref(h2d),
                                          ctypes.byref(d2h)))
         return {"launches": int(n.value), "h2d_bytes": int(h2d.value), "d2h_bytes": int(d2h.value)}
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Query server with continuous batching over `nslots` workers (one CUDA
+    stream each) and a device cache of reusable leaf filters (Sec. 2.3)."""
+
+    def __init__(self, device: int = 0, nslots: int = 4, hbm_budget: int = 0, passes=FWD_BWD,
+                 cache_filters: bool = True, bits_per_key=8, k=3, layout=REGBLOCKED32, seed=0):
+        torch = _torch()
+        if not torch.cuda.is_available():
+            raise RuntimeError("sievejoin needs a CUDA GPU; none is visible")
+        self.lib = load_library()
+        self.device = int(device)
+        self._keep = []
+        opts = ServerOpts(self.device, int(nslots), int(hbm_budget), int(passes),
+                          1 if cache_filters else 0, _params(bits_per_key, k, layout, seed))
+        h = ctypes.c_void_p()
+        st = self.lib.sj_server_create(ctypes.byref(h), ctypes.byref(opts))
+        if st != 0:
+            raise SieveJoinError(st, "sj_server_create failed")
+        self.srv = h
+
+    def add_relation(self, cols) -> int:
+        """Register device int32 columns (torch CUDA tensors, kept alive here)."""
+        ptrs = (ctypes.c_void_p * len(cols))(*[c.data_ptr() for c in cols])
+        rid = ctypes.c_int32()
+        st = self.lib.sj_server_add_relation(self.srv, len(cols), ptrs, len(cols[0]), ctypes.byref(rid))
+        if st != 0:
+            raise SieveJoinError(st, "sj_server_add_relation failed")
+        self._keep.append(cols)
+        return int(rid.value)
+
+    @staticmethod
+    def make_query(rel_ids, edges, preds=None, terms=(), root=-1) -> Query:
+        q = Query()
+        q.nrel = len(rel_ids)
+        q.root = int(root)
+        for i, r in enumerate(rel_ids):
+            q.rel[i] = int(r)
+            p = preds[i] if preds is not None else None
+            q.preds[i] = _pred(p) if p is not None else Pred(-1, 0, 0)
+        for e, ed in enumerate(edges):
+            q.edges[e] = Edge(*map(int, ed))
+        q.nterms = len(terms)
+        for t, tr in enumerate(terms):
+            q.terms[t] = ColRef(int(tr[0]), int(tr[1]), int(tr[2]) if len(tr) > 2 else 0, 0)
+        return q
+
+    def submit(self, rel_ids, edges, preds=None, terms=(), root=-1) -> int:
+        q = self.make_query(rel_ids, edges, preds, terms, root)
+        t = ctypes.c_uint64()
+        st = self.lib.sj_server_submit(self.srv, ctypes.byref(q), ctypes.byref(t))
+        if st != 0:
+            raise SieveJoinError(st, "sj_server_submit rejected the query")
+        return int(t.value)
+
+    def poll(self, max_n: int = 4096, wait_ms: int = 0):
+        buf = (Completion * max_n)()
+        n = ctypes.c_int()
+        self.lib.sj_server_poll(self.srv, buf, max_n, ctypes.byref(n), int(wait_ms))
+        return [{"ticket": int(c.ticket), "status": int(c.status), "count": int(c.count),
+                 "sum": int(c.sum), "cache_hits": int(c.cache_hits), "submit_ms": c.submit_ms,
+                 "start_ms": c.start_ms, "done_ms": c.done_ms} for c in buf[:n.value]]
+
+    def stats(self):
+        s = ServerStats()
+        self.lib.sj_server_stats_get(self.srv, ctypes.byref(s))
+        return {f: int(getattr(s, f)) for f, _ in ServerStats._fields_ if f != "reserved"}
+
+    def close(self):
+        if getattr(self, "srv", None):
+            self.lib.sj_server_destroy(self.srv)
+            self.srv = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
     def __del__(self):
         try:

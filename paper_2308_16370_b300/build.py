@@ -14,7 +14,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "libsievejoin.so")
-SOURCES = ["sj_kernels.cu", "sj_api.cu", "sj_noalloc.cu"]
+SOURCES = ["sj_kernels.cu", "sj_api.cu", "sj_noalloc.cu", "sj_server.cu"]
 HEADERS = ["sj_device.cuh", "sj_kernels.cuh"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-std=c++17", "-O3", "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo",

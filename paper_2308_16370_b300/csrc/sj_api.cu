@@ -786,8 +786,13 @@ sj_status sj_sieve_path(sj_ctx* c, const sj_path* path, const sj_sieve_opts* opt
           }
           st = do_step(v, 1, t);
         }
-        if (st == SJ_OK && tr.parent[v] >= 0)
-          st = do_build(v, edge_col(path->edges[tr.pedge[v]], v), &up[v]);
+        if (st == SJ_OK && tr.parent[v] >= 0) {
+          if (tr.children[v].empty() && o.leaf_filters && o.leaf_filters[v]) {
+            up[v] = o.leaf_filters[v];  // reused (Sec. 2.3); owned by the caller
+          } else {
+            st = do_build(v, edge_col(path->edges[tr.pedge[v]], v), &up[v]);
+          }
+        }
       }
     }
     for (int v : tr.pre) {

@@ -50,6 +50,21 @@ __device__ __forceinline__ void or_bits(uint32_t* p, uint32_t mask) {
   if ((__ldcg(p) & mask) != mask) atomicOr(p, mask);
 }
 
+// Per-CTA cache of key hashes this CTA has already inserted, so a key repeated
+// many times (Zipf-hot keys) issues about one atomicOr per CTA instead of one
+// per occurrence: a stale L1 copy of a hot word would otherwise keep every
+// occurrence on the slow same-address atomic path.  A slot holds a whole
+// 64-bit hash written in one store; a hash equal to 0 is never skipped, since
+// 0 also marks an empty slot.
+constexpr int kSeenSlots = 2048;
+
+__device__ __forceinline__ bool seen_before(unsigned long long* seen, uint64_t h) {
+  const uint32_t slot = (uint32_t)(h ^ (h >> 29)) & (kSeenSlots - 1);
+  if (h != 0 && seen[slot] == h) return true;
+  seen[slot] = h;
+  return false;
+}
+
 __device__ __forceinline__ void bloom_insert_classic(const BloomBuildArgs& a, uint64_t nb,
                                                      int32_t key) {
   const uint64_t h = key_hash(key, a.seed);
@@ -67,7 +82,8 @@ __device__ __forceinline__ void bloom_insert_classic(const BloomBuildArgs& a, ui
 // then an atomicOr is issued only for bits that are still clear.  A stale L1
 // copy can only cause a redundant OR, never a lost bit.
 __device__ __forceinline__ void bloom_insert_blocked4(const BloomBuildArgs& a, uint64_t nb,
-                                                      const int32_t (&key)[4], uint32_t live) {
+                                                      const int32_t (&key)[4], uint32_t live,
+                                                      unsigned long long* seen) {
   uint64_t h[4];
   uint32_t* base[4];
   uint64_t q[4][4];
@@ -80,6 +96,11 @@ __device__ __forceinline__ void bloom_insert_blocked4(const BloomBuildArgs& a, u
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     if (!((live >> j) & 1u)) continue;
+    bool all = true;
+#pragma unroll
+    for (uint32_t i = 0; i < 4; ++i)
+      if (i < a.k) all &= bit_of4(q[j][0], q[j][1], q[j][2], q[j][3], (uint32_t)(h[j] >> (8 * i)) & 255u);
+    if (all || seen_before(seen, h[j])) continue;
 #pragma unroll
     for (uint32_t i = 0; i < 4; ++i) {
       if (i < a.k) {
@@ -94,22 +115,28 @@ __device__ __forceinline__ void bloom_insert_blocked4(const BloomBuildArgs& a, u
 // Register-blocked layout, four keys at a time: load the four words first
 // (L1-cacheable), then one atomicOr per key whose bits are not all set yet.
 __device__ __forceinline__ void bloom_insert_reg4(const BloomBuildArgs& a, uint64_t nb,
-                                                  const int32_t (&key)[4], uint32_t live) {
+                                                  const int32_t (&key)[4], uint32_t live,
+                                                  unsigned long long* seen) {
   uint32_t* p[4];
   uint32_t m[4], cur[4];
+  uint64_t h[4];
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    const uint64_t h = key_hash(key[j], a.seed);
-    p[j] = a.words + reg32_word(h, nb * 8);
-    m[j] = reg32_mask((uint32_t)h, a.k);
+    h[j] = key_hash(key[j], a.seed);
+    p[j] = a.words + reg32_word(h[j], nb * 8);
+    m[j] = reg32_mask((uint32_t)h[j], a.k);
     cur[j] = __ldca(p[j]);
   }
 #pragma unroll
   for (int j = 0; j < 4; ++j)
-    if (((live >> j) & 1u) && (cur[j] & m[j]) != m[j]) atomicOr(p[j], m[j]);
+    if (((live >> j) & 1u) && (cur[j] & m[j]) != m[j] && !seen_before(seen, h[j]))
+      atomicOr(p[j], m[j]);
 }
 
 __global__ void __launch_bounds__(kBlock, 3) k_bloom_build(BloomBuildArgs a) {
+  __shared__ unsigned long long s_seen[kSeenSlots];
+  for (int i = threadIdx.x; i < kSeenSlots; i += blockDim.x) s_seen[i] = 0ull;
+  __syncthreads();
   const int64_t n = a.n_dev ? (int64_t)(*a.n_dev) : a.n_host;
   uint64_t nb = ((uint64_t)a.bits_per_key * (uint64_t)n + 255ull) / 256ull;
   if (nb < 1) nb = 1;
@@ -143,9 +170,9 @@ __global__ void __launch_bounds__(kBlock, 3) k_bloom_build(BloomBuildArgs a) {
       }
     }
     if (a.layout == 0) {
-      bloom_insert_reg4(a, nb, k4, live);
+      bloom_insert_reg4(a, nb, k4, live, s_seen);
     } else if (a.layout == 1) {
-      bloom_insert_blocked4(a, nb, k4, live);
+      bloom_insert_blocked4(a, nb, k4, live, s_seen);
     } else {
 #pragma unroll
       for (int e = 0; e < 4; ++e)

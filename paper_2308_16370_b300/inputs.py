@@ -166,3 +166,46 @@ def random_tree_join(g: np.random.Generator, nrel: int, nrows, domain: int,
     sums = [(int(g.integers(0, nrel)), int(g.integers(0, ncols)), 0) for _ in range(2)]
     return {"name": "random_tree", "rels": rels, "edges": edges, "preds": preds,
             "root": int(g.integers(0, nrel)), "sum": sums}
+
+
+def serving_pool(nrel: int = 40, min_rows: int = 10_000, max_rows: int = 50_000_000,
+                 domain: int = 1 << 22, s: float = 0.8, seed: int = 5):
+    """Resident relation pool for the serving workload: relations R_j(x, y)
+    with log-uniform sizes in [min_rows, max_rows] and Zipf(s) keys over the
+    domain, each column through its own seeded permutation."""
+    g = _rng(seed, 0)
+    sizes = np.exp(g.uniform(np.log(min_rows), np.log(max_rows), nrel)).astype(np.int64)
+    w = 1.0 / np.power(np.arange(1, domain + 1, dtype=np.float64), s)
+    cdf = np.cumsum(w)
+    cdf /= cdf[-1]
+    pool = []
+    for j in range(nrel):
+        cols = []
+        for c in range(2):
+            gj = _rng(seed, 1 + j, c)
+            perm = gj.permutation(domain)
+            r = np.minimum(np.searchsorted(cdf, gj.random(int(sizes[j])), side="right"), domain - 1)
+            cols.append(perm[r].astype(np.int32))
+        pool.append(cols)
+    return pool
+
+
+def serving_queries(pool_sizes, nq: int, domain: int = 1 << 22, min_len: int = 2,
+                    max_len: int = 6, ntemplates: int = 8, seed: int = 6):
+    """Chain queries over a pool: R_{i}.y = R_{i+1}.x for 2..6 distinct relations,
+    a range predicate on the first relation's x taken from `ntemplates` fixed
+    ranges (so filters of repeated (relation, column, predicate) are reusable),
+    COUNT(*) and SUM(first.x + last.y)."""
+    g = _rng(seed, 0)
+    npool = len(pool_sizes)
+    width = domain // 4
+    templates = [(int(t * (domain - width) // max(1, ntemplates - 1)),) for t in range(ntemplates)]
+    qs = []
+    for _ in range(nq):
+        n = int(g.integers(min_len, min(max_len, npool) + 1))
+        rels = [int(x) for x in g.choice(npool, n, replace=False)]
+        lo = templates[int(g.integers(0, ntemplates))][0]
+        preds = [(0, lo, lo + width)] + [None] * (n - 1)
+        qs.append({"rels": rels, "edges": chain_edges(n), "preds": preds, "root": n - 1,
+                   "sum": [(0, 0, 0), (n - 1, 1, 0)]})
+    return qs
