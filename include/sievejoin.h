@@ -321,6 +321,37 @@ typedef struct {
 SJ_API sj_status sj_join(sj_ctx *ctx, const sj_path *path, const sj_rel *inputs, int mode, int nrefs,
                   const sj_colref *refs, sj_result *result);
 
+/* ------------------------------------------------------------ cyclic query */
+
+typedef struct {
+    int64_t edges_in;        /* rows of the edge relation */
+    int64_t edges_sieved;    /* edges left after the pruning rounds */
+    uint64_t candidates;     /* closing pairs looked up */
+    uint64_t filter_passed;  /* of those, passed by the closing-pair filter */
+    uint64_t triangles;      /* sum of counts */
+} sj_tri_stats;
+
+/*
+ * Cyclic triangle query E(a,b) |x| E(b,c) |x| E(c,a) over a directed edge
+ * relation (columns 0 = source, 1 = target; distinct edges, no self-loops),
+ * answered as nsub subqueries in one launch: counts[i] = number of ordered
+ * (a, b, c) with a->b, b->c, c->a and cuts[i] <= a < cuts[i+1] (a below
+ * cuts[0] counts in subquery 0, at or above cuts[nsub] in subquery nsub-1).
+ * Pruning (Sec. 2.2) runs `sieve_rounds` rounds (default 2 when < 0): filters
+ * over the sources and targets keep the edges whose target has an out-edge
+ * and whose source has an in-edge.  Enumeration follows Sec. 2.3's cyclic
+ * case: the filter of the closing condition -- here over the packed pair
+ * (c, a) -- is rebuilt on the fly from the pruned edges and screens every
+ * wedge before an exact pair-set lookup; each wedge is walked from the
+ * shorter of out(b) and in(a).  The pair filter uses the register-blocked
+ * layout with `params`' bits_per_key, k (<= 6) and seed (NULL = defaults).
+ * 1 <= nsub <= 256; `cuts` (nsub + 1 increasing values) and `counts` are host
+ * arrays.  Synchronises.  Errors: SJ_EINVAL, SJ_ENOMEM, SJ_ETABLEFULL, SJ_ECUDA.
+ */
+SJ_API sj_status sj_triangles(sj_ctx *ctx, sj_rel edges, int nsub, const int32_t *cuts,
+                              int sieve_rounds, const sj_filter_params *params, uint64_t *counts,
+                              sj_tri_stats *stats);
+
 /* ---------------------------------------------------------------- serving */
 
 /*

@@ -499,3 +499,57 @@ def semijoin_reduction(w: dict, rels=None):
         rows = np.unique(res["cols"][i]) if res["count"] else np.zeros(0, dtype=np.int32)
         keep.append([np.asarray(c)[rows] for c in rels[i]])
     return keep
+
+
+def triangle_counts(src, dst, cuts):
+    """Cyclic triangle query E(a,b) |x| E(b,c) |x| E(c,a) (Sec. 2.3 cyclic joins):
+    ordered (a, b, c) with edges a->b, b->c and c->a, counted per subquery
+    cuts[i] <= a < cuts[i+1].  Plain definition: a binary hash join E |x| E on
+    b gives every wedge (a, b, c); a wedge closes when (c, a) is an edge.
+    Returns an int array of per-subquery counts."""
+    lib = _load()
+    src = np.ascontiguousarray(src, dtype=np.int32)
+    dst = np.ascontiguousarray(dst, dtype=np.int32)
+    total = lib.orc_join_pairs_count(_ptr(dst), len(dst), _ptr(src), len(src))
+    if total < 0:
+        raise MemoryError("oracle join")
+    pi = np.empty(total, dtype=np.int64)  # wedge: edge pi = (a, b), edge pj = (b, c)
+    pj = np.empty(total, dtype=np.int64)
+    if lib.orc_join_pairs_fill(_ptr(dst), len(dst), _ptr(src), len(src), _ptr(pi), _ptr(pj)):
+        raise MemoryError("oracle join")
+    a = src[pi].astype(np.int64)
+    c = dst[pj].astype(np.int64)
+    edges = np.sort((src.astype(np.int64) << 32) | dst.astype(np.int64))
+    probe = (c << 32) | a
+    pos = np.minimum(np.searchsorted(edges, probe), max(len(edges) - 1, 0))
+    closes = edges[pos] == probe if len(edges) else np.zeros(len(probe), dtype=bool)
+    sub = np.searchsorted(np.asarray(cuts, dtype=np.int64), a[closes], side="right") - 1
+    return np.bincount(sub, minlength=len(cuts) - 1).astype(np.int64)
+
+
+def triangle_counts_for(src, dst, verts):
+    """Ordered triangle counts restricted to a in `verts` (one count per vertex),
+    by the same plain definition as triangle_counts: the wedges (a, b, c) from
+    the edges leaving a, closed when (c, a) is an edge (membership by binary
+    search in the sorted edge keys)."""
+    src = np.asarray(src, dtype=np.int64)
+    dst = np.asarray(dst, dtype=np.int64)
+    edges = np.sort((src << 32) | dst)
+    order = np.argsort(src, kind="stable")
+    s_sorted = src[order]
+
+    def is_edge(keys):
+        i = np.minimum(np.searchsorted(edges, keys), len(edges) - 1)
+        return edges[i] == keys
+
+    out = []
+    for a in verts:
+        lo, hi = np.searchsorted(s_sorted, [a, a + 1])
+        bs = dst[order[lo:hi]]
+        total = 0
+        for b in bs:
+            l2, h2 = np.searchsorted(s_sorted, [b, b + 1])
+            cs = dst[order[l2:h2]]
+            total += int(is_edge((cs << 32) | a).sum())
+        out.append(total)
+    return np.array(out, dtype=np.int64)

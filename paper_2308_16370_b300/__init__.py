@@ -37,7 +37,7 @@ EXPORTS = ["sj_create", "sj_destroy", "sj_sync", "sj_last_error", "sj_status_str
            "sj_filter_probe", "sj_free_filter", "sj_sieve", "sj_sieve_path", "sj_join",
            "sj_prof_enable", "sj_prof_reset", "sj_prof_read", "sj_counters", "sj_sieve_noalloc",
            "sj_server_create", "sj_server_add_relation", "sj_server_submit", "sj_server_poll",
-           "sj_server_stats_get", "sj_server_destroy"]
+           "sj_server_stats_get", "sj_server_destroy", "sj_triangles"]
 
 
 class SieveJoinError(RuntimeError):
@@ -117,6 +117,12 @@ class ServerStats(ctypes.Structure):
                 ("reserved", ctypes.c_int32)]
 
 
+class TriStats(ctypes.Structure):
+    _fields_ = [("edges_in", ctypes.c_int64), ("edges_sieved", ctypes.c_int64),
+                ("candidates", ctypes.c_uint64), ("filter_passed", ctypes.c_uint64),
+                ("triangles", ctypes.c_uint64)]
+
+
 class Result(ctypes.Structure):
     _fields_ = [("count", ctypes.c_uint64), ("sum", ctypes.c_uint64),
                 ("intermediate", ctypes.c_uint64), ("rows", ctypes.c_void_p)]
@@ -163,6 +169,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "sj_server_poll": [P, ctypes.POINTER(Completion), I, ctypes.POINTER(I), I],
         "sj_server_stats_get": [P, ctypes.POINTER(ServerStats)],
         "sj_server_destroy": [P],
+        "sj_triangles": [P, P, I, P, I, ctypes.POINTER(FilterParams), P, ctypes.POINTER(TriStats)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -451,6 +458,21 @@ class Context:
         if res.rows:
             out["rows"] = Relation(self, res.rows)
         return out
+
+    # --------------------------------------------------------------- cyclic query
+    def triangles(self, edges: Relation, cuts, sieve_rounds: int = -1, bits_per_key=8, k=3, seed=0):
+        """Per-subquery ordered triangle counts of the directed edge relation
+        (cols: source, target) for a in [cuts[i], cuts[i+1]).  Returns
+        (counts as a numpy uint64 array, stats dict)."""
+        cuts = np.ascontiguousarray(cuts, dtype=np.int32)
+        nsub = len(cuts) - 1
+        counts = np.zeros(nsub, dtype=np.uint64)
+        st = TriStats()
+        p = _params(bits_per_key, k, REGBLOCKED32, seed)
+        self._check(self.lib.sj_triangles(self.ctx, edges.handle, nsub, cuts.ctypes.data,
+                                          int(sieve_rounds), ctypes.byref(p), counts.ctypes.data,
+                                          ctypes.byref(st)))
+        return counts, {f: int(getattr(st, f)) for f, _ in TriStats._fields_}
 
     # --------------------------------------------------------------- profiling
     def prof_enable(self, on: bool = True):

@@ -1356,3 +1356,188 @@ sj_status sj_counters(sj_ctx* c, int64_t* launches, int64_t* h2d_bytes, int64_t*
 }
 
 }  // extern "C"
+
+// ======================================================================== cyclic query
+namespace {
+
+// Multimap of row ids keyed by `keys` (the same build as a join level):
+// distinct keys get dense ids, rows are grouped by key id.
+sj_status build_adjacency(sj_ctx* c, Temps& tmp, const int32_t* keys, int64_t n, Adjacency* g) {
+  sj_status st = SJ_OK;
+  Table2 tb;
+  SJ_TRY(make_table(c, tmp, n, &tb));
+  uint32_t* cnt = tmp.get<uint32_t>(n, &st);
+  uint32_t* rid = tmp.get<uint32_t>(n, &st);
+  uint32_t* rank = tmp.get<uint32_t>(n, &st);
+  uint64_t* off = tmp.get<uint64_t>(n, &st);
+  int32_t* rows = tmp.get<int32_t>(n, &st);
+  if (st != SJ_OK) return fail(c, st, "adjacency allocation failed");
+  SJ_CUDA(c, cudaMemsetAsync(cnt, 0, (size_t)n * 4, c->stream));
+  SJ_CUDA(c, cudaMemsetAsync(c->d_misc + kMiscNuniq, 0, 8, c->stream));
+  uint32_t* nuniq = reinterpret_cast<uint32_t*>(c->d_misc + kMiscNuniq);
+  MMInsertArgs mi{keys, n, tb.t, nuniq, cnt, rid, rank, status_ptr(c)};
+  {
+    Launch L(c, SJ_K_HT_BUILD, 12.0 * (double)n);
+    launch_mm_insert(mi, c->num_sms, c->stream);
+  }
+  SJ_TRY(check_launch(c, "k_mm_insert"));
+  ScanArgs sa;
+  sa.in = cnt;
+  sa.out = off;
+  sa.n_host = 0;
+  sa.n_dev = nuniq;
+  sa.total = nullptr;
+  SJ_TRY(scratch_for<1>(c, (n + kScanTile - 1) / kScanTile, &sa.tile_counter, &sa.lb));
+  {
+    Launch L(c, SJ_K_HT_BUILD, 12.0 * (double)n);
+    launch_scan_u32(sa, n, c->stream);
+  }
+  SJ_TRY(check_launch(c, "k_scan_u32"));
+  MMScatterArgs ms{rid, rank, off, n, rows};
+  {
+    Launch L(c, SJ_K_HT_BUILD, 20.0 * (double)n);
+    launch_mm_scatter(ms, c->num_sms, c->stream);
+  }
+  SJ_TRY(check_launch(c, "k_mm_scatter"));
+  g->t = tb.t;
+  g->cnt = cnt;
+  g->off = off;
+  g->rows = rows;
+  return SJ_OK;
+}
+
+}  // namespace
+
+extern "C" sj_status sj_triangles(sj_ctx* c, sj_rel edges, int nsub, const int32_t* cuts,
+                                  int sieve_rounds, const sj_filter_params* params,
+                                  uint64_t* counts, sj_tri_stats* stats) {
+  if (!c || !edges || !cuts || !counts) return fail(c, SJ_EINVAL, "null argument");
+  if (edges->ncols < 2 || edges->nrows < 0) return fail(c, SJ_EINVAL, "edges need 2 columns");
+  if (nsub < 1 || nsub > 256) return fail(c, SJ_EINVAL, "nsub must be in 1..256");
+  for (int i = 0; i < nsub; ++i)
+    if (cuts[i + 1] <= cuts[i]) return fail(c, SJ_EINVAL, "cuts must increase");
+  sj_filter_params fp = norm_params(params);
+  fp.layout = SJ_REGBLOCKED32;
+  SJ_TRY(check_params(c, fp));
+  if (sieve_rounds < 0) sieve_rounds = 2;
+  if (sieve_rounds > 8) return fail(c, SJ_EINVAL, "sieve_rounds must be <= 8");
+
+  // ---- pruning: keep (a, b) with b among the sources and a among the targets
+  const size_t p0 = c->prof.size();
+  sj_rel cur = nullptr;
+  const sj_rel_s* E = edges;
+  int slot_in = -1;
+  for (int r = 0; r < sieve_rounds; ++r) {
+    sj_filter fs = nullptr, fd = nullptr;
+    sj_status st = build_filter_nosync(c, E, 0, fp, slot_in, &fs);
+    if (st == SJ_OK) st = build_filter_nosync(c, E, 1, fp, slot_in, &fd);
+    sj_rel nx = nullptr;
+    if (st == SJ_OK) {
+      std::vector<TestSpec> t{{1, false, 0, 0, fs}, {0, false, 0, 0, fd}};
+      st = sieve_step_timed(c, E, t, r, slot_in, &nx);
+    }
+    free_filter(c, fs);
+    free_filter(c, fd);
+    if (st != SJ_OK) {
+      free_rel(c, cur);
+      return st;
+    }
+    free_rel(c, cur);
+    cur = nx;
+    E = cur;
+    slot_in = r;
+  }
+  sj_status st = sync_read(c);
+  if (st != SJ_OK) {
+    free_rel(c, cur);
+    return st;
+  }
+  prof_resolve(c, p0);
+  const int64_t ne = slot_in >= 0 ? (int64_t)c->h_misc[kMiscSteps + slot_in] : edges->nrows;
+  if (cur) cur->nrows = ne;
+  struct RelGuard {
+    sj_ctx* c;
+    sj_rel r;
+    ~RelGuard() { free_rel(c, r); }
+  } guard{c, cur};
+  for (int i = 0; i < nsub; ++i) counts[i] = 0;
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    stats->edges_in = edges->nrows;
+    stats->edges_sieved = ne;
+  }
+  if (ne == 0) return SJ_OK;
+
+  Temps tmp(c);
+  Adjacency out{}, in{};
+  SJ_TRY(build_adjacency(c, tmp, E->cols[0], ne, &out));
+  SJ_TRY(build_adjacency(c, tmp, E->cols[1], ne, &in));
+
+  // closing-pair filter, rebuilt from the pruned edges (Sec. 2.3)
+  uint64_t nb = ((uint64_t)fp.bits_per_key * (uint64_t)ne + 255) / 256;
+  if (nb < 1) nb = 1;
+  uint8_t* fmem = tmp.get<uint8_t>(kAlign + nb * 32, &st);
+  if (!fmem) return fail(c, st, "pair filter allocation failed");
+  SJ_CUDA(c, cudaMemsetAsync(fmem, 0, kAlign + nb * 32, c->stream));
+  PairFilterBuildArgs pf{E->cols[0], E->cols[1], ne, reinterpret_cast<uint64_t*>(fmem),
+                         reinterpret_cast<uint32_t*>(fmem + kAlign), nb, fp.k, fp.seed};
+  {
+    Launch L(c, SJ_K_BLOOM_BUILD, (8.0 + fp.bits_per_key / 8.0) * (double)ne);
+    launch_pair_filter_build(pf, c->num_sms, c->stream);
+  }
+  SJ_TRY(check_launch(c, "k_pair_filter_build"));
+
+  // exact pair set
+  Table2 ps;
+  SJ_TRY(make_table(c, tmp, ne, &ps));
+  PairSetArgs pa{E->cols[0], E->cols[1], ne, ps.t, status_ptr(c)};
+  {
+    Launch L(c, SJ_K_HT_BUILD, 16.0 * (double)ne);
+    launch_pairset_insert(pa, c->num_sms, c->stream);
+  }
+  SJ_TRY(check_launch(c, "k_pairset_insert"));
+
+  int32_t* dcuts = tmp.get<int32_t>((size_t)nsub + 1, &st);
+  unsigned long long* dcnt = tmp.get<unsigned long long>((size_t)nsub + 3, &st);
+  if (st != SJ_OK) return fail(c, st, "allocation failed");
+  SJ_CUDA(c, cudaMemcpyAsync(dcuts, cuts, ((size_t)nsub + 1) * 4, cudaMemcpyHostToDevice, c->stream));
+  c->h2d_bytes += ((int64_t)nsub + 1) * 4;
+  SJ_CUDA(c, cudaMemsetAsync(dcnt, 0, ((size_t)nsub + 3) * 8, c->stream));
+  TriangleArgs ta;
+  ta.src = E->cols[0];
+  ta.dst = E->cols[1];
+  ta.ne = ne;
+  ta.out = out;
+  ta.in = in;
+  ta.pf.words = pf.words;
+  ta.pf.hdr = pf.hdr;
+  ta.pf.k = fp.k;
+  ta.pf.layout = SJ_REGBLOCKED32;
+  ta.pf.seed = fp.seed;
+  ta.pairs = ps.t;
+  ta.cuts = dcuts;
+  ta.nsub = nsub;
+  ta.counts = dcnt;
+  ta.stats = dcnt + nsub;
+  ta.work = dcnt + nsub + 2;
+  {
+    Launch L(c, SJ_K_OTHER, 8.0 * (double)ne);
+    launch_triangles(ta, c->num_sms, c->stream);
+  }
+  SJ_TRY(check_launch(c, "k_triangles"));
+  std::vector<unsigned long long> h((size_t)nsub + 2);
+  SJ_CUDA(c, cudaMemcpyAsync(h.data(), dcnt, ((size_t)nsub + 2) * 8, cudaMemcpyDeviceToHost, c->stream));
+  c->d2h_bytes += ((int64_t)nsub + 2) * 8;
+  SJ_TRY(sync_read(c));
+  uint64_t tot = 0;
+  for (int i = 0; i < nsub; ++i) {
+    counts[i] = h[i];
+    tot += h[i];
+  }
+  if (stats) {
+    stats->candidates = h[nsub];
+    stats->filter_passed = h[nsub + 1];
+    stats->triangles = tot;
+  }
+  return SJ_OK;
+}

@@ -846,6 +846,165 @@ __global__ void __launch_bounds__(kBlock) k_sum_terms(SumTermsArgs a) {
   }
 }
 
+
+// ---------------------------------------------------------------- cyclic query
+// Sec. 2.3: for a cyclic join the filter of the closing condition is rebuilt
+// on the fly.  For E(a,b) |x| E(b,c) |x| E(c,a) the closing relation is E
+// itself on the pair (c, a): a Bloom filter over packed edge pairs screens
+// every wedge before the exact pair-set lookup.
+__device__ __forceinline__ uint64_t pack_pair(int32_t s, int32_t d) {
+  return ((uint64_t)(uint32_t)s << 32) | (uint32_t)d;
+}
+
+__global__ void __launch_bounds__(kBlock) k_pair_filter_build(PairFilterBuildArgs a) {
+  __shared__ unsigned long long s_seen[kSeenSlots];
+  for (int i = threadIdx.x; i < kSeenSlots; i += blockDim.x) s_seen[i] = 0ull;
+  __syncthreads();
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.hdr[0] = a.nblocks;
+    a.hdr[1] = (uint64_t)a.n;
+  }
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+    const uint64_t h = fmix64(pack_pair(__ldcs(a.src + i), __ldcs(a.dst + i)) ^ a.seed);
+    uint32_t* p = a.words + reg32_word(h, a.nblocks * 8);
+    const uint32_t m = reg32_mask((uint32_t)h, a.k);
+    if ((__ldca(p) & m) != m && !seen_before(s_seen, h)) atomicOr(p, m);
+  }
+}
+
+__device__ __forceinline__ uint32_t pair_bucket(uint64_t v, uint32_t mask) {
+  return (uint32_t)fmix64(v ^ kTableSeed) & mask;
+}
+
+__global__ void __launch_bounds__(kBlock) k_pairset_insert(PairSetArgs a) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+    const unsigned long long v = pack_pair(__ldcs(a.src + i), __ldcs(a.dst + i)) + 1ull;
+    uint32_t b = pair_bucket(v, a.t.bucket_mask);
+    bool done = false;
+    for (uint32_t step = 0; step <= a.t.bucket_mask && !done; ++step) {
+      unsigned long long* bk = a.t.slots + (uint64_t)b * 4;
+#pragma unroll 1
+      for (int s = 0; s < 4 && !done; ++s) {
+        unsigned long long cur = ld_volatile_u64(reinterpret_cast<const uint64_t*>(bk + s));
+        if (cur == 0) cur = atomicCAS(bk + s, 0ull, v);
+        done = (cur == 0 || cur == v);
+      }
+      b = (b + 1) & a.t.bucket_mask;
+    }
+    if (!done) atomicOr(a.status, kErrTableFull);
+  }
+}
+
+__device__ __forceinline__ bool pairset_contains(const Table& t, uint64_t pair) {
+  const unsigned long long v = pair + 1ull;
+  uint32_t b = pair_bucket(v, t.bucket_mask);
+  for (uint32_t step = 0; step <= t.bucket_mask; ++step) {
+    const ulonglong2* p = reinterpret_cast<const ulonglong2*>(t.slots + (uint64_t)b * 4);
+    const ulonglong2 q0 = __ldg(p);
+    const ulonglong2 q1 = __ldg(p + 1);
+    if (q0.x == v || q0.y == v || q1.x == v || q1.y == v) return true;
+    if (q0.x == 0 || q0.y == 0 || q1.x == 0 || q1.y == 0) return false;
+    b = (b + 1) & t.bucket_mask;
+  }
+  return false;
+}
+
+// Adjacency list (offset, length) of vertex v, or length 0.
+__device__ __forceinline__ void adj_of(const Adjacency& g, int32_t v, uint64_t* off, uint32_t* len) {
+  const int64_t s = table_find(g.t, v);
+  if (s < 0) {
+    *off = 0;
+    *len = 0;
+    return;
+  }
+  const uint32_t id = (uint32_t)(__ldg(g.t.slots + s) >> 32) - 1u;
+  *off = __ldg(g.off + id);
+  *len = __ldg(g.cnt + id);
+}
+
+// Persistent warps take 32 edges (a, b) at a time.  For each edge the warp
+// walks the shorter of out(b) and in(a); a candidate c closes a triangle when
+// the pair (c, a) [walking out(b)] or (b, c) [walking in(a)] is an edge: the
+// pair filter screens it, the pair set confirms it.  Counts go to the
+// subquery whose vertex range holds a.
+__global__ void __launch_bounds__(kBlock) k_triangles(TriangleArgs a) {
+  __shared__ int32_t s_cuts[257];
+  __shared__ unsigned long long s_cnt[256];
+  for (int i = threadIdx.x; i <= a.nsub; i += blockDim.x) s_cuts[i] = a.cuts[i];
+  for (int i = threadIdx.x; i < a.nsub; i += blockDim.x) s_cnt[i] = 0ull;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const uint64_t pnb = __ldg(a.pf.hdr);
+  unsigned long long checked = 0, passed = 0;
+  while (true) {
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(a.work, 32ull);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (base >= (unsigned long long)a.ne) break;
+    const int64_t e = (int64_t)base + lane;
+    int32_t va = 0, vb = 0, sub = 0;
+    uint64_t off = 0;
+    uint32_t len = 0, side = 0;
+    if (e < a.ne) {
+      va = __ldg(a.src + e);
+      vb = __ldg(a.dst + e);
+      uint64_t o1, o2;
+      uint32_t l1, l2;
+      adj_of(a.out, vb, &o1, &l1);
+      adj_of(a.in, va, &o2, &l2);
+      side = l1 <= l2 ? 0u : 1u;
+      off = side ? o2 : o1;
+      len = side ? l2 : l1;
+      int lo = 0, hi = a.nsub;  // largest i with cuts[i] <= va
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_cuts[mid] <= va) lo = mid;
+        else hi = mid - 1;
+      }
+      sub = lo < a.nsub ? lo : a.nsub - 1;
+    }
+    for (int j = 0; j < 32; ++j) {
+      const uint32_t L = __shfl_sync(0xffffffffu, len, j);
+      if (L == 0) continue;
+      const uint64_t O = __shfl_sync(0xffffffffu, off, j);
+      const uint32_t S = __shfl_sync(0xffffffffu, side, j);
+      const int32_t A = __shfl_sync(0xffffffffu, va, j);
+      const int32_t B = __shfl_sync(0xffffffffu, vb, j);
+      const int SB = __shfl_sync(0xffffffffu, sub, j);
+      const int32_t* rows = S ? a.in.rows : a.out.rows;
+      unsigned long long found = 0;
+      for (uint32_t t = lane; t < L; t += 32) {
+        const int32_t row = __ldg(rows + O + t);
+        const uint64_t pair = S ? pack_pair(B, __ldg(a.src + row)) : pack_pair(__ldg(a.dst + row), A);
+        ++checked;
+        const uint64_t h = fmix64(pair ^ a.pf.seed);
+        const uint32_t m = reg32_mask((uint32_t)h, a.pf.k);
+        if ((__ldg(a.pf.words + reg32_word(h, pnb * 8)) & m) == m) {
+          ++passed;
+          if (pairset_contains(a.pairs, pair)) ++found;
+        }
+      }
+#pragma unroll
+      for (int d = 16; d > 0; d >>= 1) found += __shfl_xor_sync(0xffffffffu, found, d);
+      if (lane == 0 && found) atomicAdd(s_cnt + SB, found);
+    }
+  }
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) {
+    checked += __shfl_xor_sync(0xffffffffu, checked, d);
+    passed += __shfl_xor_sync(0xffffffffu, passed, d);
+  }
+  if (lane == 0) {
+    atomicAdd(a.stats + 0, checked);
+    atomicAdd(a.stats + 1, passed);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < a.nsub; i += blockDim.x)
+    if (s_cnt[i]) atomicAdd(a.counts + i, s_cnt[i]);
+}
+
 int host_grid(int64_t work, int per_block, int cap) {
   int64_t g = (work + per_block - 1) / per_block;
   if (g < 1) g = 1;
@@ -895,6 +1054,18 @@ void launch_agg_insert(const AggInsertArgs& a, int num_sms, cudaStream_t s) {
 
 void launch_agg_probe(const AggProbeArgs& a, int num_sms, cudaStream_t s) {
   k_agg_probe<<<host_grid(a.n, kBlock, num_sms * 8), kBlock, 0, s>>>(a);
+}
+
+void launch_pair_filter_build(const PairFilterBuildArgs& a, int num_sms, cudaStream_t s) {
+  k_pair_filter_build<<<host_grid(a.n, kBlock * 4, num_sms * 4), kBlock, 0, s>>>(a);
+}
+
+void launch_pairset_insert(const PairSetArgs& a, int num_sms, cudaStream_t s) {
+  k_pairset_insert<<<host_grid(a.n, kBlock, num_sms * 8), kBlock, 0, s>>>(a);
+}
+
+void launch_triangles(const TriangleArgs& a, int num_sms, cudaStream_t s) {
+  k_triangles<<<num_sms * 8, kBlock, 0, s>>>(a);
 }
 
 void launch_sum_terms(const SumTermsArgs& a, int num_sms, cudaStream_t s) {

@@ -174,4 +174,52 @@ struct SumTermsArgs {
 };
 void launch_sum_terms(const SumTermsArgs& a, int num_sms, cudaStream_t s);
 
+// ------------------------------------------------------------------ cyclic query
+// Edge pairs are packed (src << 32) | dst.  The pair filter uses the
+// register-blocked layout over h = fmix64(pair ^ seed); the pair set is an
+// open-addressing table whose slots hold pair + 1 (0 = empty).
+struct PairFilterBuildArgs {
+  const int32_t* src;
+  const int32_t* dst;
+  int64_t n;
+  uint64_t* hdr;
+  uint32_t* words;   // zeroed, nblocks * 8 words
+  uint64_t nblocks;
+  uint32_t k;
+  uint64_t seed;
+};
+void launch_pair_filter_build(const PairFilterBuildArgs& a, int num_sms, cudaStream_t s);
+
+struct PairSetArgs {
+  const int32_t* src;
+  const int32_t* dst;
+  int64_t n;
+  Table t;
+  uint32_t* status;
+};
+void launch_pairset_insert(const PairSetArgs& a, int num_sms, cudaStream_t s);
+
+struct Adjacency {          // multimap of edge ids keyed by one endpoint
+  Table t;
+  const uint32_t* cnt;
+  const uint64_t* off;
+  const int32_t* rows;
+};
+
+struct TriangleArgs {
+  const int32_t* src;
+  const int32_t* dst;
+  int64_t ne;
+  Adjacency out;            // keyed by src
+  Adjacency in;             // keyed by dst
+  FilterView pf;            // pair filter (register-blocked)
+  Table pairs;              // exact pair set
+  const int32_t* cuts;      // nsub + 1, increasing
+  int nsub;                 // <= 256
+  unsigned long long* counts;   // [nsub], zeroed
+  unsigned long long* stats;    // [0] candidates checked, [1] passed the pair filter; zeroed
+  unsigned long long* work;     // edge cursor, zeroed
+};
+void launch_triangles(const TriangleArgs& a, int num_sms, cudaStream_t s);
+
 }  // namespace sj

@@ -209,3 +209,52 @@ def serving_queries(pool_sizes, nq: int, domain: int = 1 << 22, min_len: int = 2
         qs.append({"rels": rels, "edges": chain_edges(n), "preds": preds, "root": n - 1,
                    "sum": [(0, 0, 0), (n - 1, 1, 0)]})
     return qs
+
+
+def rmat_edges(scale: int = 22, nedges: int = 50_000_000, a: float = 0.57, b: float = 0.19,
+               c: float = 0.19, seed: int = 4):
+    """Directed R-MAT graph on 2^scale vertices with exactly `nedges` distinct
+    edges and no self-loops (edges drawn until that many distinct ones exist;
+    the first distinct ones in draw order are kept).  Returns (src, dst) int32."""
+    g = _rng(seed, 0)
+    keys_seen = np.zeros(0, np.int64)
+    order_seen = np.zeros(0, np.int64)
+    drawn = 0
+    while len(keys_seen) < nedges:
+        m = int((nedges - len(keys_seen)) * 1.25) + 1024
+        s = np.zeros(m, np.int64)
+        d = np.zeros(m, np.int64)
+        for lvl in range(scale):
+            u = g.random(m)
+            right = (u >= a) & (u < a + b) | (u >= a + b + c)
+            down = u >= a + b
+            s |= down.astype(np.int64) << lvl
+            d |= right.astype(np.int64) << lvl
+        keep = s != d
+        k = (s[keep] << 32) | d[keep]
+        allk = np.concatenate([keys_seen, k])
+        allo = np.concatenate([order_seen, drawn + np.arange(len(k))])
+        drawn += len(k)
+        # distinct keys with the draw index of their first occurrence (stable sort)
+        srt = np.argsort(allk, kind="stable")
+        ks = allk[srt]
+        first = np.ones(len(ks), dtype=bool)
+        first[1:] = ks[1:] != ks[:-1]
+        keys_seen, order_seen = ks[first], allo[srt][first]
+    take = np.argsort(order_seen, kind="stable")[:nedges]
+    k = keys_seen[take]
+    return (k >> 32).astype(np.int32), (k & 0xFFFFFFFF).astype(np.int32)
+
+
+def uneven_cuts(nvert: int, nsub: int = 64, seed: int = 4):
+    """nsub + 1 increasing vertex cut points 0 = c_0 < ... < c_nsub = nvert,
+    uneven: subquery sizes drawn log-uniform before normalising."""
+    g = _rng(seed, 99)
+    w = np.exp(g.uniform(0.0, 3.0, nsub))
+    c = np.concatenate([[0.0], np.cumsum(w) / w.sum()]) * nvert
+    cuts = np.unique(np.round(c).astype(np.int64))
+    cuts[0], cuts[-1] = 0, nvert
+    while len(cuts) < nsub + 1:  # tiny graphs: pad with distinct points
+        extra = np.setdiff1d(np.arange(nvert + 1), cuts)[: nsub + 1 - len(cuts)]
+        cuts = np.unique(np.concatenate([cuts, extra]))
+    return cuts.astype(np.int32)

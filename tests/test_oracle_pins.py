@@ -335,3 +335,53 @@ def test_sieve_shrinks_skewed_chain():
     a = oracle.agg_propagation(w)
     b = oracle.agg_propagation(w, rels=sv, presieved=True)
     assert (a["count"], a["sum"]) == (b["count"], b["sum"])
+
+
+# ------------------------------------------------------------------ cyclic query (triangles)
+def _dense_trace_counts(src, dst, n, cuts):
+    A = np.zeros((n, n))
+    A[src, dst] = 1.0
+    d = np.diag(A @ A @ A)  # closed walks of length 3; exact integers in float64
+    return np.array([int(round(d[cuts[i]:cuts[i + 1]].sum())) for i in range(len(cuts) - 1)])
+
+
+@pytest.mark.parametrize("scale,ne", [(6, 300), (8, 2500), (9, 4000)])
+def test_triangles_vs_trace_of_a_cubed(scale, ne):
+    """Ordered directed 3-cycles per a-range equal diag(A^3) summed over the
+    range (no self-loops, so every closed 3-walk is a triangle)."""
+    src, dst = inputs.rmat_edges(scale=scale, nedges=ne, seed=scale)
+    assert len(set(zip(src.tolist(), dst.tolist()))) == ne and not np.any(src == dst)
+    n = 1 << scale
+    cuts = inputs.uneven_cuts(n, 8, seed=scale)
+    got = oracle.triangle_counts(src, dst, cuts)
+    assert np.array_equal(got, _dense_trace_counts(src, dst, n, cuts))
+    assert got.sum() % 3 == 0
+
+
+def test_triangles_complete_digraph():
+    """Complete directed graph on n vertices: n(n-1)(n-2) ordered triangles."""
+    n = 12
+    s, d = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    keep = s != d
+    src, dst = s[keep].astype(np.int32), d[keep].astype(np.int32)
+    got = oracle.triangle_counts(src, dst, np.array([0, 5, n], dtype=np.int32))
+    assert got.sum() == n * (n - 1) * (n - 2)
+    assert list(got) == [5 * (n - 1) * (n - 2), 7 * (n - 1) * (n - 2)]
+
+
+def test_triangles_single_cycle():
+    src = np.array([3, 7, 9, 3], dtype=np.int32)
+    dst = np.array([7, 9, 3, 9], dtype=np.int32)  # 3->7->9->3 plus a chord 3->9
+    got = oracle.triangle_counts(src, dst, np.array([0, 4, 8, 16], dtype=np.int32))
+    assert list(got) == [1, 1, 1]
+
+
+def test_triangle_counts_for_matches_full():
+    src, dst = inputs.rmat_edges(scale=9, nedges=4000, seed=3)
+    n = 1 << 9
+    verts = [int(v) for v in np.unique(src)[:: 37]]
+    cuts = np.unique(np.concatenate([[0, n], verts, np.array(verts) + 1])).astype(np.int32)
+    full = oracle.triangle_counts(src, dst, cuts)
+    got = oracle.triangle_counts_for(src, dst, verts)
+    for v, c in zip(verts, got):
+        assert full[np.searchsorted(cuts, v, side="right") - 1] == c
