@@ -423,6 +423,16 @@ SJ_API sj_status sj_server_stats_get(sj_server *srv, sj_server_stats *stats);
 /* Finish queued queries, stop the workers and free cached filters. */
 SJ_API sj_status sj_server_destroy(sj_server *srv);
 
+/*
+ * The whole method in one call: sj_sieve_path, then sj_join over the sieved
+ * relations, which are freed before returning (Sec. 2.2: pruning phase, then
+ * enumeration phase).  `opts` and `stats` as for sj_sieve_path, the rest as
+ * for sj_join.  Errors: those of the two calls.
+ */
+SJ_API sj_status sj_sieve_join(sj_ctx *ctx, const sj_path *path, const sj_sieve_opts *opts,
+                               int mode, int nrefs, const sj_colref *refs, sj_result *result,
+                               sj_sieve_stats *stats);
+
 /* ---------------------------------------------------------------- profiling */
 
 enum {

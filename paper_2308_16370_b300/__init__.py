@@ -37,7 +37,7 @@ EXPORTS = ["sj_create", "sj_destroy", "sj_sync", "sj_last_error", "sj_status_str
            "sj_filter_probe", "sj_free_filter", "sj_sieve", "sj_sieve_path", "sj_join",
            "sj_prof_enable", "sj_prof_reset", "sj_prof_read", "sj_counters", "sj_sieve_noalloc",
            "sj_server_create", "sj_server_add_relation", "sj_server_submit", "sj_server_poll",
-           "sj_server_stats_get", "sj_server_destroy", "sj_triangles"]
+           "sj_server_stats_get", "sj_server_destroy", "sj_triangles", "sj_sieve_join"]
 
 
 class SieveJoinError(RuntimeError):
@@ -170,6 +170,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "sj_server_stats_get": [P, ctypes.POINTER(ServerStats)],
         "sj_server_destroy": [P],
         "sj_triangles": [P, P, I, P, I, ctypes.POINTER(FilterParams), P, ctypes.POINTER(TriStats)],
+        "sj_sieve_join": [P, ctypes.POINTER(Path), ctypes.POINTER(SieveOpts), I, I,
+                          ctypes.POINTER(ColRef), ctypes.POINTER(Result), ctypes.POINTER(SieveStats)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -457,6 +459,25 @@ class Context:
                "rows": None}
         if res.rows:
             out["rows"] = Relation(self, res.rows)
+        return out
+
+    def sieve_join(self, rels, edges, preds=None, root=-1, mode=COUNT_SUM, refs=(), passes=FWD_BWD,
+                   bits_per_key=8, k=3, layout=REGBLOCKED32, seed=0, stats=False):
+        """Pruning phase then enumeration phase in one library call."""
+        path, keep = self._path(rels, edges, preds, root)
+        opts = SieveOpts(int(passes), 0, _params(bits_per_key, k, layout, seed), None)
+        rs = (ColRef * max(1, len(refs)))(*[ColRef(int(r[0]), int(r[1]), int(r[2]) if len(r) > 2 else 0, 0)
+                                            for r in refs])
+        res = Result()
+        st = SieveStats() if stats else None
+        self._check(self.lib.sj_sieve_join(self.ctx, ctypes.byref(path), ctypes.byref(opts), int(mode),
+                                           len(refs), rs, ctypes.byref(res),
+                                           ctypes.byref(st) if st is not None else None))
+        out = {"count": int(res.count), "sum": int(res.sum), "intermediate": int(res.intermediate),
+               "rows": Relation(self, res.rows) if res.rows else None}
+        if st is not None:
+            out["steps"] = [(("select", "fwd", "bwd")[st.step[s].kind], st.step[s].rel,
+                             st.step[s].rows_in, st.step[s].rows_out) for s in range(st.nsteps)]
         return out
 
     # --------------------------------------------------------------- cyclic query

@@ -1043,8 +1043,12 @@ extern "C" sj_status sj_join(sj_ctx* c, const sj_path* path, const sj_rel* input
 
     if (last && mode == SJ_COUNT_SUM) {
       if (np == 0 || nb == 0) break;  // empty join
+      // Per-key (count, sum) table on the smaller side, probed by the other:
+      // COUNT += cnt and SUM += value(probe row) * cnt + sum for every hit.
+      const bool swap = np < nb;  // build on the intermediate, probe with the relation
+      const int64_t n_build = swap ? np : nb;
       Table2 tb;
-      if ((st = make_table(c, tmp, nb, &tb)) != SJ_OK) break;
+      if ((st = make_table(c, tmp, n_build, &tb)) != SJ_OK) break;
       unsigned long long* cnt = tmp.get<unsigned long long>(tb.nslots, &st);
       unsigned long long* sum = tmp.get<unsigned long long>(tb.nslots, &st);
       if (st != SJ_OK) {
@@ -1054,37 +1058,38 @@ extern "C" sj_status sj_join(sj_ctx* c, const sj_path* path, const sj_rel* input
       cudaMemsetAsync(cnt, 0, tb.nslots * 8, c->stream);
       cudaMemsetAsync(sum, 0, tb.nslots * 8, c->stream);
       cudaMemsetAsync(c->d_misc + kMiscResult, 0, 3 * 8, c->stream);
+      Terms none;
+      memset(&none, 0, sizeof(none));
+      const Terms rel_terms = want_sum ? terms_of(B, lp.rel, nrefs, refs) : none;
+      const Terms base_terms = (want_sum && in.base) ? terms_of(rels[0], 0, nrefs, refs) : none;
+      const uint64_t* inter_vals = (want_sum && !in.base) ? in.psum : nullptr;
       AggInsertArgs ai;
-      ai.keys = B->cols[lp.rel_col];
-      ai.n = nb;
+      ai.keys = swap ? pk : B->cols[lp.rel_col];
+      ai.n = n_build;
       ai.t = tb.t;
-      ai.terms = want_sum ? terms_of(B, lp.rel, nrefs, refs) : Terms{};
-      if (!want_sum) memset(&ai.terms, 0, sizeof(ai.terms));
+      ai.terms = swap ? base_terms : rel_terms;
+      ai.vals = swap ? inter_vals : nullptr;
       ai.cnt = cnt;
       ai.sum = sum;
       ai.status = status_ptr(c);
       {
-        Launch Lk(c, SJ_K_AGG, (4.0 + 4.0 * ai.terms.n) * (double)nb);
+        Launch Lk(c, SJ_K_AGG, (4.0 + 4.0 * ai.terms.n + (ai.vals ? 8.0 : 0.0)) * (double)n_build);
         launch_agg_insert(ai, nsm, c->stream);
       }
       if ((st = check_launch(c, "k_agg_insert")) != SJ_OK) break;
       AggProbeArgs ap;
-      ap.keys = pk;
-      ap.n = np;
+      ap.keys = swap ? B->cols[lp.rel_col] : pk;
+      ap.n = swap ? nb : np;
       ap.t = tb.t;
       ap.cnt = cnt;
       ap.sum = sum;
-      memset(&ap.probe_terms, 0, sizeof(ap.probe_terms));
-      ap.psum_in = nullptr;
-      if (want_sum) {
-        if (in.base) ap.probe_terms = terms_of(rels[0], 0, nrefs, refs);
-        else ap.psum_in = in.psum;
-      }
+      ap.probe_terms = swap ? rel_terms : base_terms;
+      ap.psum_in = swap ? nullptr : inter_vals;
       ap.result = reinterpret_cast<unsigned long long*>(c->d_misc + kMiscResult);
       ap.status = status_ptr(c);
       {
         const double per = 4.0 + (ap.psum_in ? 8.0 : 4.0 * ap.probe_terms.n);
-        Launch Lk(c, SJ_K_AGG, per * (double)np);
+        Launch Lk(c, SJ_K_AGG, per * (double)ap.n);
         launch_agg_probe(ap, nsm, c->stream);
       }
       if ((st = check_launch(c, "k_agg_probe")) != SJ_OK) break;
@@ -1540,4 +1545,16 @@ extern "C" sj_status sj_triangles(sj_ctx* c, sj_rel edges, int nsub, const int32
     stats->triangles = tot;
   }
   return SJ_OK;
+}
+
+extern "C" sj_status sj_sieve_join(sj_ctx* c, const sj_path* path, const sj_sieve_opts* opts,
+                                   int mode, int nrefs, const sj_colref* refs, sj_result* result,
+                                   sj_sieve_stats* stats) {
+  if (!c || !path || !result) return fail(c, SJ_EINVAL, "null argument");
+  if (path->nrel < 1 || path->nrel > SJ_MAX_REL) return fail(c, SJ_EINVAL, "nrel out of range");
+  sj_rel sieved[SJ_MAX_REL] = {};
+  SJ_TRY(sj_sieve_path(c, path, opts, sieved, stats));
+  const sj_status st = sj_join(c, path, sieved, mode, nrefs, refs, result);
+  for (int i = 0; i < path->nrel; ++i) free_rel(c, sieved[i]);
+  return st;
 }

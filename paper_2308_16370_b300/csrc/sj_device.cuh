@@ -119,9 +119,9 @@ struct Vec {
   uint64_t v[NCH];
 };
 
-template <int NCH>
+template <int NCH, int NT = kBlock>
 __device__ __forceinline__ Vec<NCH> block_exclusive_scan(Vec<NCH> x, Vec<NCH>* total,
-                                                         Vec<NCH>* s_warp /* [8] */) {
+                                                         Vec<NCH>* s_warp /* [NT / 32] */) {
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   Vec<NCH> inc = x;
@@ -140,7 +140,7 @@ __device__ __forceinline__ Vec<NCH> block_exclusive_scan(Vec<NCH> x, Vec<NCH>* t
 #pragma unroll
   for (int c = 0; c < NCH; ++c) { wpre.v[c] = 0; tot.v[c] = 0; }
 #pragma unroll
-  for (int w = 0; w < kBlock / 32; ++w) {
+  for (int w = 0; w < NT / 32; ++w) {
 #pragma unroll
     for (int c = 0; c < NCH; ++c) {
       if (w < warp) wpre.v[c] += s_warp[w].v[c];

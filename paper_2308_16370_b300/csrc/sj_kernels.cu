@@ -275,16 +275,19 @@ __device__ __forceinline__ uint32_t test16(const SieveTest& t, const int32_t* ke
   return test_classic(t, nb, key, live);
 }
 
-__global__ void __launch_bounds__(kBlock, 4) k_sieve(SieveArgs a) {
+// NT threads per CTA, 16 rows per thread: tiles of NT * 16 rows.
+template <int NT>
+__global__ void __launch_bounds__(NT, 1024 / NT) k_sieve(SieveArgs a) {
+  constexpr int kTile = NT * 16;
   __shared__ uint32_t s_tile;
-  __shared__ Vec<1> s_warp[kBlock / 32];
+  __shared__ Vec<1> s_warp[NT / 32];
   __shared__ uint64_t s_prefix;
   const int tid = threadIdx.x;
   if (tid == 0) s_tile = draw_ticket(a.tile_counter);
   __syncthreads();
   const uint32_t tile = s_tile;
   const int64_t n = a.n_dev ? (int64_t)(*a.n_dev) : a.n_host;
-  const int64_t ntiles = (n + kSieveTile - 1) / kSieveTile;
+  const int64_t ntiles = (n + kTile - 1) / kTile;
   if ((int64_t)tile >= ntiles) {
     if (tile == 0 && tid == 0) {
       *a.out_n = 0;
@@ -292,7 +295,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_sieve(SieveArgs a) {
     }
     return;
   }
-  const int64_t base = (int64_t)tile * kSieveTile;
+  const int64_t base = (int64_t)tile * kTile;
   const int32_t* vcol = a.ntest > 0 ? a.test[0].col : nullptr;
 
   // 1. first test column: 4 coalesced 16-byte loads per thread
@@ -300,7 +303,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_sieve(SieveArgs a) {
   uint32_t alive = 0;
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
-    const int64_t r0 = base + (int64_t)(v * kBlock + tid) * 4;
+    const int64_t r0 = base + (int64_t)(v * NT + tid) * 4;
     if (r0 + 4 <= n) {
       if (vcol) {
         const int4 x = __ldcs(reinterpret_cast<const int4*>(vcol + r0));
@@ -329,7 +332,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_sieve(SieveArgs a) {
     if (t < a.ntest && alive) {
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
-        const int64_t row = base + (int64_t)((i >> 2) * kBlock + tid) * 4 + (i & 3);
+        const int64_t row = base + (int64_t)((i >> 2) * NT + tid) * 4 + (i & 3);
         key[i] = ((alive >> i) & 1u) ? __ldcs(a.test[t].col + row) : 0;
       }
       alive = test16(a.test[t], key, alive);
@@ -344,7 +347,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_sieve(SieveArgs a) {
 #pragma unroll
   for (int v = 0; v < 4; ++v) cnt.v[0] |= (uint64_t)__popc((alive >> (4 * v)) & 0xfu) << (16 * v);
   Vec<1> tot;
-  const Vec<1> ex = block_exclusive_scan<1>(cnt, &tot, s_warp);
+  const Vec<1> ex = block_exclusive_scan<1, NT>(cnt, &tot, s_warp);
   uint64_t chunk_off[4];
   uint64_t tile_total = 0;
 #pragma unroll
@@ -386,7 +389,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_sieve(SieveArgs a) {
     const uint32_t bits = (alive >> (4 * v)) & 0xfu;
     if (!bits) continue;
     const uint64_t pos0 = prefix + chunk_off[v] + ((ex.v[0] >> (16 * v)) & 0xffffull);
-    const int64_t r0 = base + (int64_t)(v * kBlock + tid) * 4;
+    const int64_t r0 = base + (int64_t)(v * NT + tid) * 4;
 #pragma unroll
     for (int j = 0; j < kMaxCols; ++j) {
       if (j >= a.nout) break;
@@ -695,31 +698,23 @@ __device__ __forceinline__ uint64_t upper_q(const uint64_t* o, uint64_t lo, uint
   return lo;
 }
 
+// One thread per output tuple j: the matching probe row is the largest q with
+// o[q] <= j (binary search; the upper levels of the search stay in L1), and
+// the build row is the (j - o[q])-th row of that key's group.  A hot key's
+// fan-out is spread over as many threads as it has outputs.
 __global__ void __launch_bounds__(kBlock) k_mm_expand(MMExpandArgs a) {
-  __shared__ uint64_t s_q[2];
-  const uint64_t span = (uint64_t)kBlock * kExpandItems;
-  const uint64_t j0 = (uint64_t)blockIdx.x * span;
-  if (j0 >= a.T) return;
-  const uint64_t j1 = (j0 + span < a.T ? j0 + span : a.T) - 1;
-  if (threadIdx.x == 0) s_q[0] = upper_q(a.o, 0, a.Q - 1, j0);
-  if (threadIdx.x == 32) s_q[1] = upper_q(a.o, 0, a.Q - 1, j1);
-  __syncthreads();
-  const uint64_t qlo = s_q[0], qhi = s_q[1];
-#pragma unroll 2
-  for (int it = 0; it < kExpandItems; ++it) {
-    const uint64_t j = j0 + (uint64_t)it * kBlock + threadIdx.x;
-    if (j > j1) break;
-    const uint64_t q = upper_q(a.o, qlo, qhi, j);
-    const uint64_t t = j - __ldg(a.o + q);
-    const int32_t prow = __ldg(a.prow + q);
-    const int32_t brow = __ldg(a.rows + __ldg(a.off + __ldg(a.pid + q)) + t);
+  const uint64_t j = (uint64_t)blockIdx.x * kBlock + threadIdx.x;
+  if (j >= a.T) return;
+  const uint64_t q = upper_q(a.o, 0, a.Q - 1, j);
+  const uint64_t t = j - __ldg(a.o + q);
+  const int32_t prow = __ldg(a.prow + q);
+  const int32_t brow = __ldg(a.rows + __ldg(a.off + __ldg(a.pid + q)) + t);
 #pragma unroll
-    for (int c = 0; c < kMaxCols; ++c)
-      if (c < a.nout) a.out[c][j] = __ldg(a.src[c] + (a.src_build[c] ? brow : prow));
-    if (a.psum_out) {
-      const uint64_t ps = a.psum_in ? __ldg(a.psum_in + prow) : term_sum(a.probe_terms, prow);
-      a.psum_out[j] = ps + term_sum(a.build_terms, brow);
-    }
+  for (int c = 0; c < kMaxCols; ++c)
+    if (c < a.nout) a.out[c][j] = __ldg(a.src[c] + (a.src_build[c] ? brow : prow));
+  if (a.psum_out) {
+    const uint64_t ps = a.psum_in ? __ldg(a.psum_in + prow) : term_sum(a.probe_terms, prow);
+    a.psum_out[j] = ps + term_sum(a.build_terms, brow);
   }
 }
 
@@ -756,7 +751,7 @@ __global__ void __launch_bounds__(kBlock) k_agg_insert(AggInsertArgs a) {
     uint64_t val = 0;
     if (active) {
       s = agg_find_or_insert(a.t, __ldcs(a.keys + row), a.status);
-      val = term_sum(a.terms, row);
+      val = a.vals ? __ldg(a.vals + row) : term_sum(a.terms, row);
     }
     // combine rows of the same key within the warp, then one atomic pair per key
     const long long gk = (s >= 0) ? s : (-2 - lane);
@@ -773,7 +768,7 @@ __global__ void __launch_bounds__(kBlock) k_agg_insert(AggInsertArgs a) {
     }
     if (s >= 0 && lane == __ffs(group) - 1) {
       atomicAdd(a.cnt + s, (unsigned long long)__popc(group));
-      if (a.terms.n) atomicAdd(a.sum + s, (unsigned long long)gsum);
+      if (a.terms.n || a.vals) atomicAdd(a.sum + s, (unsigned long long)gsum);
     }
   }
 }
@@ -1024,7 +1019,7 @@ void launch_bloom_probe(const BloomProbeArgs& a, int num_sms, cudaStream_t s) {
 }
 
 void launch_sieve(const SieveArgs& a, int64_t n_upper, cudaStream_t s) {
-  k_sieve<<<host_grid(n_upper, kSieveTile, 1 << 30), kBlock, 0, s>>>(a);
+  k_sieve<kSieveThreads><<<host_grid(n_upper, kSieveTile, 1 << 30), kSieveThreads, 0, s>>>(a);
 }
 
 void launch_scan_u32(const ScanArgs& a, int64_t n_upper, cudaStream_t s) {
@@ -1044,8 +1039,7 @@ void launch_mm_probe(const MMProbeArgs& a, cudaStream_t s) {
 }
 
 void launch_mm_expand(const MMExpandArgs& a, cudaStream_t s) {
-  const int64_t span = (int64_t)kBlock * kExpandItems;
-  k_mm_expand<<<host_grid((int64_t)a.T, (int)span, 1 << 30), kBlock, 0, s>>>(a);
+  k_mm_expand<<<host_grid((int64_t)a.T, kBlock, 1 << 30), kBlock, 0, s>>>(a);
 }
 
 void launch_agg_insert(const AggInsertArgs& a, int num_sms, cudaStream_t s) {

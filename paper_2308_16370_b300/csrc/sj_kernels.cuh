@@ -56,8 +56,12 @@ struct SieveArgs {
   uint32_t* tile_counter; // 0 at launch (reset by the kernel for the next one)
   LookBack<1> lb;
 };
-// Tiles of 4096 rows: 256 threads x 4 vectors x 4 int32.
-constexpr int kSieveTile = kBlock * 16;
+// Tiles of kSieveThreads x 16 rows: each thread 4 vectors x 4 int32.
+#ifndef SJ_SIEVE_THREADS
+#define SJ_SIEVE_THREADS 256
+#endif
+constexpr int kSieveThreads = SJ_SIEVE_THREADS;
+constexpr int kSieveTile = kSieveThreads * 16;
 void launch_sieve(const SieveArgs& a, int64_t n_upper, cudaStream_t s);
 
 // ------------------------------------------------------------------ scans
@@ -140,7 +144,6 @@ struct MMExpandArgs {       // one output tuple per (matching probe row, build r
   Terms build_terms;
   uint64_t* psum_out;            // null: no SUM carried
 };
-constexpr int kExpandItems = 8;
 void launch_mm_expand(const MMExpandArgs& a, cudaStream_t s);
 
 struct AggInsertArgs {
@@ -148,6 +151,7 @@ struct AggInsertArgs {
   int64_t n;
   Table t;
   Terms terms;
+  const uint64_t* vals;     // per-row value instead of terms, or null
   unsigned long long* cnt;  // [nslots] zeroed
   unsigned long long* sum;  // [nslots] zeroed
   uint32_t* status;

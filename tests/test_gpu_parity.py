@@ -323,3 +323,15 @@ def test_invalid_arguments(ctx):
     # the context stays usable after rejected calls
     r = ctx.join(rels, w["edges"], refs=w["sum"])
     assert r["count"] == oracle.hash_join(w)["count"]
+
+
+def test_sieve_join_one_call(ctx):
+    """sj_sieve_join equals sj_sieve_path followed by sj_join, and the oracle."""
+    w = inputs.zipf_chain(nrows=300_000, domain=150_000, seed=12)
+    rels = load(ctx, w)
+    one = ctx.sieve_join(rels, w["edges"], w["preds"], w["root"], refs=w["sum"], stats=True)
+    sv, st = ctx.sieve_path(rels, w["edges"], w["preds"], w["root"])
+    two = join_both(ctx, w, rels, inputs_=sv)
+    exp = oracle.agg_propagation(w)
+    assert (one["count"], one["sum"]) == (two["count"], two["sum"]) == (exp["count"], exp["sum"])
+    assert one["steps"] == st["steps"]
