@@ -428,6 +428,7 @@ def main():
         ctx.prof_enable(False)
     counters = ctx.counters()
     kstats = {k: ctx.prof_read(k) for k in sj.KERNEL_KINDS}
+    gaps = ctx.prof_gaps()
     total_ms = max_over_ranks(total_ms, ws)
     ms_per_step = total_ms / args.steps
     value = tuples * ws / (ms_per_step / 1000.0)
@@ -502,6 +503,7 @@ def main():
                     for k, v in kstats.items() if v["launches"]},
         "serving": serving,
         "cyclic_triangles": cyclic,
+        "device_idle_ms_per_step_after": {k: v / args.steps for k, v in gaps.items() if v},
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)

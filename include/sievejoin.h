@@ -459,6 +459,10 @@ SJ_API sj_status sj_prof_enable(sj_ctx *ctx, int on);
 SJ_API sj_status sj_prof_reset(sj_ctx *ctx);
 SJ_API sj_status sj_prof_read(sj_ctx *ctx, int kind, int64_t *launches, double *ms, double *bytes);
 SJ_API sj_status sj_counters(sj_ctx *ctx, int64_t *launches, int64_t *h2d_bytes, int64_t *d2h_bytes);
+/* Device idle time (ms) between the end of a profiled launch of each class and
+ * the start of the next profiled launch (host work, syncs, memsets), summed
+ * per class into gap_ms[SJ_K_COUNT]. */
+SJ_API sj_status sj_prof_gaps(sj_ctx *ctx, double *gap_ms);
 
 #ifdef __cplusplus
 }

@@ -53,6 +53,15 @@ struct sj_ctx {
   uint8_t* scratch = nullptr;
   size_t scratch_bytes = 0;
   uint32_t epoch = 0;  // look-back flag epoch of the last scan launch
+  cudaEvent_t ev_wait = nullptr;  // host waits on one point of the stream
+  // per-call arena (sj_sieve_join): temporaries are bump-allocated from one
+  // device block and released together, instead of one allocator call each
+  struct {
+    bool on = false;
+    uint8_t* base = nullptr;
+    size_t size = 0, off = 0, peak = 0;
+    std::vector<std::pair<void*, size_t>> overflow;
+  } arena;
   int64_t launches = 0;
   int64_t h2d_bytes = 0;
   int64_t d2h_bytes = 0;
@@ -61,6 +70,7 @@ struct sj_ctx {
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
   double prof_ms[SJ_K_COUNT] = {};
+  double prof_gap_ms[SJ_K_COUNT] = {};  // device idle after a launch of each class
   double prof_bytes[SJ_K_COUNT] = {};
   int64_t prof_n[SJ_K_COUNT] = {};
 };
@@ -104,8 +114,7 @@ sj_status fail(sj_ctx* c, sj_status s, const std::string& msg) {
     if (s_ != SJ_OK) return s_;   \
   } while (0)
 
-void* dalloc(sj_ctx* c, size_t bytes) {
-  bytes = round_up(bytes ? bytes : 1);
+void* raw_alloc(sj_ctx* c, size_t bytes) {
   void* p = nullptr;
   if (c->alloc) {
     p = c->alloc(bytes, c->user);
@@ -116,11 +125,71 @@ void* dalloc(sj_ctx* c, size_t bytes) {
   return p;
 }
 
+void raw_free(sj_ctx* c, void* p, size_t bytes) {
+  if (!p) return;
+  if (c->free_) c->free_(p, bytes, c->user);
+  else cudaFreeAsync(p, c->stream);
+}
+
+bool in_arena(const sj_ctx* c, const void* p) {
+  const uint8_t* q = static_cast<const uint8_t*>(p);
+  return c->arena.base && q >= c->arena.base && q < c->arena.base + c->arena.size;
+}
+
+// Device memory for temporaries.  Inside an arena scope it is bump-allocated
+// (or, when the arena is full, allocated and released with the scope).
+// `persistent` allocations (results handed to the caller, context state)
+// always bypass the arena.
+void* dalloc(sj_ctx* c, size_t bytes, bool persistent = false) {
+  bytes = round_up(bytes ? bytes : 1);
+  if (c->arena.on && !persistent) {
+    auto& A = c->arena;
+    if (A.off + bytes <= A.size) {
+      void* p = A.base + A.off;
+      A.off += bytes;
+      A.peak = std::max(A.peak, A.off);
+      return p;
+    }
+    A.peak = std::max(A.peak, A.off + bytes);
+    void* p = raw_alloc(c, bytes);
+    if (p) A.overflow.emplace_back(p, bytes);
+    return p;
+  }
+  return raw_alloc(c, bytes);
+}
+
 void dfree(sj_ctx* c, void* p, size_t bytes) {
   if (!p) return;
   bytes = round_up(bytes ? bytes : 1);
-  if (c->free_) c->free_(p, bytes, c->user);
-  else cudaFreeAsync(p, c->stream);
+  if (c->arena.on) {
+    if (in_arena(c, p)) return;
+    for (auto& o : c->arena.overflow)
+      if (o.first == p) return;  // released when the arena scope ends
+  }
+  raw_free(c, p, bytes);
+}
+
+void arena_begin(sj_ctx* c) {
+  c->arena.on = true;
+  c->arena.off = 0;
+  c->arena.peak = 0;
+}
+
+// End the scope: release overflow blocks and grow the arena to the peak seen,
+// so the next call of the same size needs no allocator call at all.  All
+// releases are stream-ordered after the work that used the memory.
+void arena_end(sj_ctx* c) {
+  auto& A = c->arena;
+  A.on = false;
+  for (auto& o : A.overflow) raw_free(c, o.first, o.second);
+  A.overflow.clear();
+  if (A.peak > A.size) {
+    raw_free(c, A.base, A.size);
+    const size_t nb = round_up(A.peak + A.peak / 4, 1 << 20);
+    A.base = static_cast<uint8_t*>(raw_alloc(c, nb));
+    A.size = A.base ? nb : 0;
+  }
+  A.off = 0;
 }
 
 // Temporaries of one call, released (stream-ordered) when the call returns.
@@ -214,9 +283,9 @@ sj_status scratch_for(sj_ctx* c, int64_t ntiles, uint32_t** counter, LookBack<NC
   const size_t need = kAlign + (size_t)ntiles * NCH * 8;
   if (need > c->scratch_bytes) {
     // the old scratch may still be used by enqueued work: stream-ordered free
-    dfree(c, c->scratch, c->scratch_bytes);
+    raw_free(c, c->scratch, c->scratch_bytes);
     const size_t nb = round_up(std::max(need, c->scratch_bytes * 2));
-    c->scratch = static_cast<uint8_t*>(dalloc(c, nb));
+    c->scratch = static_cast<uint8_t*>(dalloc(c, nb, true));
     c->scratch_bytes = c->scratch ? nb : 0;
     if (!c->scratch) return fail(c, SJ_ENOMEM, "scratch allocation failed");
     SJ_CUDA(c, cudaMemsetAsync(c->scratch, 0, nb, c->stream));
@@ -234,11 +303,11 @@ sj_status scratch_for(sj_ctx* c, int64_t ntiles, uint32_t** counter, LookBack<NC
 }
 
 // --------------------------------------------------------------- relations
-sj_rel new_rel(sj_ctx* c, int ncols, int64_t cap) {
+sj_rel new_rel(sj_ctx* c, int ncols, int64_t cap, bool persistent = false) {
   sj_rel r = new sj_rel_s();
   const size_t colb = round_up((size_t)std::max<int64_t>(cap, 1) * 4);
   r->mem_bytes = kAlign + colb * (size_t)ncols;
-  r->mem = dalloc(c, r->mem_bytes);
+  r->mem = dalloc(c, r->mem_bytes, persistent);
   if (!r->mem) {
     delete r;
     return nullptr;
@@ -310,14 +379,31 @@ sj_status sieve_step_timed(sj_ctx* c, const sj_rel_s* in, const std::vector<Test
   }
   a.n_host = in->d_n ? 0 : in->nrows;
   a.n_dev = in->d_n;
-  a.out_n = r->d_n;
-  a.out_n2 = slot >= 0 ? c->d_misc + kMiscSteps + slot : nullptr;
+  // two passes: each tile compacts into its slot of a gapped buffer, then the
+  // move kernel packs the slots in order (no tile waits for another)
   const int64_t ntiles = (cap + kSieveTile - 1) / kSieveTile;
-  sj_status st = scratch_for<1>(c, ntiles, &a.tile_counter, &a.lb);
-  if (st != SJ_OK) {
+  const size_t gcol = round_up((size_t)std::max<int64_t>(cap, 1) * 4);
+  const size_t gbytes = gcol * (size_t)in->ncols + round_up((size_t)std::max<int64_t>(ntiles, 1) * 4);
+  uint8_t* gap = static_cast<uint8_t*>(dalloc(c, gbytes));
+  if (!gap) {
     free_rel(c, r);
-    return st;
+    return fail(c, SJ_ENOMEM, "sieve staging allocation failed");
   }
+  SieveMoveArgs m;
+  memset(&m, 0, sizeof(m));
+  for (int j = 0; j < in->ncols; ++j) {
+    a.out[j] = reinterpret_cast<int32_t*>(gap + gcol * j);
+    m.gap[j] = a.out[j];
+    m.out[j] = r->cols[j];
+  }
+  a.tile_cnt = reinterpret_cast<uint32_t*>(gap + gcol * in->ncols);
+  m.nout = in->ncols;
+  m.tile = kSieveTile;
+  m.tile_cnt = a.tile_cnt;
+  m.n_host = a.n_host;
+  m.n_dev = a.n_dev;
+  m.out_n = r->d_n;
+  m.out_n2 = slot >= 0 ? c->d_misc + kMiscSteps + slot : nullptr;
   // algorithmic bytes: the first tested column of every input row; each kept
   // row's other columns read and all of its columns written
   const int nvec = tests.empty() ? 0 : 1;
@@ -326,9 +412,12 @@ sj_status sieve_step_timed(sj_ctx* c, const sj_rel_s* in, const std::vector<Test
   {
     Launch L = in->d_n ? Launch(c, SJ_K_SIEVE, 0, slot_in, per_in, slot, per_out)
                        : Launch(c, SJ_K_SIEVE, per_in * (double)in->nrows, slot, per_out);
-    launch_sieve(a, cap, c->stream);
+    c->launches++;  // two kernels
+    launch_sieve_two_pass(a, m, cap, c->stream);
   }
-  st = check_launch(c, "k_sieve");
+  dfree(c, gap, gbytes);
+  sj_status st = SJ_OK;
+  st = check_launch(c, "k_sieve_local/k_sieve_move");
   if (st != SJ_OK) {
     free_rel(c, r);
     return st;
@@ -558,11 +647,13 @@ sj_status sj_create(sj_ctx** out, int device, void* stream, sj_alloc_fn alloc, s
 sj_status sj_destroy(sj_ctx* c) {
   if (!c) return SJ_EINVAL;
   cudaStreamSynchronize(c->stream);
-  dfree(c, c->scratch, c->scratch_bytes);
-  dfree(c, c->d_misc, kMiscWords * sizeof(uint64_t));
+  raw_free(c, c->scratch, c->scratch_bytes);
+  raw_free(c, c->arena.base, c->arena.size);
+  raw_free(c, c->d_misc, kMiscWords * sizeof(uint64_t));
   cudaStreamSynchronize(c->stream);
   cudaFreeHost(c->h_misc);
   for (auto e : c->ev_pool) cudaEventDestroy(e);
+  if (c->ev_wait) cudaEventDestroy(c->ev_wait);
   delete c;
   return SJ_OK;
 }
@@ -920,6 +1011,52 @@ sj_status make_table(sj_ctx* c, Temps& tmp, int64_t nrows, Table2* out) {
   return SJ_OK;
 }
 
+// Multimap of row ids keyed by `keys` (the same build as a join level):
+// distinct keys get dense ids, rows are grouped by key id.
+sj_status build_adjacency(sj_ctx* c, Temps& tmp, const int32_t* keys, int64_t n, Adjacency* g) {
+  sj_status st = SJ_OK;
+  Table2 tb;
+  SJ_TRY(make_table(c, tmp, n, &tb));
+  uint32_t* cnt = tmp.get<uint32_t>(n, &st);
+  uint32_t* rid = tmp.get<uint32_t>(n, &st);
+  uint32_t* rank = tmp.get<uint32_t>(n, &st);
+  uint64_t* off = tmp.get<uint64_t>(n, &st);
+  int32_t* rows = tmp.get<int32_t>(n, &st);
+  if (st != SJ_OK) return fail(c, st, "adjacency allocation failed");
+  SJ_CUDA(c, cudaMemsetAsync(cnt, 0, (size_t)n * 4, c->stream));
+  SJ_CUDA(c, cudaMemsetAsync(c->d_misc + kMiscNuniq, 0, 8, c->stream));
+  uint32_t* nuniq = reinterpret_cast<uint32_t*>(c->d_misc + kMiscNuniq);
+  MMInsertArgs mi{keys, n, tb.t, nuniq, cnt, rid, rank, status_ptr(c)};
+  {
+    Launch L(c, SJ_K_HT_BUILD, 12.0 * (double)n);
+    launch_mm_insert(mi, c->num_sms, c->stream);
+  }
+  SJ_TRY(check_launch(c, "k_mm_insert"));
+  ScanArgs sa;
+  sa.in = cnt;
+  sa.out = off;
+  sa.n_host = 0;
+  sa.n_dev = nuniq;
+  sa.total = nullptr;
+  SJ_TRY(scratch_for<1>(c, (n + kScanTile - 1) / kScanTile, &sa.tile_counter, &sa.lb));
+  {
+    Launch L(c, SJ_K_HT_BUILD, 12.0 * (double)n);
+    launch_scan_u32(sa, n, c->stream);
+  }
+  SJ_TRY(check_launch(c, "k_scan_u32"));
+  MMScatterArgs ms{rid, rank, off, n, rows};
+  {
+    Launch L(c, SJ_K_HT_BUILD, 20.0 * (double)n);
+    launch_mm_scatter(ms, c->num_sms, c->stream);
+  }
+  SJ_TRY(check_launch(c, "k_mm_scatter"));
+  g->t = tb.t;
+  g->cnt = cnt;
+  g->off = off;
+  g->rows = rows;
+  return SJ_OK;
+}
+
 }  // namespace
 
 extern "C" sj_status sj_join(sj_ctx* c, const sj_path* path, const sj_rel* inputs, int mode,
@@ -999,7 +1136,7 @@ extern "C" sj_status sj_join(sj_ctx* c, const sj_path* path, const sj_rel* input
       }
       return SJ_OK;
     }
-    sj_rel out = new_rel(c, nrefs, r0->nrows);
+    sj_rel out = new_rel(c, nrefs, r0->nrows, true);
     if (!out) return fail(c, SJ_ENOMEM, "result allocation failed");
     out->d_n = nullptr;
     out->nrows = r0->nrows;
@@ -1030,6 +1167,22 @@ extern "C" sj_status sj_join(sj_ctx* c, const sj_path* path, const sj_rel* input
   uint64_t intermediate = 0;
   sj_rel out_rel = nullptr;
   sj_status st = SJ_OK;
+  if (!c->ev_wait && cudaEventCreateWithFlags(&c->ev_wait, cudaEventDisableTiming) != cudaSuccess)
+    return fail(c, SJ_ECUDA, "event creation failed");
+
+  // Multimap tables of the non-final levels depend only on their relation, so
+  // each is enqueued ahead of the wait for the previous level's totals.
+  Temps keep(c);
+  std::vector<Adjacency> tables(plan.size());
+  std::vector<char> built(plan.size(), 0);
+  auto is_mm = [&](size_t L) { return !(L + 1 == plan.size() && mode == SJ_COUNT_SUM); };
+  auto enqueue_build = [&](size_t L) -> sj_status {
+    const sj_rel_s* Bl = rels[plan[L].rel];
+    built[L] = 1;
+    tables[L] = Adjacency{};
+    if (Bl->nrows == 0) return SJ_OK;
+    return build_adjacency(c, keep, Bl->cols[plan[L].rel_col], Bl->nrows, &tables[L]);
+  };
 
   for (size_t L = 0; L < plan.size() && st == SJ_OK; ++L) {
     const LevelPlan& lp = plan[L];
@@ -1121,18 +1274,11 @@ extern "C" sj_status sj_join(sj_ctx* c, const sj_path* path, const sj_rel* input
     const bool carry_sum = want_sum && !last;
 
     uint64_t Q = 0, T = 0;
-    Table2 tb{};
-    int32_t* rows = nullptr;
-    uint64_t* off = nullptr;
     int32_t *prow = nullptr, *pid = nullptr;
     uint64_t* o = nullptr;
+    if (!built[L] && (st = enqueue_build(L)) != SJ_OK) break;
+    const Adjacency& G = tables[L];
     if (np > 0 && nb > 0) {
-      if ((st = make_table(c, tmp, nb, &tb)) != SJ_OK) break;
-      uint32_t* cnt = tmp.get<uint32_t>(nb, &st);
-      uint32_t* rid = tmp.get<uint32_t>(nb, &st);
-      uint32_t* rank = tmp.get<uint32_t>(nb, &st);
-      off = tmp.get<uint64_t>(nb, &st);
-      rows = tmp.get<int32_t>(nb, &st);
       prow = tmp.get<int32_t>(np, &st);
       pid = tmp.get<int32_t>(np, &st);
       o = tmp.get<uint64_t>(np, &st);
@@ -1140,39 +1286,11 @@ extern "C" sj_status sj_join(sj_ctx* c, const sj_path* path, const sj_rel* input
         fail(c, st, "join level allocation failed");
         break;
       }
-      cudaMemsetAsync(cnt, 0, (size_t)nb * 4, c->stream);
-      cudaMemsetAsync(c->d_misc + kMiscNuniq, 0, 8, c->stream);
-      uint32_t* nuniq = reinterpret_cast<uint32_t*>(c->d_misc + kMiscNuniq);
-      MMInsertArgs mi{B->cols[lp.rel_col], nb, tb.t, nuniq, cnt, rid, rank, status_ptr(c)};
-      {
-        Launch Lk(c, SJ_K_HT_BUILD, 12.0 * (double)nb);
-        launch_mm_insert(mi, nsm, c->stream);
-      }
-      if ((st = check_launch(c, "k_mm_insert")) != SJ_OK) break;
-      ScanArgs sa;
-      sa.in = cnt;
-      sa.out = off;
-      sa.n_host = 0;
-      sa.n_dev = nuniq;
-      sa.total = nullptr;
-      if ((st = scratch_for<1>(c, (nb + kScanTile - 1) / kScanTile, &sa.tile_counter, &sa.lb)) != SJ_OK)
-        break;
-      {
-        Launch Lk(c, SJ_K_HT_BUILD, 12.0 * (double)nb);
-        launch_scan_u32(sa, nb, c->stream);
-      }
-      if ((st = check_launch(c, "k_scan_u32")) != SJ_OK) break;
-      MMScatterArgs ms{rid, rank, off, nb, rows};
-      {
-        Launch Lk(c, SJ_K_HT_BUILD, 20.0 * (double)nb);
-        launch_mm_scatter(ms, nsm, c->stream);
-      }
-      if ((st = check_launch(c, "k_mm_scatter")) != SJ_OK) break;
       MMProbeArgs mp;
       mp.keys = pk;
       mp.n = np;
-      mp.t = tb.t;
-      mp.cnt = cnt;
+      mp.t = G.t;
+      mp.cnt = G.cnt;
       mp.prow = prow;
       mp.pid = pid;
       mp.o = o;
@@ -1185,11 +1303,33 @@ extern "C" sj_status sj_join(sj_ctx* c, const sj_path* path, const sj_rel* input
         launch_mm_probe(mp, c->stream);
       }
       if ((st = check_launch(c, "k_mm_probe")) != SJ_OK) break;
-      if ((st = sync_read(c)) != SJ_OK) break;
+      // read the level's totals at an event, and let the next level's table
+      // build run on the device meanwhile
+      if (cudaMemcpyAsync(c->h_misc + kMiscTotals, c->d_misc + kMiscTotals, 16,
+                          cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+          cudaEventRecord(c->ev_wait, c->stream) != cudaSuccess) {
+        st = fail(c, SJ_ECUDA, "level totals readback failed");
+        break;
+      }
+      c->d2h_bytes += 16;
+      if (L + 1 < plan.size() && is_mm(L + 1) && !built[L + 1] && (st = enqueue_build(L + 1)) != SJ_OK)
+        break;
+      if (cudaEventSynchronize(c->ev_wait) != cudaSuccess) {
+        st = fail(c, SJ_ECUDA, "level totals wait failed");
+        break;
+      }
       Q = c->h_misc[kMiscTotals];
       T = c->h_misc[kMiscTotals + 1];
-      if (c->prof_on && !c->prof.empty()) c->prof.back().bytes += 16.0 * (double)Q;
+      if (c->prof_on && !c->prof.empty()) {
+        for (size_t r = c->prof.size(); r-- > 0;)
+          if (c->prof[r].kind == SJ_K_HT_PROBE) {
+            c->prof[r].bytes += 16.0 * (double)Q;
+            break;
+          }
+      }
     }
+    const int32_t* rows = G.rows;
+    const uint64_t* off = G.off;
     if (!last) intermediate += T;
     if (T >= (uint64_t(1) << 31) * 16) {
       st = fail(c, SJ_ENOMEM, "intermediate result too large");
@@ -1202,7 +1342,7 @@ extern "C" sj_status sj_join(sj_ctx* c, const sj_path* path, const sj_rel* input
     nx.base = false;
     std::vector<int32_t*> outs;
     if (last) {
-      out_rel = new_rel(c, nrefs, (int64_t)T);
+      out_rel = new_rel(c, nrefs, (int64_t)T, true);
       if (!out_rel) {
         st = fail(c, SJ_ENOMEM, "result allocation failed");
         break;
@@ -1289,7 +1429,7 @@ extern "C" sj_status sj_join(sj_ctx* c, const sj_path* path, const sj_rel* input
   }
   if (mode == SJ_MATERIALIZE) {
     if (!out_rel) {  // an empty level before the last
-      out_rel = new_rel(c, nrefs, 0);
+      out_rel = new_rel(c, nrefs, 0, true);
       if (!out_rel) return fail(c, SJ_ENOMEM, "result allocation failed");
       out_rel->d_n = nullptr;
       out_rel->nrows = 0;
@@ -1312,15 +1452,21 @@ sj_status sj_prof_enable(sj_ctx* c, int on) {
 
 static sj_status prof_collect(sj_ctx* c) {
   SJ_CUDA(c, cudaStreamSynchronize(c->stream));
-  for (const ProfRec& r : c->prof) {
+  for (size_t i = 0; i < c->prof.size(); ++i) {
+    const ProfRec& r = c->prof[i];
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, r.e0, r.e1) != cudaSuccess) {
       cudaGetLastError();
       continue;
     }
     c->prof_ms[r.kind] += ms;
-    c->prof_bytes[r.kind] += (r.slot_a < 0 && r.slot_b < 0) ? r.bytes : r.bytes;
+    c->prof_bytes[r.kind] += r.bytes;
     c->prof_n[r.kind] += 1;
+    float gap = 0.f;
+    if (i + 1 < c->prof.size() &&
+        cudaEventElapsedTime(&gap, r.e1, c->prof[i + 1].e0) == cudaSuccess && gap > 0.f)
+      c->prof_gap_ms[r.kind] += gap;
+    cudaGetLastError();
   }
   c->prof.clear();
   c->ev_used = 0;
@@ -1334,6 +1480,7 @@ sj_status sj_prof_reset(sj_ctx* c) {
   c->ev_used = 0;
   for (int k = 0; k < SJ_K_COUNT; ++k) {
     c->prof_ms[k] = 0;
+    c->prof_gap_ms[k] = 0;
     c->prof_bytes[k] = 0;
     c->prof_n[k] = 0;
   }
@@ -1352,6 +1499,13 @@ sj_status sj_prof_read(sj_ctx* c, int kind, int64_t* launches, double* ms, doubl
   return SJ_OK;
 }
 
+sj_status sj_prof_gaps(sj_ctx* c, double* gap_ms) {
+  if (!c || !gap_ms) return SJ_EINVAL;
+  SJ_TRY(prof_collect(c));
+  for (int k = 0; k < SJ_K_COUNT; ++k) gap_ms[k] = c->prof_gap_ms[k];
+  return SJ_OK;
+}
+
 sj_status sj_counters(sj_ctx* c, int64_t* launches, int64_t* h2d_bytes, int64_t* d2h_bytes) {
   if (!c) return SJ_EINVAL;
   if (launches) *launches = c->launches;
@@ -1364,52 +1518,6 @@ sj_status sj_counters(sj_ctx* c, int64_t* launches, int64_t* h2d_bytes, int64_t*
 
 // ======================================================================== cyclic query
 namespace {
-
-// Multimap of row ids keyed by `keys` (the same build as a join level):
-// distinct keys get dense ids, rows are grouped by key id.
-sj_status build_adjacency(sj_ctx* c, Temps& tmp, const int32_t* keys, int64_t n, Adjacency* g) {
-  sj_status st = SJ_OK;
-  Table2 tb;
-  SJ_TRY(make_table(c, tmp, n, &tb));
-  uint32_t* cnt = tmp.get<uint32_t>(n, &st);
-  uint32_t* rid = tmp.get<uint32_t>(n, &st);
-  uint32_t* rank = tmp.get<uint32_t>(n, &st);
-  uint64_t* off = tmp.get<uint64_t>(n, &st);
-  int32_t* rows = tmp.get<int32_t>(n, &st);
-  if (st != SJ_OK) return fail(c, st, "adjacency allocation failed");
-  SJ_CUDA(c, cudaMemsetAsync(cnt, 0, (size_t)n * 4, c->stream));
-  SJ_CUDA(c, cudaMemsetAsync(c->d_misc + kMiscNuniq, 0, 8, c->stream));
-  uint32_t* nuniq = reinterpret_cast<uint32_t*>(c->d_misc + kMiscNuniq);
-  MMInsertArgs mi{keys, n, tb.t, nuniq, cnt, rid, rank, status_ptr(c)};
-  {
-    Launch L(c, SJ_K_HT_BUILD, 12.0 * (double)n);
-    launch_mm_insert(mi, c->num_sms, c->stream);
-  }
-  SJ_TRY(check_launch(c, "k_mm_insert"));
-  ScanArgs sa;
-  sa.in = cnt;
-  sa.out = off;
-  sa.n_host = 0;
-  sa.n_dev = nuniq;
-  sa.total = nullptr;
-  SJ_TRY(scratch_for<1>(c, (n + kScanTile - 1) / kScanTile, &sa.tile_counter, &sa.lb));
-  {
-    Launch L(c, SJ_K_HT_BUILD, 12.0 * (double)n);
-    launch_scan_u32(sa, n, c->stream);
-  }
-  SJ_TRY(check_launch(c, "k_scan_u32"));
-  MMScatterArgs ms{rid, rank, off, n, rows};
-  {
-    Launch L(c, SJ_K_HT_BUILD, 20.0 * (double)n);
-    launch_mm_scatter(ms, c->num_sms, c->stream);
-  }
-  SJ_TRY(check_launch(c, "k_mm_scatter"));
-  g->t = tb.t;
-  g->cnt = cnt;
-  g->off = off;
-  g->rows = rows;
-  return SJ_OK;
-}
 
 }  // namespace
 
@@ -1553,8 +1661,10 @@ extern "C" sj_status sj_sieve_join(sj_ctx* c, const sj_path* path, const sj_siev
   if (!c || !path || !result) return fail(c, SJ_EINVAL, "null argument");
   if (path->nrel < 1 || path->nrel > SJ_MAX_REL) return fail(c, SJ_EINVAL, "nrel out of range");
   sj_rel sieved[SJ_MAX_REL] = {};
-  SJ_TRY(sj_sieve_path(c, path, opts, sieved, stats));
-  const sj_status st = sj_join(c, path, sieved, mode, nrefs, refs, result);
+  arena_begin(c);
+  sj_status st = sj_sieve_path(c, path, opts, sieved, stats);
+  if (st == SJ_OK) st = sj_join(c, path, sieved, mode, nrefs, refs, result);
   for (int i = 0; i < path->nrel; ++i) free_rel(c, sieved[i]);
+  arena_end(c);
   return st;
 }

@@ -416,6 +416,153 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_sieve(SieveArgs a) {
   }
 }
 
+// Pass 1 of the two-pass sieve: the same tile work as k_sieve, but each tile
+// writes its survivors, compacted and in order, to its own slot of a gapped
+// buffer (rows tile*kTile ..) and its count to a.tile_cnt[tile].  No tile
+// waits for another, so probe-latency variance between tiles costs nothing.
+template <int NT>
+__global__ void __launch_bounds__(NT, 1024 / NT) k_sieve_local(SieveArgs a) {
+  constexpr int kTile = NT * 16;
+  __shared__ Vec<1> s_warp[NT / 32];
+  const int tid = threadIdx.x;
+  const uint32_t tile = blockIdx.x;
+  const int64_t n = a.n_dev ? (int64_t)(*a.n_dev) : a.n_host;
+  const int64_t ntiles = (n + kTile - 1) / kTile;
+  if ((int64_t)tile >= ntiles) return;
+  const int64_t base = (int64_t)tile * kTile;
+  const int32_t* vcol = a.ntest > 0 ? a.test[0].col : nullptr;
+
+  // 1. first test column: 4 coalesced 16-byte loads per thread
+  int32_t key[16];
+  uint32_t alive = 0;
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const int64_t r0 = base + (int64_t)(v * NT + tid) * 4;
+    if (r0 + 4 <= n) {
+      if (vcol) {
+        const int4 x = __ldcs(reinterpret_cast<const int4*>(vcol + r0));
+        key[4 * v + 0] = x.x;
+        key[4 * v + 1] = x.y;
+        key[4 * v + 2] = x.z;
+        key[4 * v + 3] = x.w;
+      }
+      alive |= 0xfu << (4 * v);
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        key[4 * v + e] = 0;
+        if (r0 + e < n) {
+          if (vcol) key[4 * v + e] = __ldcs(vcol + r0 + e);
+          alive |= 1u << (4 * v + e);
+        }
+      }
+    }
+  }
+
+  // 2. tests; later tests only load the rows still alive
+  if (a.ntest > 0) alive = test16(a.test[0], key, alive);
+#pragma unroll
+  for (int t = 1; t < kMaxTests; ++t) {
+    if (t < a.ntest && alive) {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int64_t row = base + (int64_t)((i >> 2) * NT + tid) * 4 + (i & 3);
+        key[i] = ((alive >> i) & 1u) ? __ldcs(a.test[t].col + row) : 0;
+      }
+      alive = test16(a.test[t], key, alive);
+    }
+  }
+  // the first test column's values are reloaded for output if tests overwrote them
+  const bool keys_valid = a.ntest <= 1;
+
+  // 3. block scan of the survivor counts of the 4 chunks (16 bits each)
+  Vec<1> cnt;
+  cnt.v[0] = 0;
+#pragma unroll
+  for (int v = 0; v < 4; ++v) cnt.v[0] |= (uint64_t)__popc((alive >> (4 * v)) & 0xfu) << (16 * v);
+  Vec<1> tot;
+  const Vec<1> ex = block_exclusive_scan<1, NT>(cnt, &tot, s_warp);
+  uint64_t chunk_off[4];
+  uint64_t tile_total = 0;
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    chunk_off[v] = tile_total;
+    tile_total += (tot.v[0] >> (16 * v)) & 0xffffull;
+  }
+
+  // 4. this tile's slot of the gapped buffer
+  if (tid == 0) a.tile_cnt[tile] = (uint32_t)tile_total;
+  const uint64_t prefix = (uint64_t)tile * kTile;
+
+  // 5. write the survivors of every output column, in input order
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const uint32_t bits = (alive >> (4 * v)) & 0xfu;
+    if (!bits) continue;
+    const uint64_t pos0 = prefix + chunk_off[v] + ((ex.v[0] >> (16 * v)) & 0xffffull);
+    const int64_t r0 = base + (int64_t)(v * NT + tid) * 4;
+#pragma unroll
+    for (int j = 0; j < kMaxCols; ++j) {
+      if (j >= a.nout) break;
+      int32_t val[4];
+      if (a.out_is_vec[j] && keys_valid) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) val[e] = key[4 * v + e];
+      } else if (r0 + 4 <= n) {
+        const int4 x = __ldcs(reinterpret_cast<const int4*>(a.in[j] + r0));
+        val[0] = x.x;
+        val[1] = x.y;
+        val[2] = x.z;
+        val[3] = x.w;
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) val[e] = ((bits >> e) & 1u) ? __ldcs(a.in[j] + r0 + e) : 0;
+      }
+      int32_t* dst = a.out[j] + pos0;
+      int k = 0;
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        if ((bits >> e) & 1u) dst[k++] = val[e];
+    }
+  }
+}
+
+
+// Pass 2: move every tile's survivors from its gapped slot to the dense
+// output.  Block t sums the counts of tiles 0..t-1 (a few KB from L2) and
+// copies its tile's rows; the block of the last tile writes the total.
+__global__ void __launch_bounds__(kBlock) k_sieve_move(SieveMoveArgs a) {
+  __shared__ uint64_t s_red[kBlock / 32];
+  const int64_t n = a.n_dev ? (int64_t)(*a.n_dev) : a.n_host;
+  const int64_t ntiles = (n + a.tile - 1) / a.tile;
+  const int64_t t = blockIdx.x;
+  if (ntiles == 0 && t == 0 && threadIdx.x == 0) {
+    *a.out_n = 0;
+    if (a.out_n2) *a.out_n2 = 0;
+  }
+  if (t >= ntiles) return;
+  uint64_t part = 0;
+  for (int64_t u = threadIdx.x; u < t; u += kBlock) part += __ldg(a.tile_cnt + u);
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) part += __shfl_xor_sync(0xffffffffu, part, d);
+  if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = part;
+  __syncthreads();
+  uint64_t prefix = 0;
+#pragma unroll
+  for (int w = 0; w < kBlock / 32; ++w) prefix += s_red[w];
+  const uint32_t cnt = __ldg(a.tile_cnt + t);
+  if (t == ntiles - 1 && threadIdx.x == 0) {
+    *a.out_n = prefix + cnt;
+    if (a.out_n2) *a.out_n2 = prefix + cnt;
+  }
+  const uint64_t src0 = (uint64_t)t * a.tile;
+  for (int c = 0; c < a.nout; ++c) {
+    const int32_t* src = a.gap[c] + src0;
+    int32_t* dst = a.out[c] + prefix;
+    for (uint32_t i = threadIdx.x; i < cnt; i += kBlock) dst[i] = __ldcs(src + i);
+  }
+}
+
 // ---------------------------------------------------------------- scan
 __global__ void __launch_bounds__(kBlock) k_scan_u32(ScanArgs a) {
   __shared__ uint32_t s_tile;
@@ -1020,6 +1167,13 @@ void launch_bloom_probe(const BloomProbeArgs& a, int num_sms, cudaStream_t s) {
 
 void launch_sieve(const SieveArgs& a, int64_t n_upper, cudaStream_t s) {
   k_sieve<kSieveThreads><<<host_grid(n_upper, kSieveTile, 1 << 30), kSieveThreads, 0, s>>>(a);
+}
+
+void launch_sieve_two_pass(const SieveArgs& a, const SieveMoveArgs& m, int64_t n_upper,
+                           cudaStream_t s) {
+  const int g = host_grid(n_upper, kSieveTile, 1 << 30);
+  k_sieve_local<kSieveThreads><<<g, kSieveThreads, 0, s>>>(a);
+  k_sieve_move<<<g, kBlock, 0, s>>>(m);
 }
 
 void launch_scan_u32(const ScanArgs& a, int64_t n_upper, cudaStream_t s) {

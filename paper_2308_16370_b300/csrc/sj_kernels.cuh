@@ -55,6 +55,20 @@ struct SieveArgs {
   uint64_t* out_n2;       // optional second copy (per-step statistics), or null
   uint32_t* tile_counter; // 0 at launch (reset by the kernel for the next one)
   LookBack<1> lb;
+  uint32_t* tile_cnt;     // two-pass sieve: survivors per tile
+};
+
+// Pass 2 of the two-pass sieve (see k_sieve_move).
+struct SieveMoveArgs {
+  const int32_t* gap[kMaxCols];   // gapped pass-1 output, kSieveTile rows per tile slot
+  int32_t* out[kMaxCols];
+  int nout;
+  int64_t tile;
+  const uint32_t* tile_cnt;
+  int64_t n_host;
+  const uint64_t* n_dev;
+  uint64_t* out_n;
+  uint64_t* out_n2;
 };
 // Tiles of kSieveThreads x 16 rows: each thread 4 vectors x 4 int32.
 #ifndef SJ_SIEVE_THREADS
@@ -63,6 +77,10 @@ struct SieveArgs {
 constexpr int kSieveThreads = SJ_SIEVE_THREADS;
 constexpr int kSieveTile = kSieveThreads * 16;
 void launch_sieve(const SieveArgs& a, int64_t n_upper, cudaStream_t s);
+// Two-pass variant: pass 1 writes each tile's survivors to a gapped buffer
+// (a.out) and its count to a.tile_cnt; pass 2 compacts them into m.out.
+void launch_sieve_two_pass(const SieveArgs& a, const SieveMoveArgs& m, int64_t n_upper,
+                           cudaStream_t s);
 
 // ------------------------------------------------------------------ scans
 struct ScanArgs {
