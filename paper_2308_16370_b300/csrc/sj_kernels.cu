@@ -133,6 +133,31 @@ __device__ __forceinline__ void bloom_insert_reg4(const BloomBuildArgs& a, uint6
       atomicOr(p[j], m[j]);
 }
 
+// Register-blocked layout, kBuildKeys keys per thread per round: the key
+// vectors, then all the filter words are loaded before any atomic, so a thread
+// has kBuildKeys independent L2 reads in flight instead of a serial chain.
+constexpr int kBuildVecs = 2;
+constexpr int kBuildKeys = 4 * kBuildVecs;
+
+__device__ __forceinline__ void bloom_insert_regN(const BloomBuildArgs& a, uint64_t nb,
+                                                  const int32_t (&key)[kBuildKeys], uint32_t live,
+                                                  unsigned long long* seen) {
+  uint32_t w[kBuildKeys], cur[kBuildKeys], m[kBuildKeys];
+  const uint64_t nwords = nb * 8;
+#pragma unroll
+  for (int j = 0; j < kBuildKeys; ++j) {
+    const uint64_t h = key_hash(key[j], a.seed);
+    w[j] = (uint32_t)reg32_word(h, nwords);
+    m[j] = reg32_mask((uint32_t)h, a.k);
+  }
+#pragma unroll
+  for (int j = 0; j < kBuildKeys; ++j) cur[j] = __ldca(a.words + w[j]);
+#pragma unroll
+  for (int j = 0; j < kBuildKeys; ++j)
+    if (((live >> j) & 1u) && (cur[j] & m[j]) != m[j] && !seen_before(seen, key_hash(key[j], a.seed)))
+      atomicOr(a.words + w[j], m[j]);
+}
+
 __global__ void __launch_bounds__(kBlock, 3) k_bloom_build(BloomBuildArgs a) {
   __shared__ unsigned long long s_seen[kSeenSlots];
   for (int i = threadIdx.x; i < kSeenSlots; i += blockDim.x) s_seen[i] = 0ull;
@@ -147,8 +172,40 @@ __global__ void __launch_bounds__(kBlock, 3) k_bloom_build(BloomBuildArgs a) {
   }
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t nvec = (n + 3) >> 2;
   const int4* kv = reinterpret_cast<const int4*>(a.keys);
+  if (a.layout == 0 && nb * 8 < (1ull << 32)) {
+    // rounds of kBuildKeys keys per thread: vector v of a round is key vector
+    // base + v * stride, so every warp load is one contiguous 512 B
+    const int64_t nvec = (n + 3) >> 2;
+    for (int64_t base = gid; base < nvec; base += kBuildVecs * stride) {
+      int32_t k16[kBuildKeys];
+      uint32_t live = 0;
+#pragma unroll
+      for (int v = 0; v < kBuildVecs; ++v) {
+        const int64_t i = base + v * stride;
+        if (i < nvec && (i << 2) + 4 <= n) {
+          const int4 x = __ldcs(kv + i);
+          k16[4 * v] = x.x;
+          k16[4 * v + 1] = x.y;
+          k16[4 * v + 2] = x.z;
+          k16[4 * v + 3] = x.w;
+          live |= 0xfu << (4 * v);
+        } else {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            k16[4 * v + e] = 0;
+            if (i < nvec && (i << 2) + e < n) {
+              k16[4 * v + e] = __ldcs(a.keys + (i << 2) + e);
+              live |= 1u << (4 * v + e);
+            }
+          }
+        }
+      }
+      bloom_insert_regN(a, nb, k16, live, s_seen);
+    }
+    return;
+  }
+  const int64_t nvec = (n + 3) >> 2;
   for (int64_t i = gid; i < nvec; i += stride) {
     int32_t k4[4];
     uint32_t live = 0xfu;
@@ -1158,7 +1215,7 @@ int host_grid(int64_t work, int per_block, int cap) {
 
 // ---------------------------------------------------------------- launchers
 void launch_bloom_build(const BloomBuildArgs& a, int64_t n_upper, int num_sms, cudaStream_t s) {
-  k_bloom_build<<<host_grid(n_upper, kBlock * 4, num_sms * 3), kBlock, 0, s>>>(a);
+  k_bloom_build<<<host_grid(n_upper, kBlock * kBuildKeys, num_sms * 3), kBlock, 0, s>>>(a);
 }
 
 void launch_bloom_probe(const BloomProbeArgs& a, int num_sms, cudaStream_t s) {
