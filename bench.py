@@ -69,6 +69,7 @@ def parse():
                     help="largest pool relation (50M in the full-size serving workload)")
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--no-cyclic", action="store_true", help="skip the triangle-query run")
+    ap.add_argument("--no-star", action="store_true", help="skip the star-join run")
     return ap.parse_args()
 
 
@@ -314,6 +315,56 @@ def serving_run(args, torch, sj):
                     f"from 8 templates; COUNT and SUM"}
 
 
+# ----------------------------------------------------------------------------- star join
+def star_run(torch, sj, ctx, stream):
+    """Star join: 100M fact rows (4 int32 FKs + int64 measure), 4 dimensions of
+    1M rows with a 10% range predicate each; COUNT and SUM(measure), sieved
+    (filters from the filtered dimensions sieve the fact table) and plain."""
+    from paper_2308_16370_b300 import inputs
+    w = inputs.star()
+    fact = w["rels"][0]
+    ok = np.ones(len(fact[0]), dtype=bool)
+    for i in range(4):
+        _, lo, hi = w["preds"][1 + i]
+        a = w["rels"][1 + i][1][fact[i]]
+        ok &= (a >= lo) & (a < hi)
+    meas = fact[4].view(np.uint32).astype(np.int64) | (fact[5].astype(np.int64) << 32)
+    exp = (int(ok.sum()), int(meas[ok].sum()) % (1 << 64))
+    dev = [[torch.from_numpy(c).cuda() for c in r] for r in w["rels"]]
+    rels = [ctx.load_relation(cols, where="borrow") for cols in dev]
+    tuples = sum(len(r[0]) for r in w["rels"])
+    out = {"workload": "star: fact 100M rows x (4 int32 FKs + int64 measure), 4 dimensions of 1M "
+                       "rows with 10% range predicates; COUNT and SUM(measure)",
+           "input_tuples": tuples}
+
+    def timeit(fn, reps):
+        fn()
+        ts = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts)), r
+
+    ms, r = timeit(lambda: ctx.sieve_join(rels, w["edges"], w["preds"], w["root"], refs=w["sum"],
+                                          stats=True), 5)
+    out["sieved"] = {"ms": ms, "tuples_per_s": tuples / (ms / 1000.0), "count": r["count"],
+                     "sum": r["sum"], "matches_direct_lookup": (r["count"], r["sum"]) == exp,
+                     "sieve_steps": [list(x) for x in r["steps"]]}
+    ms, r = timeit(lambda: ctx.join(rels, w["edges"], w["preds"], w["root"], refs=w["sum"]), 3)
+    out["plain"] = {"ms": ms, "tuples_per_s": tuples / (ms / 1000.0),
+                    "matches_direct_lookup": (r["count"], r["sum"]) == exp,
+                    "intermediate_tuples": r["intermediate"]}
+    for x in rels:
+        x.free()
+    return out
+
+
 # ----------------------------------------------------------------------------- cyclic query
 def cyclic_run(torch, sj, ctx, stream):
     """Triangle query E(a,b) E(b,c) E(c,a) on an R-MAT graph (0.57, 0.19,
@@ -466,6 +517,10 @@ def main():
     if not args.no_cyclic:
         cyclic = cyclic_run(torch, sj, ctx, stream)
 
+    star = None
+    if not args.no_star:
+        star = star_run(torch, sj, ctx, stream)
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_oracle_run(spec)
@@ -503,6 +558,7 @@ def main():
                     for k, v in kstats.items() if v["launches"]},
         "serving": serving,
         "cyclic_triangles": cyclic,
+        "star": star,
         "device_idle_ms_per_step_after": {k: v / args.steps for k, v in gaps.items() if v},
         "cpu_baseline": cpu,
     }

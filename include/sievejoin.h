@@ -433,6 +433,16 @@ SJ_API sj_status sj_sieve_join(sj_ctx *ctx, const sj_path *path, const sj_sieve_
                                int mode, int nrefs, const sj_colref *refs, sj_result *result,
                                sj_sieve_stats *stats);
 
+/*
+ * Self-test of the bounded device waits (no counterpart in the paper): one
+ * warp polls a device flag that nothing sets, with the bound and backoff of
+ * the look-back waits.  The wait gives up after about a second, records
+ * SJ_ETIMEOUT in the status word and the kernel finishes; this call then
+ * synchronises and returns SJ_ETIMEOUT, and the context stays usable.  It
+ * faults or traps nothing.
+ */
+SJ_API sj_status sj_selftest_wait_timeout(sj_ctx *ctx);
+
 /* ---------------------------------------------------------------- profiling */
 
 enum {

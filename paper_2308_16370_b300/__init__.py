@@ -37,7 +37,8 @@ EXPORTS = ["sj_create", "sj_destroy", "sj_sync", "sj_last_error", "sj_status_str
            "sj_filter_probe", "sj_free_filter", "sj_sieve", "sj_sieve_path", "sj_join",
            "sj_prof_enable", "sj_prof_reset", "sj_prof_read", "sj_counters", "sj_sieve_noalloc",
            "sj_server_create", "sj_server_add_relation", "sj_server_submit", "sj_server_poll",
-           "sj_server_stats_get", "sj_server_destroy", "sj_triangles", "sj_sieve_join", "sj_prof_gaps"]
+           "sj_server_stats_get", "sj_server_destroy", "sj_triangles", "sj_sieve_join", "sj_prof_gaps",
+           "sj_selftest_wait_timeout"]
 
 
 class SieveJoinError(RuntimeError):
@@ -162,6 +163,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                          ctypes.POINTER(ctypes.c_double)],
         "sj_counters": [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64)],
         "sj_prof_gaps": [P, ctypes.POINTER(ctypes.c_double)],
+        "sj_selftest_wait_timeout": [P],
         "sj_sieve_noalloc": [P, I, PP, I64, I, P, ctypes.c_uint64, ctypes.POINTER(FilterParams),
                              PP, P, P, ctypes.POINTER(ctypes.c_char_p)],
         "sj_server_create": [PP, ctypes.POINTER(ServerOpts)],
@@ -516,6 +518,10 @@ class Context:
         g = (ctypes.c_double * 7)()
         self._check(self.lib.sj_prof_gaps(self.ctx, g))
         return {k: float(g[v]) for k, v in KERNEL_KINDS.items()}
+
+    def selftest_wait_timeout(self) -> int:
+        """Make one bounded device wait run out; returns the status (4 = timeout)."""
+        return int(self.lib.sj_selftest_wait_timeout(self.ctx))
 
     def counters(self):
         """Kernel launches, host-to-device and device-to-host bytes since the

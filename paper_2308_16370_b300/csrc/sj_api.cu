@@ -1668,3 +1668,18 @@ extern "C" sj_status sj_sieve_join(sj_ctx* c, const sj_path* path, const sj_siev
   arena_end(c);
   return st;
 }
+
+extern "C" sj_status sj_selftest_wait_timeout(sj_ctx* c) {
+  if (!c) return SJ_EINVAL;
+  Temps tmp(c);
+  sj_status st = SJ_OK;
+  uint32_t* flag = tmp.get<uint32_t>(1, &st);
+  if (st != SJ_OK) return fail(c, st, "self-test allocation failed");
+  SJ_CUDA(c, cudaMemsetAsync(flag, 0, 4, c->stream));
+  {
+    Launch L(c, SJ_K_OTHER, 0.0);
+    launch_wait_flag(flag, status_ptr(c), c->stream);
+  }
+  SJ_TRY(check_launch(c, "k_wait_flag"));
+  return sync_read(c);
+}

@@ -1204,6 +1204,20 @@ __global__ void __launch_bounds__(kBlock) k_triangles(TriangleArgs a) {
     if (s_cnt[i]) atomicAdd(a.counts + i, s_cnt[i]);
 }
 
+// Self-test of the bounded waits: one warp polls `flag` (which nothing sets)
+// with the same bound and backoff as the look-back, then records a timeout.
+__global__ void k_wait_flag(const uint32_t* flag, uint32_t* status) {
+  uint32_t spins = 0, ns = 8;
+  uint32_t f = ld_volatile_u32(flag);
+  while (f == 0) {
+    if (++spins > kSpinLimit) break;
+    __nanosleep(ns);
+    if (ns < 256) ns <<= 1;
+    f = ld_volatile_u32(flag);
+  }
+  if (f == 0 && threadIdx.x == 0) atomicOr(status, kErrTimeout);
+}
+
 int host_grid(int64_t work, int per_block, int cap) {
   int64_t g = (work + per_block - 1) / per_block;
   if (g < 1) g = 1;
@@ -1271,6 +1285,10 @@ void launch_pairset_insert(const PairSetArgs& a, int num_sms, cudaStream_t s) {
 
 void launch_triangles(const TriangleArgs& a, int num_sms, cudaStream_t s) {
   k_triangles<<<num_sms * 8, kBlock, 0, s>>>(a);
+}
+
+void launch_wait_flag(const uint32_t* flag, uint32_t* status, cudaStream_t s) {
+  k_wait_flag<<<1, 32, 0, s>>>(flag, status);
 }
 
 void launch_sum_terms(const SumTermsArgs& a, int num_sms, cudaStream_t s) {

@@ -195,6 +195,7 @@ struct SumTermsArgs {
   unsigned long long* result;  // [2] += sum
 };
 void launch_sum_terms(const SumTermsArgs& a, int num_sms, cudaStream_t s);
+void launch_wait_flag(const uint32_t* flag, uint32_t* status, cudaStream_t s);
 
 // ------------------------------------------------------------------ cyclic query
 // Edge pairs are packed (src << 32) | dst.  The pair filter uses the
