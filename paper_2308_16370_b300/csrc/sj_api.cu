@@ -29,6 +29,8 @@ constexpr int kMiscNuniq = 6;    // uint32 distinct-key counter in the low half
 constexpr int kMiscSteps = 8;    // [8 .. 8 + kMaxSlots) per-step row counts
 constexpr int kMaxSlots = 120;
 constexpr int kMiscWords = kMiscSteps + kMaxSlots;
+// sieve steps over at most this many tiles use the one-pass look-back kernel
+constexpr int64_t kLookBackMaxTiles = 64;
 
 struct ProfRec {
   int kind;
@@ -379,44 +381,60 @@ sj_status sieve_step_timed(sj_ctx* c, const sj_rel_s* in, const std::vector<Test
   }
   a.n_host = in->d_n ? 0 : in->nrows;
   a.n_dev = in->d_n;
-  // two passes: each tile compacts into its slot of a gapped buffer, then the
-  // move kernel packs the slots in order (no tile waits for another)
   const int64_t ntiles = (cap + kSieveTile - 1) / kSieveTile;
-  const size_t gcol = round_up((size_t)std::max<int64_t>(cap, 1) * 4);
-  const size_t gbytes = gcol * (size_t)in->ncols + round_up((size_t)std::max<int64_t>(ntiles, 1) * 4);
-  uint8_t* gap = static_cast<uint8_t*>(dalloc(c, gbytes));
-  if (!gap) {
-    free_rel(c, r);
-    return fail(c, SJ_ENOMEM, "sieve staging allocation failed");
-  }
-  SieveMoveArgs m;
-  memset(&m, 0, sizeof(m));
-  for (int j = 0; j < in->ncols; ++j) {
-    a.out[j] = reinterpret_cast<int32_t*>(gap + gcol * j);
-    m.gap[j] = a.out[j];
-    m.out[j] = r->cols[j];
-  }
-  a.tile_cnt = reinterpret_cast<uint32_t*>(gap + gcol * in->ncols);
-  m.nout = in->ncols;
-  m.tile = kSieveTile;
-  m.tile_cnt = a.tile_cnt;
-  m.n_host = a.n_host;
-  m.n_dev = a.n_dev;
-  m.out_n = r->d_n;
-  m.out_n2 = slot >= 0 ? c->d_misc + kMiscSteps + slot : nullptr;
   // algorithmic bytes: the first tested column of every input row; each kept
   // row's other columns read and all of its columns written
   const int nvec = tests.empty() ? 0 : 1;
   const double per_in = 4.0 * nvec;
   const double per_out = 4.0 * (in->ncols - nvec) + 4.0 * in->ncols;
-  {
+  sj_status st = SJ_OK;
+  if (ntiles <= kLookBackMaxTiles) {
+    // few tiles: one pass with a decoupled look-back (short chains, one launch)
+    for (int j = 0; j < in->ncols; ++j) a.out[j] = r->cols[j];
+    a.out_n = r->d_n;
+    a.out_n2 = slot >= 0 ? c->d_misc + kMiscSteps + slot : nullptr;
+    st = scratch_for<1>(c, ntiles, &a.tile_counter, &a.lb);
+    if (st != SJ_OK) {
+      free_rel(c, r);
+      return st;
+    }
     Launch L = in->d_n ? Launch(c, SJ_K_SIEVE, 0, slot_in, per_in, slot, per_out)
                        : Launch(c, SJ_K_SIEVE, per_in * (double)in->nrows, slot, per_out);
-    c->launches++;  // two kernels
-    launch_sieve_two_pass(a, m, cap, c->stream);
+    launch_sieve(a, cap, c->stream);
+  } else {
+    // many tiles: two passes -- each tile compacts into its slot of a gapped
+    // buffer, then the move kernel packs the slots in order; no tile waits
+    // for another, which matters when hundreds of tiles are in flight
+    const size_t gcol = round_up((size_t)std::max<int64_t>(cap, 1) * 4);
+    const size_t gbytes = gcol * (size_t)in->ncols + round_up((size_t)std::max<int64_t>(ntiles, 1) * 4);
+    uint8_t* gap = static_cast<uint8_t*>(dalloc(c, gbytes));
+    if (!gap) {
+      free_rel(c, r);
+      return fail(c, SJ_ENOMEM, "sieve staging allocation failed");
+    }
+    SieveMoveArgs m;
+    memset(&m, 0, sizeof(m));
+    for (int j = 0; j < in->ncols; ++j) {
+      a.out[j] = reinterpret_cast<int32_t*>(gap + gcol * j);
+      m.gap[j] = a.out[j];
+      m.out[j] = r->cols[j];
+    }
+    a.tile_cnt = reinterpret_cast<uint32_t*>(gap + gcol * in->ncols);
+    m.nout = in->ncols;
+    m.tile = kSieveTile;
+    m.tile_cnt = a.tile_cnt;
+    m.n_host = a.n_host;
+    m.n_dev = a.n_dev;
+    m.out_n = r->d_n;
+    m.out_n2 = slot >= 0 ? c->d_misc + kMiscSteps + slot : nullptr;
+    {
+      Launch L = in->d_n ? Launch(c, SJ_K_SIEVE, 0, slot_in, per_in, slot, per_out)
+                         : Launch(c, SJ_K_SIEVE, per_in * (double)in->nrows, slot, per_out);
+      c->launches++;  // two kernels
+      launch_sieve_two_pass(a, m, cap, c->stream);
+    }
+    dfree(c, gap, gbytes);
   }
-  dfree(c, gap, gbytes);
-  sj_status st = SJ_OK;
   st = check_launch(c, "k_sieve_local/k_sieve_move");
   if (st != SJ_OK) {
     free_rel(c, r);

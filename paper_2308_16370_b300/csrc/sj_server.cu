@@ -163,12 +163,8 @@ void run_query(sj_server* s, int w, const Pending& p, sj_completion* c) {
   o.passes = s->opts.passes;
   o.filter = s->opts.filter;
   o.leaf_filters = s->opts.cache_filters ? leaf : nullptr;
-  sj_rel sieved[SJ_MAX_REL] = {};
-  sj_status st = sj_sieve_path(ctx, &path, &o, sieved, nullptr);
   sj_result res{};
-  if (st == SJ_OK) st = sj_join(ctx, &path, sieved, SJ_COUNT_SUM, q.nterms, q.terms, &res);
-  for (int i = 0; i < q.nrel; ++i)
-    if (sieved[i]) sj_free_rel(ctx, sieved[i]);
+  const sj_status st = sj_sieve_join(ctx, &path, &o, SJ_COUNT_SUM, q.nterms, q.terms, &res, nullptr);
   c->status = st;
   c->count = res.count;
   c->sum = res.sum;
