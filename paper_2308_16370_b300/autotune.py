@@ -1,0 +1,104 @@
+"""Autotuner for the sieved join: filter size (bits per key), hash count k,
+filter layout and sieve schedule.
+
+The paper fixes none of these (Sec. 2.1 sizes Bloomjoin's filter at one bit
+per tuple; Sec. 2.2 leaves the second pruning pass optional).  The tuner times
+``Context.sieve_join`` for each candidate with CUDA events on the context's
+stream, checks that every candidate returns the identical exact result (the
+pruning never changes the join), and keeps the fastest.  Results are cached
+in a JSON file keyed by (GPU name, query shape, size bucket), so a later run of
+a query of the same shape and size class reuses the choice without timing.
+"""
+from __future__ import annotations
+
+import itertools
+import json
+import math
+import os
+
+from . import BLOCKED256, BWD_ONLY, FWD_BWD, REGBLOCKED32
+
+DEFAULT_CANDIDATES = {
+    "bits_per_key": (6, 8, 12),
+    "k": (2, 3, 4),
+    "layout": (REGBLOCKED32, BLOCKED256),
+    "passes": (FWD_BWD, BWD_ONLY),
+}
+
+
+def cache_path() -> str:
+    return os.environ.get("SIEVEJOIN_AUTOTUNE_CACHE",
+                          os.path.join(os.path.expanduser("~"), ".cache", "sievejoin", "autotune.json"))
+
+
+def shape_key(gpu: str, rels, edges, root) -> str:
+    """(GPU, query shape, size bucket): relations, edges and root, and the
+    total row count rounded to a power of two."""
+    total = sum(r.nrows for r in rels)
+    bucket = int(math.ceil(math.log2(max(total, 1))))
+    return json.dumps([gpu, len(rels), [list(map(int, e)) for e in edges], int(root), bucket])
+
+
+def _load(path):
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store(path, data):
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    tmp = f"{path}.tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(data, f, indent=1)
+    os.replace(tmp, path)
+
+
+def tune(ctx, rels, edges, preds=None, root=-1, refs=(), candidates=None, reps=3,
+         use_cache=True, path=None):
+    """Return {"params": {...}, "ms": best, "timings": [...], "cached": bool}.
+
+    ``params`` holds bits_per_key, k, layout and passes for ``sieve_join``.
+    """
+    import torch
+    path = path or cache_path()
+    gpu = torch.cuda.get_device_name(ctx.device)
+    key = shape_key(gpu, rels, edges, root)
+    cache = _load(path) if use_cache else {}
+    if use_cache and key in cache:
+        return {**cache[key], "cached": True}
+    cand = dict(DEFAULT_CANDIDATES)
+    cand.update(candidates or {})
+    timings = []
+    reference = None
+    stream = ctx.stream
+    for bpk, k, layout, passes in itertools.product(cand["bits_per_key"], cand["k"],
+                                                    cand["layout"], cand["passes"]):
+        if layout == BLOCKED256 and k > 4:
+            continue
+        kw = dict(bits_per_key=bpk, k=k, layout=layout, passes=passes)
+        res = ctx.sieve_join(rels, edges, preds, root, refs=refs, **kw)  # warm-up
+        got = (res["count"], res["sum"])
+        if reference is None:
+            reference = got
+        elif got != reference:
+            raise RuntimeError(f"candidate {kw} changed the join result: {got} != {reference}")
+        ts = []
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            ctx.sieve_join(rels, edges, preds, root, refs=refs, **kw)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        timings.append({"params": kw, "ms": sorted(ts)[len(ts) // 2]})
+    best = min(timings, key=lambda t: t["ms"])
+    out = {"params": best["params"], "ms": best["ms"], "timings": timings}
+    if use_cache:
+        cache = _load(path)
+        cache[key] = out
+        _store(path, cache)
+    return {**out, "cached": False}
