@@ -70,6 +70,9 @@ def parse():
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--no-cyclic", action="store_true", help="skip the triangle-query run")
     ap.add_argument("--no-star", action="store_true", help="skip the star-join run")
+    ap.add_argument("--filter-params", default=None,
+                    help="bits_per_key,k,layout,passes: fixed parameters (no default-parameter "
+                         "timing, no tuning), e.g. for profiling the tuned path")
     ap.add_argument("--no-tune", action="store_true",
                     help="use the default filter parameters (8 bits/key, k=3, register-blocked, "
                          "forward+backward) instead of autotuning them")
@@ -470,10 +473,15 @@ def main():
 
     # default-parameter step time, then the autotuner (bits per key, k, layout,
     # schedule), whose choice the timed region uses
-    dms, _ = timed(torch, stream, lambda: sieved_step(ctx, rels, w), 20, 3, flush, ws)
-    default_ms = max_over_ranks(dms, ws) / 20
+    default_ms = None
     tune_info = None
-    if not args.no_tune:
+    if args.filter_params:
+        bpk, k, layout, passes = (int(x) for x in args.filter_params.split(","))
+        TUNED.update(bits_per_key=bpk, k=k, layout=layout, passes=passes)
+    else:
+        dms, _ = timed(torch, stream, lambda: sieved_step(ctx, rels, w), 20, 3, flush, ws)
+        default_ms = max_over_ranks(dms, ws) / 20
+    if not args.no_tune and not args.filter_params:
         from paper_2308_16370_b300 import autotune
         tr = autotune.tune(ctx, rels, w["edges"], w["preds"], w["root"], w["sum"], reps=3,
                            use_cache=False)
