@@ -58,6 +58,20 @@ __device__ __forceinline__ uint32_t reg32_mask(uint32_t hlo, uint32_t k) {
   return m;
 }
 
+// Compile-time-k variants (the hot loops dispatch on k once per tile).
+template <int K>
+__device__ __forceinline__ uint32_t reg32_mask_k(uint32_t hlo) {
+  uint32_t m = 0;
+#pragma unroll
+  for (int i = 0; i < K; ++i) m |= 1u << ((hlo >> (5 * i)) & 31u);
+  return m;
+}
+
+// Word index when the filter has fewer than 2^32 words: one high multiply.
+__device__ __forceinline__ uint32_t reg32_word32(uint64_t h, uint32_t nwords) {
+  return __umulhi((uint32_t)(h >> 32), nwords);
+}
+
 __device__ __forceinline__ bool bit_of4(uint64_t q0, uint64_t q1, uint64_t q2, uint64_t q3,
                                         uint32_t bit) {
   const uint32_t i = bit >> 6;

@@ -139,16 +139,16 @@ __device__ __forceinline__ void bloom_insert_reg4(const BloomBuildArgs& a, uint6
 constexpr int kBuildVecs = 2;
 constexpr int kBuildKeys = 4 * kBuildVecs;
 
-__device__ __forceinline__ void bloom_insert_regN(const BloomBuildArgs& a, uint64_t nb,
+template <int K>
+__device__ __forceinline__ void bloom_insert_regN(const BloomBuildArgs& a, uint32_t nwords,
                                                   const int32_t (&key)[kBuildKeys], uint32_t live,
                                                   unsigned long long* seen) {
   uint32_t w[kBuildKeys], cur[kBuildKeys], m[kBuildKeys];
-  const uint64_t nwords = nb * 8;
 #pragma unroll
   for (int j = 0; j < kBuildKeys; ++j) {
     const uint64_t h = key_hash(key[j], a.seed);
-    w[j] = (uint32_t)reg32_word(h, nwords);
-    m[j] = reg32_mask((uint32_t)h, a.k);
+    w[j] = reg32_word32(h, nwords);
+    m[j] = K > 0 ? reg32_mask_k<(K > 0 ? K : 1)>((uint32_t)h) : reg32_mask((uint32_t)h, a.k);
   }
 #pragma unroll
   for (int j = 0; j < kBuildKeys; ++j) cur[j] = __ldca(a.words + w[j]);
@@ -174,6 +174,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_bloom_build(BloomBuildArgs a) {
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int4* kv = reinterpret_cast<const int4*>(a.keys);
   if (a.layout == 0 && nb * 8 < (1ull << 32)) {
+    const uint32_t nwords = (uint32_t)(nb * 8);
     // rounds of kBuildKeys keys per thread: vector v of a round is key vector
     // base + v * stride, so every warp load is one contiguous 512 B
     const int64_t nvec = (n + 3) >> 2;
@@ -201,7 +202,11 @@ __global__ void __launch_bounds__(kBlock, 3) k_bloom_build(BloomBuildArgs a) {
           }
         }
       }
-      bloom_insert_regN(a, nb, k16, live, s_seen);
+      switch (a.k) {
+        case 3: bloom_insert_regN<3>(a, nwords, k16, live, s_seen); break;
+        case 4: bloom_insert_regN<4>(a, nwords, k16, live, s_seen); break;
+        default: bloom_insert_regN<0>(a, nwords, k16, live, s_seen); break;
+      }
     }
     return;
   }
@@ -281,6 +286,34 @@ __device__ __forceinline__ uint32_t test_reg32(const SieveTest& t, uint64_t nb, 
   return pass & live;
 }
 
+// Register-blocked probe with k and a 32-bit word count fixed at compile
+// time: the word index is one high multiply and the mask k shift-ors.
+template <int NK, int K>
+__device__ __forceinline__ uint32_t test_reg32_k(const SieveTest& t, uint32_t nwords,
+                                                 const int32_t* key, uint32_t live) {
+  uint32_t hlo[NK], w[NK];
+#pragma unroll
+  for (int j = 0; j < NK; ++j) {
+    const uint64_t h = key_hash(key[j], t.f.seed);
+    hlo[j] = (uint32_t)h;
+    w[j] = __ldg(t.f.words + (((live >> j) & 1u) ? reg32_word32(h, nwords) : 0u));
+  }
+  uint32_t pass = 0;
+#pragma unroll
+  for (int j = 0; j < NK; ++j) {
+    const uint32_t m = reg32_mask_k<K>(hlo[j]);
+    pass |= ((w[j] & m) == m) ? (1u << j) : 0u;
+  }
+  return pass & live;
+}
+
+template <int K>
+__device__ __forceinline__ uint32_t test16_reg32_k(const SieveTest& t, uint32_t nwords,
+                                                   const int32_t* key, uint32_t live) {
+  return test_reg32_k<8, K>(t, nwords, key, live & 0xffu) |
+         (test_reg32_k<8, K>(t, nwords, key + 8, live >> 8) << 8);
+}
+
 template <int NK>
 __device__ __forceinline__ uint32_t test_blocked(const SieveTest& t, uint64_t nb, const int32_t* key,
                                                  uint32_t live) {
@@ -320,6 +353,16 @@ __device__ __forceinline__ uint32_t test16(const SieveTest& t, const int32_t* ke
   if (t.is_pred) return test_pred<16>(t, key, live);
   const uint64_t nb = __ldg(t.f.hdr);
   if (t.f.layout == 0) {
+    if (nb * 8 < (1ull << 32)) {
+      const uint32_t nw = (uint32_t)(nb * 8);
+      switch (t.f.k) {
+        case 1: return test16_reg32_k<1>(t, nw, key, live);
+        case 2: return test16_reg32_k<2>(t, nw, key, live);
+        case 3: return test16_reg32_k<3>(t, nw, key, live);
+        case 4: return test16_reg32_k<4>(t, nw, key, live);
+        default: break;
+      }
+    }
     return test_reg32<8>(t, nb, key, live & 0xffu) | (test_reg32<8>(t, nb, key + 8, live >> 8) << 8);
   }
   if (t.f.layout == 1) {
@@ -986,6 +1029,9 @@ __device__ __forceinline__ void add128(U128& x, uint64_t lo, uint64_t hi) {
   x.lo = nl;
 }
 
+// One probe row per thread and iteration: the table is small and cache
+// resident here, so occupancy (32 registers, 8 CTAs per SM) hides latency
+// better than batching rows per thread.
 __global__ void __launch_bounds__(kBlock) k_agg_probe(AggProbeArgs a) {
   __shared__ uint64_t s_red[3][kBlock / 32];
   U128 cnt = {0, 0};
