@@ -31,6 +31,11 @@ constexpr int kMaxSlots = 120;
 constexpr int kMiscWords = kMiscSteps + kMaxSlots;
 // sieve steps over at most this many tiles use the one-pass look-back kernel
 constexpr int64_t kLookBackMaxTiles = 64;
+// internal status: a device-sized join outgrew a buffer and must be rerun
+constexpr sj_status kRetry = 100;
+// d_misc words of the device-sized join: per-level totals and output counts
+constexpr int kMiscLevelTotals = kMiscSteps + 96;  // 2 words per level, 8 levels
+constexpr int kMiscLevelCount = kMiscSteps + 112;  // 1 word per level
 
 struct ProfRec {
   int kind;
@@ -56,6 +61,9 @@ struct sj_ctx {
   size_t scratch_bytes = 0;
   uint32_t epoch = 0;  // look-back flag epoch of the last scan launch
   cudaEvent_t ev_wait = nullptr;  // host waits on one point of the stream
+  // per query shape: output tuples of each join level in the last exact run,
+  // used to size the buffers of the device-sized (host-sync-free) join
+  std::map<uint64_t, std::vector<uint64_t>> plan_caps;
   // per-call arena (sj_sieve_join): temporaries are bump-allocated from one
   // device block and released together, instead of one allocator call each
   struct {
@@ -268,6 +276,7 @@ sj_status sync_read(sj_ctx* c) {
     SJ_CUDA(c, cudaMemsetAsync(c->d_misc + kMiscStatus, 0, sizeof(uint64_t), c->stream));
     if (st & kErrTimeout) return fail(c, SJ_ETIMEOUT, "a bounded device wait timed out");
     if (st & kErrTableFull) return fail(c, SJ_ETABLEFULL, "hash table probe chain exhausted");
+    if (st == kErrCapacity) return kRetry;  // a device-sized buffer was too small
     return fail(c, SJ_ECUDA, "device status word set");
   }
   return SJ_OK;
@@ -825,8 +834,24 @@ sj_status sj_sieve(sj_ctx* c, sj_rel rel, int nprobe, const int* key_cols, const
   return SJ_OK;
 }
 
-sj_status sj_sieve_path(sj_ctx* c, const sj_path* path, const sj_sieve_opts* opts, sj_rel* out_sieved,
-                        sj_sieve_stats* stats) {
+}  // extern "C"
+
+namespace {
+sj_status sieve_path_impl(sj_ctx* c, const sj_path* path, const sj_sieve_opts* opts, sj_rel* out_sieved,
+                          sj_sieve_stats* stats, bool sync_end);
+}
+
+extern "C" sj_status sj_sieve_path(sj_ctx* c, const sj_path* path, const sj_sieve_opts* opts,
+                                   sj_rel* out_sieved, sj_sieve_stats* stats) {
+  return sieve_path_impl(c, path, opts, out_sieved, stats, true);
+}
+
+namespace {
+// The pruning phase.  With sync_end the call ends with one synchronisation and
+// every output handle knows its row count; without it the outputs keep their
+// counts on the device only (nrows = -1) for a device-sized join to read.
+sj_status sieve_path_impl(sj_ctx* c, const sj_path* path, const sj_sieve_opts* opts, sj_rel* out_sieved,
+                          sj_sieve_stats* stats, bool sync_end) {
   if (!c || !path || !out_sieved) return fail(c, SJ_EINVAL, "null argument");
   Tree tr;
   SJ_TRY(validate_path(c, path, path->rels, &tr));
@@ -914,22 +939,23 @@ sj_status sj_sieve_path(sj_ctx* c, const sj_path* path, const sj_sieve_opts* opt
       }
     }
   }
-  if (st == SJ_OK) st = sync_read(c);
+  if (st == SJ_OK && sync_end) st = sync_read(c);
   if (st != SJ_OK) {
     cleanup();
     return st;
   }
-  prof_resolve(c, p0);
+  if (sync_end) prof_resolve(c, p0);
   for (auto f : filters) free_filter(c, f);
   filters.clear();
   for (int i = 0; i < n; ++i) {
     if (cur[i]) {
-      cur[i]->nrows = (int64_t)c->h_misc[kMiscSteps + last_slot[i]];
+      cur[i]->nrows = sync_end ? (int64_t)c->h_misc[kMiscSteps + last_slot[i]] : -1;
       out_sieved[i] = cur[i];
     } else {
       out_sieved[i] = view_of(path->rels[i]);
     }
   }
+  if (!sync_end) return SJ_OK;
   if (stats) {
     memset(stats, 0, sizeof(*stats));
     stats->nsteps = (int)steps.size();
@@ -947,7 +973,7 @@ sj_status sj_sieve_path(sj_ctx* c, const sj_path* path, const sj_sieve_opts* opt
   return SJ_OK;
 }
 
-}  // extern "C"
+}  // namespace
 
 // ======================================================================== join
 namespace {
@@ -1077,8 +1103,18 @@ sj_status build_adjacency(sj_ctx* c, Temps& tmp, const int32_t* keys, int64_t n,
 
 }  // namespace
 
+sj_status join_impl(sj_ctx* c, const sj_path* path, const sj_rel* inputs, int mode, int nrefs,
+                    const sj_colref* refs, sj_result* result, std::vector<uint64_t>* levelT);
+
 extern "C" sj_status sj_join(sj_ctx* c, const sj_path* path, const sj_rel* inputs, int mode,
                              int nrefs, const sj_colref* refs, sj_result* result) {
+  return join_impl(c, path, inputs, mode, nrefs, refs, result, nullptr);
+}
+
+// The enumeration phase with host-known sizes (one synchronisation per level);
+// `levelT` (optional) receives the output tuples of every multimap level.
+sj_status join_impl(sj_ctx* c, const sj_path* path, const sj_rel* inputs, int mode, int nrefs,
+                    const sj_colref* refs, sj_result* result, std::vector<uint64_t>* levelT) {
   if (!c || !path || !result) return fail(c, SJ_EINVAL, "null argument");
   Tree tr;
   SJ_TRY(validate_path(c, path, path->rels, &tr));
@@ -1346,6 +1382,7 @@ extern "C" sj_status sj_join(sj_ctx* c, const sj_path* path, const sj_rel* input
           }
       }
     }
+    if (levelT) levelT->push_back(T);
     const int32_t* rows = G.rows;
     const uint64_t* off = G.off;
     if (!last) intermediate += T;
@@ -1458,6 +1495,292 @@ extern "C" sj_status sj_join(sj_ctx* c, const sj_path* path, const sj_rel* input
   result->intermediate = intermediate;
   return SJ_OK;
 }
+
+// ======================================================================== device-sized join
+namespace {
+
+struct AsyncInter {
+  std::map<ColKey, const int32_t*> cols;
+  const uint64_t* n_dev = nullptr;  // null: n_host is the row count
+  int64_t n_host = 0;
+  int64_t cap = 0;                  // rows allocated
+  const uint64_t* psum = nullptr;
+  bool base = true;
+};
+
+// Multimap build whose row count may be known on the device only: the table
+// is allocated for `cap` rows and sized and cleared by k_table_init.
+sj_status build_adjacency_dev(sj_ctx* c, Temps& tmp, const int32_t* keys, const uint64_t* n_dev,
+                              int64_t n_host, int64_t cap, uint32_t* mask, uint32_t* nuniq,
+                              Adjacency* g) {
+  sj_status st = SJ_OK;
+  const int64_t capn = std::max<int64_t>(cap, 1);
+  const uint64_t cap_slots = pow2_at_least(std::max<uint64_t>(64, 2 * (uint64_t)capn));
+  unsigned long long* slots = tmp.get<unsigned long long>(cap_slots, &st);
+  uint32_t* cnt = tmp.get<uint32_t>(capn, &st);
+  uint32_t* rid = tmp.get<uint32_t>(capn, &st);
+  uint32_t* rank = tmp.get<uint32_t>(capn, &st);
+  uint64_t* off = tmp.get<uint64_t>(capn, &st);
+  int32_t* rows = tmp.get<int32_t>(capn, &st);
+  if (st != SJ_OK) return fail(c, st, "adjacency allocation failed");
+  TableInitArgs ti{slots, mask, n_dev, n_host, nullptr, nullptr, cnt, nuniq};
+  {
+    Launch L(c, SJ_K_HT_BUILD, 0.0);
+    launch_table_init(ti, (int64_t)cap_slots, c->num_sms, c->stream);
+  }
+  SJ_TRY(check_launch(c, "k_table_init"));
+  Table t;
+  t.slots = slots;
+  t.bucket_mask = 0;
+  t.mask_dev = mask;
+  MMInsertArgs mi{keys, cap, t, nuniq, cnt, rid, rank, status_ptr(c)};
+  mi.n_dev = n_dev;
+  if (!n_dev) mi.n = n_host;
+  {
+    Launch L(c, SJ_K_HT_BUILD, 12.0 * (double)cap);
+    launch_mm_insert(mi, c->num_sms, c->stream);
+  }
+  SJ_TRY(check_launch(c, "k_mm_insert"));
+  ScanArgs sa;
+  sa.in = cnt;
+  sa.out = off;
+  sa.n_host = 0;
+  sa.n_dev = nuniq;
+  sa.total = nullptr;
+  SJ_TRY(scratch_for<1>(c, (capn + kScanTile - 1) / kScanTile, &sa.tile_counter, &sa.lb));
+  {
+    Launch L(c, SJ_K_HT_BUILD, 12.0 * (double)cap);
+    launch_scan_u32(sa, capn, c->stream);
+  }
+  SJ_TRY(check_launch(c, "k_scan_u32"));
+  MMScatterArgs ms{rid, rank, off, n_dev ? cap : n_host, rows};
+  ms.n_dev = n_dev;
+  {
+    Launch L(c, SJ_K_HT_BUILD, 20.0 * (double)cap);
+    launch_mm_scatter(ms, c->num_sms, c->stream);
+  }
+  SJ_TRY(check_launch(c, "k_mm_scatter"));
+  g->t = t;
+  g->cnt = cnt;
+  g->off = off;
+  g->rows = rows;
+  return SJ_OK;
+}
+
+// COUNT/SUM join with every size kept on the device: no host round trip
+// until the one synchronisation at the end.  caps[L] bounds the output of
+// multimap level L; a level that outgrows it records kErrCapacity and the call
+// returns kRetry (the caller reruns the exact, synchronising join).
+sj_status join_async(sj_ctx* c, const sj_path* path, const sj_rel* in_rels, int nrefs,
+                     const sj_colref* refs, const std::vector<uint64_t>& caps, sj_result* result,
+                     std::vector<uint64_t>* levelT) {
+  const int n = path->nrel;
+  std::vector<const sj_rel_s*> rels(in_rels, in_rels + n);
+  const std::vector<LevelPlan> plan = join_order(path);
+  if (plan.size() != caps.size() + 1) return kRetry;
+  const bool want_sum = nrefs > 0;
+  Temps keep(c);
+  sj_status st = SJ_OK;
+  uint32_t* small = keep.get<uint32_t>(64, &st);
+  if (st != SJ_OK) return fail(c, st, "allocation failed");
+  SJ_CUDA(c, cudaMemsetAsync(c->d_misc + kMiscResult, 0, 3 * 8, c->stream));
+  AsyncInter in;
+  for (int col = 0; col < rels[0]->ncols; ++col) in.cols[{0, col}] = rels[0]->cols[col];
+  in.n_dev = rels[0]->d_n;
+  in.n_host = rels[0]->nrows;
+  in.cap = rel_cap(rels[0]);
+  std::vector<int> joined(n, 0);
+  joined[0] = 1;
+  Terms none;
+  memset(&none, 0, sizeof(none));
+  for (size_t L = 0; L < plan.size(); ++L) {
+    const LevelPlan& lp = plan[L];
+    const sj_rel_s* B = rels[lp.rel];
+    joined[lp.rel] = 1;
+    const int32_t* pk = in.cols.at({lp.probe_rel, lp.probe_col});
+    const int64_t capB = rel_cap(B);
+    if (L + 1 == plan.size()) {
+      // final level: per-key (count, sum) table on the side with the smaller capacity
+      const bool swap = in.cap < capB;
+      const Terms rel_terms = want_sum ? terms_of(B, lp.rel, nrefs, refs) : none;
+      const Terms base_terms = (want_sum && in.base) ? terms_of(rels[0], 0, nrefs, refs) : none;
+      const uint64_t* inter_vals = (want_sum && !in.base) ? in.psum : nullptr;
+      const int64_t cap_build = swap ? in.cap : capB;
+      const uint64_t cap_slots = pow2_at_least(std::max<uint64_t>(64, 2 * (uint64_t)std::max<int64_t>(cap_build, 1)));
+      unsigned long long* slots = keep.get<unsigned long long>(cap_slots, &st);
+      unsigned long long* cnt = keep.get<unsigned long long>(cap_slots, &st);
+      unsigned long long* sum = keep.get<unsigned long long>(cap_slots, &st);
+      if (st != SJ_OK) return fail(c, st, "aggregate table allocation failed");
+      TableInitArgs ti{slots, small + 2 * L, swap ? in.n_dev : B->d_n, swap ? in.n_host : B->nrows,
+                       cnt, sum, nullptr, nullptr};
+      {
+        Launch Lk(c, SJ_K_AGG, 0.0);
+        launch_table_init(ti, (int64_t)cap_slots, c->num_sms, c->stream);
+      }
+      SJ_TRY(check_launch(c, "k_table_init"));
+      Table t;
+      t.slots = slots;
+      t.bucket_mask = 0;
+      t.mask_dev = small + 2 * L;
+      AggInsertArgs ai;
+      ai.keys = swap ? pk : B->cols[lp.rel_col];
+      ai.n = swap ? (in.n_dev ? in.cap : in.n_host) : (B->d_n ? capB : B->nrows);
+      ai.n_dev = swap ? in.n_dev : B->d_n;
+      ai.t = t;
+      ai.terms = swap ? base_terms : rel_terms;
+      ai.vals = swap ? inter_vals : nullptr;
+      ai.cnt = cnt;
+      ai.sum = sum;
+      ai.status = status_ptr(c);
+      {
+        Launch Lk(c, SJ_K_AGG, 4.0 * (double)ai.n);
+        launch_agg_insert(ai, c->num_sms, c->stream);
+      }
+      SJ_TRY(check_launch(c, "k_agg_insert"));
+      AggProbeArgs ap;
+      ap.keys = swap ? B->cols[lp.rel_col] : pk;
+      ap.n = swap ? (B->d_n ? capB : B->nrows) : (in.n_dev ? in.cap : in.n_host);
+      ap.n_dev = swap ? B->d_n : in.n_dev;
+      ap.t = t;
+      ap.cnt = cnt;
+      ap.sum = sum;
+      ap.probe_terms = swap ? rel_terms : base_terms;
+      ap.psum_in = swap ? nullptr : inter_vals;
+      ap.result = reinterpret_cast<unsigned long long*>(c->d_misc + kMiscResult);
+      ap.status = status_ptr(c);
+      {
+        Launch Lk(c, SJ_K_AGG, 4.0 * (double)ap.n);
+        launch_agg_probe(ap, c->num_sms, c->stream);
+      }
+      SJ_TRY(check_launch(c, "k_agg_probe"));
+      break;
+    }
+    // ---- multimap level
+    Adjacency G{};
+    SJ_TRY(build_adjacency_dev(c, keep, B->cols[lp.rel_col], B->d_n, B->nrows, capB,
+                               small + 2 * L, small + 2 * L + 1, &G));
+    const int64_t capP = std::max<int64_t>(in.cap, 1);
+    int32_t* prow = keep.get<int32_t>(capP, &st);
+    int32_t* pid = keep.get<int32_t>(capP, &st);
+    uint64_t* o = keep.get<uint64_t>(capP, &st);
+    if (st != SJ_OK) return fail(c, st, "join level allocation failed");
+    uint64_t* totals = c->d_misc + kMiscLevelTotals + 2 * L;
+    MMProbeArgs mp;
+    mp.keys = pk;
+    mp.n = in.n_dev ? in.cap : in.n_host;
+    mp.n_dev = in.n_dev;
+    mp.t = G.t;
+    mp.cnt = G.cnt;
+    mp.prow = prow;
+    mp.pid = pid;
+    mp.o = o;
+    mp.totals = totals;
+    SJ_TRY(scratch_for<2>(c, (capP + kProbeTile - 1) / kProbeTile, &mp.tile_counter, &mp.lb));
+    {
+      Launch Lk(c, SJ_K_HT_PROBE, 4.0 * (double)mp.n);
+      launch_mm_probe(mp, c->stream);
+    }
+    SJ_TRY(check_launch(c, "k_mm_probe"));
+    std::map<ColKey, int> need;
+    for (size_t L2 = L + 1; L2 < plan.size(); ++L2)
+      if (joined[plan[L2].probe_rel]) need[{plan[L2].probe_rel, plan[L2].probe_col}] = 1;
+    std::vector<ColKey> carried;
+    for (auto& kv : need) carried.push_back(kv.first);
+    const uint64_t C = std::max<uint64_t>(caps[L], 1);
+    AsyncInter nx;
+    nx.base = false;
+    nx.cap = (int64_t)C;
+    nx.n_dev = c->d_misc + kMiscLevelCount + L;
+    for (auto& ck : carried) nx.cols[ck] = keep.get<int32_t>(C, &st);
+    uint64_t* psum_out = want_sum ? keep.get<uint64_t>(C, &st) : nullptr;
+    if (st != SJ_OK) return fail(c, st, "intermediate allocation failed");
+    nx.psum = psum_out;
+    const size_t ncar = carried.size();
+    for (size_t c0 = 0; c0 < std::max<size_t>(ncar, 1); c0 += kMaxCols) {
+      MMExpandArgs ex;
+      memset(&ex, 0, sizeof(ex));
+      ex.o = o;
+      ex.prow = prow;
+      ex.pid = pid;
+      ex.off = G.off;
+      ex.rows = G.rows;
+      const size_t c1 = std::min(ncar, c0 + kMaxCols);
+      for (size_t k = c0; k < c1; ++k) {
+        const ColKey ck = carried[k];
+        const int slot = (int)(k - c0);
+        ex.src_build[slot] = ck.first == lp.rel ? 1 : 0;
+        ex.src[slot] = ck.first == lp.rel ? B->cols[ck.second] : in.cols.at(ck);
+        ex.out[slot] = const_cast<int32_t*>(nx.cols[ck]);
+      }
+      ex.nout = (int)(c1 - c0);
+      if (c0 == 0 && want_sum) {
+        ex.psum_out = psum_out;
+        if (in.base) ex.probe_terms = terms_of(rels[0], 0, nrefs, refs);
+        else ex.psum_in = in.psum;
+        ex.build_terms = terms_of(B, lp.rel, nrefs, refs);
+      }
+      ex.totals_dev = totals;
+      ex.cap = C;
+      ex.n_out = c->d_misc + kMiscLevelCount + L;
+      ex.status = status_ptr(c);
+      {
+        Launch Lk(c, SJ_K_HT_EXPAND, 0.0);
+        launch_mm_expand_dev(ex, c->num_sms, c->stream);
+      }
+      SJ_TRY(check_launch(c, "k_mm_expand_dev"));
+    }
+    in = std::move(nx);
+  }
+  SJ_TRY(sync_read(c));
+  const uint64_t lo = c->h_misc[kMiscResult], hi = c->h_misc[kMiscResult + 1];
+  if (hi != 0 || lo >= (1ull << 63)) return fail(c, SJ_EOVERFLOW, "COUNT(*) reached 2^63");
+  memset(result, 0, sizeof(*result));
+  result->count = lo;
+  result->sum = c->h_misc[kMiscResult + 2];
+  for (size_t L = 0; L + 1 < plan.size(); ++L) {
+    const uint64_t T = c->h_misc[kMiscLevelTotals + 2 * L + 1];
+    result->intermediate += T;
+    if (levelT) levelT->push_back(T);
+  }
+  return SJ_OK;
+}
+
+uint64_t mix_in(uint64_t h, uint64_t v) {
+  h ^= v + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2);
+  return h;
+}
+
+// Signature of a query shape for the capacity cache.
+uint64_t path_signature(const sj_path* p, const sj_sieve_opts* o, int mode, int nrefs,
+                        const sj_colref* refs) {
+  uint64_t h = 0x51e7e70117ull;
+  h = mix_in(h, (uint64_t)p->nrel);
+  h = mix_in(h, (uint64_t)(int64_t)p->root);
+  for (int i = 0; i < p->nrel; ++i) {
+    h = mix_in(h, (uint64_t)reinterpret_cast<uintptr_t>(p->rels[i]));
+    h = mix_in(h, (uint64_t)p->rels[i]->nrows);
+    if (p->preds)
+      h = mix_in(h, ((uint64_t)(uint32_t)p->preds[i].col << 40) ^ ((uint64_t)(uint32_t)p->preds[i].lo << 20) ^
+                        (uint64_t)(uint32_t)p->preds[i].hi);
+  }
+  for (int e = 0; e + 1 < p->nrel; ++e)
+    h = mix_in(h, ((uint64_t)p->edges[e].rel_a << 48) ^ ((uint64_t)p->edges[e].col_a << 32) ^
+                      ((uint64_t)p->edges[e].rel_b << 16) ^ (uint64_t)p->edges[e].col_b);
+  if (o) {
+    h = mix_in(h, (uint64_t)o->passes);
+    h = mix_in(h, ((uint64_t)o->filter.bits_per_key << 32) ^ ((uint64_t)o->filter.k << 8) ^ o->filter.layout);
+    h = mix_in(h, o->filter.seed);
+    if (o->leaf_filters)
+      for (int i = 0; i < p->nrel; ++i)
+        h = mix_in(h, (uint64_t)reinterpret_cast<uintptr_t>(o->leaf_filters[i]));
+  }
+  h = mix_in(h, (uint64_t)mode);
+  for (int k = 0; k < nrefs; ++k)
+    h = mix_in(h, ((uint64_t)refs[k].rel << 32) ^ ((uint64_t)refs[k].col << 8) ^ (uint64_t)refs[k].wide);
+  return h;
+}
+
+}  // namespace
 
 // ======================================================================== profiling
 extern "C" {
@@ -1677,11 +2000,49 @@ extern "C" sj_status sj_sieve_join(sj_ctx* c, const sj_path* path, const sj_siev
                                    int mode, int nrefs, const sj_colref* refs, sj_result* result,
                                    sj_sieve_stats* stats) {
   if (!c || !path || !result) return fail(c, SJ_EINVAL, "null argument");
-  if (path->nrel < 1 || path->nrel > SJ_MAX_REL) return fail(c, SJ_EINVAL, "nrel out of range");
+  if (path->nrel < 1 || path->nrel > SJ_MAX_REL || !path->rels) return fail(c, SJ_EINVAL, "bad path");
+  for (int i = 0; i < path->nrel; ++i)
+    if (!path->rels[i] || path->rels[i]->nrows < 0) return fail(c, SJ_EINVAL, "bad relation handle");
   sj_rel sieved[SJ_MAX_REL] = {};
+  const uint64_t sig = path_signature(path, opts, mode, nrefs, refs);
+  auto it = c->plan_caps.find(sig);
+  const bool device_sized = mode == SJ_COUNT_SUM && path->nrel >= 2 && !stats && it != c->plan_caps.end();
+  std::vector<uint64_t> T;
   arena_begin(c);
-  sj_status st = sj_sieve_path(c, path, opts, sieved, stats);
-  if (st == SJ_OK) st = sj_join(c, path, sieved, mode, nrefs, refs, result);
+  sj_status st;
+  if (device_sized) {
+    // sizes stay on the device: one synchronisation for the whole query
+    std::vector<uint64_t> caps;
+    for (uint64_t t : it->second) caps.push_back(2 * t + 4096);
+    const size_t p0 = c->prof.size();
+    st = sieve_path_impl(c, path, opts, sieved, nullptr, false);
+    if (st == SJ_OK) st = join_async(c, path, sieved, nrefs, refs, caps, result, &T);
+    if (st == SJ_OK) prof_resolve(c, p0);
+    if (st == kRetry) {
+      // an intermediate outgrew its buffer: take the sizes to the host and rerun
+      // the enumeration exactly
+      T.clear();
+      st = SJ_OK;
+      prof_resolve(c, p0);
+      for (int i = 0; i < path->nrel && st == SJ_OK; ++i) {
+        if (sieved[i] && sieved[i]->d_n && sieved[i]->nrows < 0) {
+          uint64_t v = 0;
+          if (cudaMemcpyAsync(&v, sieved[i]->d_n, 8, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+              cudaStreamSynchronize(c->stream) != cudaSuccess)
+            st = fail(c, SJ_ECUDA, "row count readback failed");
+          sieved[i]->nrows = (int64_t)v;
+        }
+      }
+      if (st == SJ_OK) st = join_impl(c, path, sieved, mode, nrefs, refs, result, &T);
+    }
+  } else {
+    st = sieve_path_impl(c, path, opts, sieved, stats, true);
+    if (st == SJ_OK) st = join_impl(c, path, sieved, mode, nrefs, refs, result, &T);
+  }
+  if (st == SJ_OK && mode == SJ_COUNT_SUM && path->nrel >= 2) {
+    if (c->plan_caps.size() > 4096) c->plan_caps.clear();
+    c->plan_caps[sig] = T;
+  }
   for (int i = 0; i < path->nrel; ++i) free_rel(c, sieved[i]);
   arena_end(c);
   return st;

@@ -14,6 +14,7 @@ namespace sj {
 constexpr uint32_t kErrTimeout = 1u;
 constexpr uint32_t kErrTableFull = 2u;
 constexpr uint32_t kErrOverflow = 4u;
+constexpr uint32_t kErrCapacity = 8u;  // a device-sized output outgrew its buffer
 
 // Spin bound for look-back / pending-slot waits: ~2^22 polls with a growing
 // nanosleep backoff (capped at 256 ns), i.e. about a second at most.

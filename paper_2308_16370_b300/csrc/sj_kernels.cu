@@ -24,6 +24,16 @@ __device__ __forceinline__ uint32_t table_bucket(int32_t key, uint32_t mask) {
   return (uint32_t)fmix64((uint64_t)(uint32_t)key ^ kTableSeed) & mask;
 }
 
+// A table whose mask was written on the device (k_table_init) reads it once.
+__device__ __forceinline__ Table resolve(Table t) {
+  if (t.mask_dev) t.bucket_mask = __ldg(t.mask_dev);
+  return t;
+}
+
+__device__ __forceinline__ int64_t dev_n(const uint64_t* n_dev, int64_t n_host) {
+  return n_dev ? (int64_t)__ldg(n_dev) : n_host;
+}
+
 // Sum of the SUM terms of one row, int64 arithmetic mod 2^64.  The loop has a
 // constant trip count so the kernel-parameter arrays are indexed statically.
 __device__ __forceinline__ uint64_t term_sum(const Terms& t, int64_t row) {
@@ -797,6 +807,8 @@ __device__ __forceinline__ int64_t table_find(const Table& t, int32_t key) {
 }
 
 __global__ void __launch_bounds__(kBlock) k_mm_insert(MMInsertArgs a) {
+  a.t = resolve(a.t);
+  a.n = dev_n(a.n_dev, a.n);
   const int lane = threadIdx.x & 31;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   // every lane of a warp runs the same number of iterations (warp-collective match)
@@ -820,6 +832,7 @@ __global__ void __launch_bounds__(kBlock) k_mm_insert(MMInsertArgs a) {
 }
 
 __global__ void __launch_bounds__(kBlock) k_mm_scatter(MMScatterArgs a) {
+  a.n = dev_n(a.n_dev, a.n);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride)
     a.rows[__ldg(a.off + __ldg(a.rid + i)) + __ldg(a.rank + i)] = (int32_t)i;
@@ -833,9 +846,16 @@ __global__ void __launch_bounds__(kBlock) k_mm_probe(MMProbeArgs a) {
   if (tid == 0) s_tile = draw_ticket(a.tile_counter);
   __syncthreads();
   const uint32_t tile = s_tile;
-  const int64_t n = a.n;
+  a.t = resolve(a.t);
+  const int64_t n = dev_n(a.n_dev, a.n);
   const int64_t ntiles = (n + kProbeTile - 1) / kProbeTile;
-  if ((int64_t)tile >= ntiles) return;
+  if ((int64_t)tile >= ntiles) {
+    if (tile == 0 && tid == 0) {
+      a.totals[0] = 0;
+      a.totals[1] = 0;
+    }
+    return;
+  }
   const int64_t base = (int64_t)tile * kProbeTile;
   int32_t id[8];
   uint32_t m[8];
@@ -965,6 +985,52 @@ __global__ void __launch_bounds__(kBlock) k_mm_expand(MMExpandArgs a) {
   }
 }
 
+// Device-sized expand: T and Q come from the probe's totals on the device;
+// outputs beyond `cap` are not written and the overflow is reported, so the
+// host can rerun the level with an exact buffer.
+__global__ void __launch_bounds__(kBlock) k_mm_expand_dev(MMExpandArgs a) {
+  const uint64_t Q = __ldg(a.totals_dev);
+  const uint64_t T = __ldg(a.totals_dev + 1);
+  const uint64_t lim = T < a.cap ? T : a.cap;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *a.n_out = lim;
+    if (T > a.cap) atomicOr(a.status, kErrCapacity);
+  }
+  const uint64_t stride = (uint64_t)gridDim.x * kBlock;
+  for (uint64_t j = (uint64_t)blockIdx.x * kBlock + threadIdx.x; j < lim; j += stride) {
+    const uint64_t q = upper_q(a.o, 0, Q - 1, j);
+    const uint64_t t = j - __ldg(a.o + q);
+    const int32_t prow = __ldg(a.prow + q);
+    const int32_t brow = __ldg(a.rows + __ldg(a.off + __ldg(a.pid + q)) + t);
+#pragma unroll
+    for (int c = 0; c < kMaxCols; ++c)
+      if (c < a.nout) a.out[c][j] = __ldg(a.src[c] + (a.src_build[c] ? brow : prow));
+    if (a.psum_out) {
+      const uint64_t ps = a.psum_in ? __ldg(a.psum_in + prow) : term_sum(a.probe_terms, prow);
+      a.psum_out[j] = ps + term_sum(a.build_terms, brow);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_table_init(TableInitArgs a) {
+  const int64_t n = dev_n(a.n_dev, a.n_host);
+  uint64_t nslots = 64;
+  while (nslots < 2 * (uint64_t)n) nslots <<= 1;
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  if (gid == 0) {
+    *a.mask_out = (uint32_t)(nslots / 4 - 1);
+    if (a.zero32) *a.zero32 = 0;
+  }
+  for (int64_t i = gid; i < (int64_t)nslots; i += stride) {
+    a.slots[i] = 0ull;
+    if (a.per_slot0) a.per_slot0[i] = 0ull;
+    if (a.per_slot1) a.per_slot1[i] = 0ull;
+  }
+  if (a.cnt)
+    for (int64_t i = gid; i < n; i += stride) a.cnt[i] = 0u;
+}
+
 // ---------------------------------------------------------------- aggregate level
 __device__ __forceinline__ int64_t agg_find_or_insert(const Table& t, int32_t key,
                                                       uint32_t* status) {
@@ -988,6 +1054,8 @@ __device__ __forceinline__ int64_t agg_find_or_insert(const Table& t, int32_t ke
 }
 
 __global__ void __launch_bounds__(kBlock) k_agg_insert(AggInsertArgs a) {
+  a.t = resolve(a.t);
+  a.n = dev_n(a.n_dev, a.n);
   const int lane = threadIdx.x & 31;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t first = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31);
@@ -1034,6 +1102,8 @@ __device__ __forceinline__ void add128(U128& x, uint64_t lo, uint64_t hi) {
 // better than batching rows per thread.
 __global__ void __launch_bounds__(kBlock) k_agg_probe(AggProbeArgs a) {
   __shared__ uint64_t s_red[3][kBlock / 32];
+  a.t = resolve(a.t);
+  a.n = dev_n(a.n_dev, a.n);
   U128 cnt = {0, 0};
   uint64_t sum = 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -1311,6 +1381,14 @@ void launch_mm_probe(const MMProbeArgs& a, cudaStream_t s) {
 
 void launch_mm_expand(const MMExpandArgs& a, cudaStream_t s) {
   k_mm_expand<<<host_grid((int64_t)a.T, kBlock, 1 << 30), kBlock, 0, s>>>(a);
+}
+
+void launch_mm_expand_dev(const MMExpandArgs& a, int num_sms, cudaStream_t s) {
+  k_mm_expand_dev<<<num_sms * 8, kBlock, 0, s>>>(a);
+}
+
+void launch_table_init(const TableInitArgs& a, int64_t cap_slots, int num_sms, cudaStream_t s) {
+  k_table_init<<<host_grid(cap_slots, kBlock * 8, num_sms * 8), kBlock, 0, s>>>(a);
 }
 
 void launch_agg_insert(const AggInsertArgs& a, int num_sms, cudaStream_t s) {

@@ -100,8 +100,24 @@ void launch_scan_u32(const ScanArgs& a, int64_t n_upper, cudaStream_t s);
 // 32-byte sector).  A slot is 0 when empty, else (tag << 32) | uint32(key).
 struct Table {
   unsigned long long* slots;
-  uint32_t bucket_mask;  // nbuckets - 1, nbuckets a power of two
+  uint32_t bucket_mask;                // nbuckets - 1, nbuckets a power of two
+  const uint32_t* mask_dev = nullptr;  // if set: the mask, written on the device by k_table_init
 };
+
+// Device-side sizing of a table (k_table_init): nslots = power of two >= max(64, 2n)
+// for the n read from n_dev, mask written to *mask_out, slots (and the
+// optional per-slot arrays) zeroed up to nslots, cnt zeroed up to n, *zero32 = 0.
+struct TableInitArgs {
+  unsigned long long* slots;
+  uint32_t* mask_out;
+  const uint64_t* n_dev;
+  int64_t n_host;
+  unsigned long long* per_slot0;  // optional, nslots entries
+  unsigned long long* per_slot1;  // optional, nslots entries
+  uint32_t* cnt;                  // optional, n entries
+  uint32_t* zero32;               // optional counter to clear
+};
+void launch_table_init(const TableInitArgs& a, int64_t cap_slots, int num_sms, cudaStream_t s);
 
 struct MMInsertArgs {       // multimap build, pass 1: distinct keys and per-row rank
   const int32_t* keys;
@@ -112,6 +128,7 @@ struct MMInsertArgs {       // multimap build, pass 1: distinct keys and per-row
   uint32_t* rid;            // [n] row -> key id
   uint32_t* rank;           // [n] row -> rank among rows of its key
   uint32_t* status;
+  const uint64_t* n_dev = nullptr;  // device row count (overrides n)
 };
 void launch_mm_insert(const MMInsertArgs& a, int num_sms, cudaStream_t s);
 
@@ -121,6 +138,7 @@ struct MMScatterArgs {      // multimap build, pass 2: rows grouped by key id
   const uint64_t* off;
   int64_t n;
   int32_t* rows;
+  const uint64_t* n_dev = nullptr;
 };
 void launch_mm_scatter(const MMScatterArgs& a, int num_sms, cudaStream_t s);
 
@@ -135,6 +153,7 @@ struct MMProbeArgs {        // probe + compaction of matching probe rows
   uint64_t* totals;         // [0] = matching rows, [1] = output tuples
   uint32_t* tile_counter;
   LookBack<2> lb;
+  const uint64_t* n_dev = nullptr;
 };
 constexpr int kProbeTile = kBlock * 8;
 void launch_mm_probe(const MMProbeArgs& a, cudaStream_t s);
@@ -161,8 +180,16 @@ struct MMExpandArgs {       // one output tuple per (matching probe row, build r
   Terms probe_terms;
   Terms build_terms;
   uint64_t* psum_out;            // null: no SUM carried
+  // device-sized mode: Q and T from totals_dev, at most `cap` outputs written,
+  // min(T, cap) stored to *n_out, kErrCapacity recorded if T > cap
+  const uint64_t* totals_dev = nullptr;
+  uint64_t cap = 0;
+  uint64_t* n_out = nullptr;
+  uint32_t* status = nullptr;
 };
 void launch_mm_expand(const MMExpandArgs& a, cudaStream_t s);
+// Device-sized expand: grid-stride over T read on the device.
+void launch_mm_expand_dev(const MMExpandArgs& a, int num_sms, cudaStream_t s);
 
 struct AggInsertArgs {
   const int32_t* keys;
@@ -173,6 +200,7 @@ struct AggInsertArgs {
   unsigned long long* cnt;  // [nslots] zeroed
   unsigned long long* sum;  // [nslots] zeroed
   uint32_t* status;
+  const uint64_t* n_dev = nullptr;
 };
 void launch_agg_insert(const AggInsertArgs& a, int num_sms, cudaStream_t s);
 
@@ -186,6 +214,7 @@ struct AggProbeArgs {
   Terms probe_terms;
   unsigned long long* result;  // [0] count lo, [1] count hi, [2] sum; zeroed
   uint32_t* status;
+  const uint64_t* n_dev = nullptr;
 };
 void launch_agg_probe(const AggProbeArgs& a, int num_sms, cudaStream_t s);
 

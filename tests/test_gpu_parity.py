@@ -335,3 +335,59 @@ def test_sieve_join_one_call(ctx):
     exp = oracle.agg_propagation(w)
     assert (one["count"], one["sum"]) == (two["count"], two["sum"]) == (exp["count"], exp["sum"])
     assert one["steps"] == st["steps"]
+
+
+# ------------------------------------------- device-sized (one-sync) sieve_join
+DEVICE_SIZED_CASES = [
+    ("zipf", sj.FWD_BWD), ("zipf", sj.BWD_ONLY), ("uniform", sj.NO_SIEVE),
+    ("star", sj.FWD_BWD), ("tree", sj.FWD_BWD), ("tree", sj.BWD_ONLY),
+]
+
+
+@pytest.mark.parametrize("kind,passes", DEVICE_SIZED_CASES)
+def test_sieve_join_device_sized_repeat(ctx, kind, passes):
+    """A repeated query shape runs with every size kept on the device (buffers
+    sized from the previous run): the result stays exact every time."""
+    if kind == "zipf":
+        w = inputs.zipf_chain(nrows=200_000, domain=100_000, seed=21)
+    elif kind == "uniform":
+        w = inputs.uniform_chain(nrel=4, nrows=50_001, domain=20_000, seed=22)
+    elif kind == "star":
+        w = inputs.star(nfact=300_001, ndim=3, dim_rows=20_000, seed=23)
+    else:
+        g = np.random.default_rng(24)
+        w = inputs.random_tree_join(g, 6, g.integers(3000, 40_000, 6), 5000)
+    rels = load(ctx, w)
+    exp = oracle.agg_propagation(w)
+    for _ in range(3):
+        got = ctx.sieve_join(rels, w["edges"], w["preds"], w["root"], refs=w["sum"], passes=passes)
+        assert (got["count"], got["sum"]) == (exp["count"], exp["sum"])
+
+
+def test_sieve_join_device_sized_overflow_falls_back(ctx):
+    """Relations borrowed from device tensors are rewritten in place so the
+    intermediate result grows far beyond the buffers sized by the earlier run:
+    the device-sized join records the overflow and the call reruns exactly."""
+    import torch
+    g = np.random.default_rng(31)
+    n = 40_000
+    cols = [[g.integers(0, 1 << 20, n, dtype=np.int32) for _ in range(2)] for _ in range(3)]
+    dev = [[torch.from_numpy(c).cuda() for c in r] for r in cols]
+    rels = [ctx.load_relation(r, where="borrow") for r in dev]
+    w = {"rels": cols, "edges": inputs.chain_edges(3), "preds": [None] * 3, "root": 2,
+         "sum": [(0, 0, 0), (2, 1, 0)]}
+    for _ in range(2):
+        got = ctx.sieve_join(rels, w["edges"], w["preds"], w["root"], refs=w["sum"])
+        exp = oracle.agg_propagation(w)
+        assert (got["count"], got["sum"]) == (exp["count"], exp["sum"])
+    # every join key collapses to 64 values: the first level's output grows
+    # from ~n^2/2^20 to ~n^2/64 tuples
+    for r in range(3):
+        for j in range(2):
+            cols[r][j] = (cols[r][j] % 64).astype(np.int32)
+            dev[r][j].copy_(torch.from_numpy(cols[r][j]))
+    torch.cuda.synchronize()
+    exp = oracle.agg_propagation(w)
+    for _ in range(2):
+        got = ctx.sieve_join(rels, w["edges"], w["preds"], w["root"], refs=w["sum"])
+        assert (got["count"], got["sum"]) == (exp["count"], exp["sum"])
