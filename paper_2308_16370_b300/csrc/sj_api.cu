@@ -414,8 +414,11 @@ sj_status sieve_step_timed(sj_ctx* c, const sj_rel_s* in, const std::vector<Test
     // many tiles: two passes -- each tile compacts into its slot of a gapped
     // buffer, then the move kernel packs the slots in order; no tile waits
     // for another, which matters when hundreds of tiles are in flight
+    const int64_t nwt = (cap + kWarpRows - 1) / kWarpRows;
+    const int64_t nbt = (cap + kSieveBlockRows - 1) / kSieveBlockRows;
     const size_t gcol = round_up((size_t)std::max<int64_t>(cap, 1) * 4);
-    const size_t gbytes = gcol * (size_t)in->ncols + round_up((size_t)std::max<int64_t>(ntiles, 1) * 4);
+    const size_t tbytes = round_up((size_t)std::max<int64_t>(nwt, 1) * 4);
+    const size_t gbytes = gcol * (size_t)in->ncols + tbytes + round_up((size_t)std::max<int64_t>(nbt, 1) * 4);
     uint8_t* gap = static_cast<uint8_t*>(dalloc(c, gbytes));
     if (!gap) {
       free_rel(c, r);
@@ -429,9 +432,12 @@ sj_status sieve_step_timed(sj_ctx* c, const sj_rel_s* in, const std::vector<Test
       m.out[j] = r->cols[j];
     }
     a.tile_cnt = reinterpret_cast<uint32_t*>(gap + gcol * in->ncols);
+    a.block_cnt = reinterpret_cast<uint32_t*>(gap + gcol * in->ncols + tbytes);
+    a.fast_words_ok = 1;
+    if (!tests.empty() && !tests[0].is_pred && tests[0].f->nblocks_cap * 8 >= (1ull << 32)) a.fast_words_ok = 0;
     m.nout = in->ncols;
-    m.tile = kSieveTile;
     m.tile_cnt = a.tile_cnt;
+    m.block_cnt = a.block_cnt;
     m.n_host = a.n_host;
     m.n_dev = a.n_dev;
     m.out_n = r->d_n;
@@ -440,7 +446,7 @@ sj_status sieve_step_timed(sj_ctx* c, const sj_rel_s* in, const std::vector<Test
       Launch L = in->d_n ? Launch(c, SJ_K_SIEVE, 0, slot_in, per_in, slot, per_out)
                          : Launch(c, SJ_K_SIEVE, per_in * (double)in->nrows, slot, per_out);
       c->launches++;  // two kernels
-      launch_sieve_two_pass(a, m, cap, c->stream);
+      launch_sieve_two_pass(a, m, cap, c->num_sms, c->stream);
     }
     dfree(c, gap, gbytes);
   }

@@ -526,150 +526,233 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_sieve(SieveArgs a) {
   }
 }
 
-// Pass 1 of the two-pass sieve: the same tile work as k_sieve, but each tile
-// writes its survivors, compacted and in order, to its own slot of a gapped
-// buffer (rows tile*kTile ..) and its count to a.tile_cnt[tile].  No tile
-// waits for another, so probe-latency variance between tiles costs nothing.
-template <int NT>
-__global__ void __launch_bounds__(NT, 1024 / NT) k_sieve_local(SieveArgs a) {
-  constexpr int kTile = NT * 16;
-  __shared__ Vec<1> s_warp[NT / 32];
-  const int tid = threadIdx.x;
-  const uint32_t tile = blockIdx.x;
-  const int64_t n = a.n_dev ? (int64_t)(*a.n_dev) : a.n_host;
-  const int64_t ntiles = (n + kTile - 1) / kTile;
-  if ((int64_t)tile >= ntiles) return;
-  const int64_t base = (int64_t)tile * kTile;
-  const int32_t* vcol = a.ntest > 0 ? a.test[0].col : nullptr;
-
-  // 1. first test column: 4 coalesced 16-byte loads per thread
-  int32_t key[16];
-  uint32_t alive = 0;
-#pragma unroll
-  for (int v = 0; v < 4; ++v) {
-    const int64_t r0 = base + (int64_t)(v * NT + tid) * 4;
-    if (r0 + 4 <= n) {
-      if (vcol) {
-        const int4 x = __ldcs(reinterpret_cast<const int4*>(vcol + r0));
-        key[4 * v + 0] = x.x;
-        key[4 * v + 1] = x.y;
-        key[4 * v + 2] = x.z;
-        key[4 * v + 3] = x.w;
+// All 8 keys of a lane against one test (the 8-row counterpart of test16).
+template <int K>
+__device__ __forceinline__ uint32_t test8(const SieveTest& t, const int32_t* key, uint32_t live) {
+  if (K > 0) {
+    const uint32_t nw = (uint32_t)(__ldg(t.f.hdr) * 8);
+    return test_reg32_k<8, K>(t, nw, key, live);
+  }
+  if (t.is_pred) return test_pred<8>(t, key, live);
+  const uint64_t nb = __ldg(t.f.hdr);
+  if (t.f.layout == 0) {
+    if (nb * 8 < (1ull << 32)) {
+      const uint32_t nw = (uint32_t)(nb * 8);
+      switch (t.f.k) {
+        case 1: return test_reg32_k<8, 1>(t, nw, key, live);
+        case 2: return test_reg32_k<8, 2>(t, nw, key, live);
+        case 3: return test_reg32_k<8, 3>(t, nw, key, live);
+        case 4: return test_reg32_k<8, 4>(t, nw, key, live);
+        default: break;
       }
-      alive |= 0xfu << (4 * v);
-    } else {
+    }
+    return test_reg32<8>(t, nb, key, live);
+  }
+  if (t.f.layout == 1) {
+    uint32_t pass = 0;
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        key[4 * v + e] = 0;
-        if (r0 + e < n) {
-          if (vcol) key[4 * v + e] = __ldcs(vcol + r0 + e);
-          alive |= 1u << (4 * v + e);
+    for (int q = 0; q < 4; ++q)
+      pass |= test_blocked<2>(t, nb, key + 2 * q, (live >> (2 * q)) & 0x3u) << (2 * q);
+    return pass;
+  }
+  uint32_t pass = 0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+    if ((live >> j) & 1u) pass |= filter_contains(t.f, nb, key[j]) ? (1u << j) : 0u;
+  return pass;
+}
+
+// Pass 1 of the two-pass sieve.  Every warp owns a tile of kWarpRows rows
+// (8 per lane, two coalesced 16-byte loads per lane) and compacts its
+// survivors, in input order, into its own slot of a gapped buffer with a
+// warp-level scan only: no warp of the block waits for another.  The first
+// non-key output column of the survivors is loaded before the scan so that its
+// latency overlaps it.  The block's total goes to block_cnt (the move kernel's
+// prefix sums), written by whichever warp finishes last.
+// K > 0: exactly one test, a register-blocked filter with k = K (the hot path).
+template <int K>
+__global__ void __launch_bounds__(kSieveWarpBlock, K > 0 ? 6 : 4) k_sieve_warp(SieveArgs a) {
+  __shared__ uint32_t s_sum, s_done;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t n = a.n_dev ? (int64_t)(*a.n_dev) : a.n_host;
+  const int64_t bbase = (int64_t)blockIdx.x * kSieveBlockRows;
+  if (bbase >= n) return;
+  if (tid == 0) {
+    s_sum = 0;
+    s_done = 0;
+  }
+  __syncthreads();
+  const int64_t wt = (int64_t)blockIdx.x * (kSieveWarpBlock / 32) + warp;
+  const int64_t base = wt * kWarpRows;
+  uint32_t total = 0;
+  if (base < n) {
+    const int32_t* vcol = a.ntest > 0 ? a.test[0].col : nullptr;
+    int32_t key[8];
+    uint32_t alive = 0;
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      const int64_t r0 = base + (int64_t)(v * 32 + lane) * 4;
+      if (r0 + 4 <= n) {
+        if (vcol) {
+          const int4 x = __ldcs(reinterpret_cast<const int4*>(vcol + r0));
+          key[4 * v + 0] = x.x;
+          key[4 * v + 1] = x.y;
+          key[4 * v + 2] = x.z;
+          key[4 * v + 3] = x.w;
+        }
+        alive |= 0xfu << (4 * v);
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          key[4 * v + e] = 0;
+          if (r0 + e < n) {
+            if (vcol) key[4 * v + e] = __ldcs(vcol + r0 + e);
+            alive |= 1u << (4 * v + e);
+          }
         }
       }
     }
-  }
-
-  // 2. tests; later tests only load the rows still alive
-  if (a.ntest > 0) alive = test16(a.test[0], key, alive);
+    if (K > 0) {
+      alive = test8<K>(a.test[0], key, alive);
+    } else {
+      if (a.ntest > 0) alive = test8<0>(a.test[0], key, alive);
+#pragma unroll 1
+      for (int t = 1; t < a.ntest; ++t) {
+        if (!alive) break;
 #pragma unroll
-  for (int t = 1; t < kMaxTests; ++t) {
-    if (t < a.ntest && alive) {
-#pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const int64_t row = base + (int64_t)((i >> 2) * NT + tid) * 4 + (i & 3);
-        key[i] = ((alive >> i) & 1u) ? __ldcs(a.test[t].col + row) : 0;
+        for (int i = 0; i < 8; ++i) {
+          const int64_t row = base + (int64_t)((i >> 2) * 32 + lane) * 4 + (i & 3);
+          key[i] = ((alive >> i) & 1u) ? __ldcs(a.test[t].col + row) : 0;
+        }
+        alive = test8<0>(a.test[t], key, alive);
       }
-      alive = test16(a.test[t], key, alive);
+    }
+    // the first test column's values are reloaded for output if tests overwrote them
+    const bool keys_valid = a.ntest <= 1;
+    // the first column not served from the key registers: loaded now
+    int pf = -1;
+    for (int j = 0; j < a.nout; ++j)
+      if (!(a.out_is_vec[j] && keys_valid)) {
+        pf = j;
+        break;
+      }
+    int32_t pay[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int64_t row = base + (int64_t)((i >> 2) * 32 + lane) * 4 + (i & 3);
+      pay[i] = (pf >= 0 && ((alive >> i) & 1u)) ? __ldcs(a.in[pf] + row) : 0;
+    }
+    // warp scan of the survivor counts of the two 4-row chunks (8 bits each)
+    const uint32_t c = (uint32_t)__popc(alive & 0xfu) | ((uint32_t)__popc(alive >> 4) << 8);
+    uint32_t inc = c;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, inc, d);
+      if (lane >= d) inc += y;
+    }
+    const uint32_t tot = __shfl_sync(0xffffffffu, inc, 31);
+    const uint32_t ex = inc - c;
+    const uint32_t tot0 = tot & 0xffu;
+    total = tot0 + (tot >> 8);
+    if (lane == 0) a.tile_cnt[wt] = total;
+    const uint64_t prefix = (uint64_t)wt * kWarpRows;
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      const uint32_t bits = (alive >> (4 * v)) & 0xfu;
+      if (!bits) continue;
+      const uint64_t pos0 = prefix + (v ? tot0 : 0u) + ((ex >> (8 * v)) & 0xffu);
+      const int64_t r0 = base + (int64_t)(v * 32 + lane) * 4;
+      for (int j = 0; j < a.nout; ++j) {
+        int32_t val[4];
+        if (a.out_is_vec[j] && keys_valid) {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) val[e] = key[4 * v + e];
+        } else if (j == pf) {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) val[e] = pay[4 * v + e];
+        } else {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) val[e] = ((bits >> e) & 1u) ? __ldcs(a.in[j] + r0 + e) : 0;
+        }
+        int32_t* dst = a.out[j] + pos0;
+        int k = 0;
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          if ((bits >> e) & 1u) dst[k++] = val[e];
+      }
     }
   }
-  // the first test column's values are reloaded for output if tests overwrote them
-  const bool keys_valid = a.ntest <= 1;
-
-  // 3. block scan of the survivor counts of the 4 chunks (16 bits each)
-  Vec<1> cnt;
-  cnt.v[0] = 0;
-#pragma unroll
-  for (int v = 0; v < 4; ++v) cnt.v[0] |= (uint64_t)__popc((alive >> (4 * v)) & 0xfu) << (16 * v);
-  Vec<1> tot;
-  const Vec<1> ex = block_exclusive_scan<1, NT>(cnt, &tot, s_warp);
-  uint64_t chunk_off[4];
-  uint64_t tile_total = 0;
-#pragma unroll
-  for (int v = 0; v < 4; ++v) {
-    chunk_off[v] = tile_total;
-    tile_total += (tot.v[0] >> (16 * v)) & 0xffffull;
-  }
-
-  // 4. this tile's slot of the gapped buffer
-  if (tid == 0) a.tile_cnt[tile] = (uint32_t)tile_total;
-  const uint64_t prefix = (uint64_t)tile * kTile;
-
-  // 5. write the survivors of every output column, in input order
-#pragma unroll
-  for (int v = 0; v < 4; ++v) {
-    const uint32_t bits = (alive >> (4 * v)) & 0xfu;
-    if (!bits) continue;
-    const uint64_t pos0 = prefix + chunk_off[v] + ((ex.v[0] >> (16 * v)) & 0xffffull);
-    const int64_t r0 = base + (int64_t)(v * NT + tid) * 4;
-#pragma unroll
-    for (int j = 0; j < kMaxCols; ++j) {
-      if (j >= a.nout) break;
-      int32_t val[4];
-      if (a.out_is_vec[j] && keys_valid) {
-#pragma unroll
-        for (int e = 0; e < 4; ++e) val[e] = key[4 * v + e];
-      } else if (r0 + 4 <= n) {
-        const int4 x = __ldcs(reinterpret_cast<const int4*>(a.in[j] + r0));
-        val[0] = x.x;
-        val[1] = x.y;
-        val[2] = x.z;
-        val[3] = x.w;
-      } else {
-#pragma unroll
-        for (int e = 0; e < 4; ++e) val[e] = ((bits >> e) & 1u) ? __ldcs(a.in[j] + r0 + e) : 0;
-      }
-      int32_t* dst = a.out[j] + pos0;
-      int k = 0;
-#pragma unroll
-      for (int e = 0; e < 4; ++e)
-        if ((bits >> e) & 1u) dst[k++] = val[e];
-    }
+  if (lane == 0) {
+    atomicAdd(&s_sum, total);
+    __threadfence_block();
+    if (atomicAdd(&s_done, 1u) == kSieveWarpBlock / 32 - 1) a.block_cnt[blockIdx.x] = atomicAdd(&s_sum, 0u);
   }
 }
 
-
-// Pass 2: move every tile's survivors from its gapped slot to the dense
-// output.  Block t sums the counts of tiles 0..t-1 (a few KB from L2) and
-// copies its tile's rows; the block of the last tile writes the total.
+// Pass 2: move every warp tile's survivors from its gapped slot to the dense
+// output.  Block b owns a contiguous range of pass-1 blocks: it sums the
+// block totals before its range (a few KB from L2), scans its warp tiles'
+// counts 256 at a time, and then each thread moves output rows tid,
+// tid + 256, ... of the chunk, finding the source tile by binary search over
+// the chunk's offsets, so a chunk's loads are all in flight together.  The
+// owner of the last tile writes the total.
 __global__ void __launch_bounds__(kBlock) k_sieve_move(SieveMoveArgs a) {
+  constexpr int kGroup = kSieveWarpBlock / 32;  // warp tiles per pass-1 block
   __shared__ uint64_t s_red[kBlock / 32];
+  __shared__ Vec<1> s_warp[kBlock / 32];
+  __shared__ uint32_t s_off[kBlock];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t n = a.n_dev ? (int64_t)(*a.n_dev) : a.n_host;
-  const int64_t ntiles = (n + a.tile - 1) / a.tile;
-  const int64_t t = blockIdx.x;
-  if (ntiles == 0 && t == 0 && threadIdx.x == 0) {
-    *a.out_n = 0;
-    if (a.out_n2) *a.out_n2 = 0;
+  const int64_t ntiles = (n + kWarpRows - 1) / kWarpRows;
+  const int64_t nblk = (n + kSieveBlockRows - 1) / kSieveBlockRows;
+  if (ntiles == 0) {
+    if (blockIdx.x == 0 && tid == 0) {
+      *a.out_n = 0;
+      if (a.out_n2) *a.out_n2 = 0;
+    }
+    return;
   }
-  if (t >= ntiles) return;
+  const int64_t per = (nblk + gridDim.x - 1) / gridDim.x;
+  const int64_t b0 = (int64_t)blockIdx.x * per;
+  const int64_t b1 = b0 + per < nblk ? b0 + per : nblk;
+  if (b0 >= b1) return;
   uint64_t part = 0;
-  for (int64_t u = threadIdx.x; u < t; u += kBlock) part += __ldg(a.tile_cnt + u);
+  for (int64_t u = tid; u < b0; u += kBlock) part += __ldg(a.block_cnt + u);
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) part += __shfl_xor_sync(0xffffffffu, part, d);
-  if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = part;
+  if (lane == 0) s_red[warp] = part;
   __syncthreads();
   uint64_t prefix = 0;
 #pragma unroll
   for (int w = 0; w < kBlock / 32; ++w) prefix += s_red[w];
-  const uint32_t cnt = __ldg(a.tile_cnt + t);
-  if (t == ntiles - 1 && threadIdx.x == 0) {
-    *a.out_n = prefix + cnt;
-    if (a.out_n2) *a.out_n2 = prefix + cnt;
+  const int64_t t0 = b0 * kGroup;
+  const int64_t t1 = b1 * kGroup < ntiles ? b1 * kGroup : ntiles;
+  for (int64_t c0 = t0; c0 < t1; c0 += kBlock) {
+    const int64_t j = c0 + tid;
+    const uint32_t cnt = j < t1 ? __ldg(a.tile_cnt + j) : 0u;
+    Vec<1> x, tot;
+    x.v[0] = cnt;
+    const Vec<1> ex = block_exclusive_scan<1, kBlock>(x, &tot, s_warp);
+    s_off[tid] = (uint32_t)ex.v[0];  // chunk-relative: at most 256 * kWarpRows
+    __syncthreads();
+    const int m = (int)(t1 - c0 < kBlock ? t1 - c0 : kBlock);
+    const uint32_t rows = (uint32_t)tot.v[0];
+    for (uint32_t r = tid; r < rows; r += kBlock) {
+      int lo = 0, hi = m - 1;  // last tile whose offset is <= r
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_off[mid] <= r) lo = mid;
+        else hi = mid - 1;
+      }
+      const uint64_t src = (uint64_t)(c0 + lo) * kWarpRows + (r - s_off[lo]);
+      for (int col = 0; col < a.nout; ++col) a.out[col][prefix + r] = __ldcs(a.gap[col] + src);
+    }
+    prefix += rows;
+    __syncthreads();  // s_off reused by the next chunk
   }
-  const uint64_t src0 = (uint64_t)t * a.tile;
-  for (int c = 0; c < a.nout; ++c) {
-    const int32_t* src = a.gap[c] + src0;
-    int32_t* dst = a.out[c] + prefix;
-    for (uint32_t i = threadIdx.x; i < cnt; i += kBlock) dst[i] = __ldcs(src + i);
+  if (t1 == ntiles && tid == 0) {
+    *a.out_n = prefix;
+    if (a.out_n2) *a.out_n2 = prefix;
   }
 }
 
@@ -1356,11 +1439,24 @@ void launch_sieve(const SieveArgs& a, int64_t n_upper, cudaStream_t s) {
   k_sieve<kSieveThreads><<<host_grid(n_upper, kSieveTile, 1 << 30), kSieveThreads, 0, s>>>(a);
 }
 
-void launch_sieve_two_pass(const SieveArgs& a, const SieveMoveArgs& m, int64_t n_upper,
+void launch_sieve_two_pass(const SieveArgs& a, const SieveMoveArgs& m, int64_t n_upper, int num_sms,
                            cudaStream_t s) {
-  const int g = host_grid(n_upper, kSieveTile, 1 << 30);
-  k_sieve_local<kSieveThreads><<<g, kSieveThreads, 0, s>>>(a);
-  k_sieve_move<<<g, kBlock, 0, s>>>(m);
+  const int g = host_grid(n_upper, kSieveBlockRows, 1 << 30);
+  // the hot instance: one register-blocked filter test with k <= 4 (k is
+  // known on the host; the 32-bit word count is checked on the device)
+  const bool fast = a.ntest == 1 && !a.test[0].is_pred && a.test[0].f.layout == 0 &&
+                    a.test[0].f.k >= 1 && a.test[0].f.k <= 4 && a.fast_words_ok;
+  if (!fast) {
+    k_sieve_warp<0><<<g, kSieveWarpBlock, 0, s>>>(a);
+  } else {
+    switch (a.test[0].f.k) {
+      case 1: k_sieve_warp<1><<<g, kSieveWarpBlock, 0, s>>>(a); break;
+      case 2: k_sieve_warp<2><<<g, kSieveWarpBlock, 0, s>>>(a); break;
+      case 3: k_sieve_warp<3><<<g, kSieveWarpBlock, 0, s>>>(a); break;
+      default: k_sieve_warp<4><<<g, kSieveWarpBlock, 0, s>>>(a); break;
+    }
+  }
+  k_sieve_move<<<g < 4 * num_sms ? g : 4 * num_sms, kBlock, 0, s>>>(m);
 }
 
 void launch_scan_u32(const ScanArgs& a, int64_t n_upper, cudaStream_t s) {

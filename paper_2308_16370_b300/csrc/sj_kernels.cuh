@@ -55,16 +55,18 @@ struct SieveArgs {
   uint64_t* out_n2;       // optional second copy (per-step statistics), or null
   uint32_t* tile_counter; // 0 at launch (reset by the kernel for the next one)
   LookBack<1> lb;
-  uint32_t* tile_cnt;     // two-pass sieve: survivors per tile
+  uint32_t* tile_cnt;     // two-pass sieve: survivors per warp tile
+  uint32_t* block_cnt;    // two-pass sieve: survivors per pass-1 block
+  int32_t fast_words_ok;  // filter word count of test 0 is below 2^32
 };
 
 // Pass 2 of the two-pass sieve (see k_sieve_move).
 struct SieveMoveArgs {
-  const int32_t* gap[kMaxCols];   // gapped pass-1 output, kSieveTile rows per tile slot
+  const int32_t* gap[kMaxCols];   // gapped pass-1 output, kWarpRows rows per tile slot
   int32_t* out[kMaxCols];
   int nout;
-  int64_t tile;
   const uint32_t* tile_cnt;
+  const uint32_t* block_cnt;
   int64_t n_host;
   const uint64_t* n_dev;
   uint64_t* out_n;
@@ -76,10 +78,14 @@ struct SieveMoveArgs {
 #endif
 constexpr int kSieveThreads = SJ_SIEVE_THREADS;
 constexpr int kSieveTile = kSieveThreads * 16;
+// Two-pass sieve: warp tiles of 32 lanes x 8 rows, 8 warps per block.
+constexpr int kWarpRows = 256;
+constexpr int kSieveWarpBlock = 256;
+constexpr int kSieveBlockRows = kWarpRows * (kSieveWarpBlock / 32);
 void launch_sieve(const SieveArgs& a, int64_t n_upper, cudaStream_t s);
 // Two-pass variant: pass 1 writes each tile's survivors to a gapped buffer
 // (a.out) and its count to a.tile_cnt; pass 2 compacts them into m.out.
-void launch_sieve_two_pass(const SieveArgs& a, const SieveMoveArgs& m, int64_t n_upper,
+void launch_sieve_two_pass(const SieveArgs& a, const SieveMoveArgs& m, int64_t n_upper, int num_sms,
                            cudaStream_t s);
 
 // ------------------------------------------------------------------ scans
