@@ -25,7 +25,6 @@ inline size_t round_up(size_t x, size_t a = kAlign) { return (x + a - 1) / a * a
 constexpr int kMiscStatus = 0;   // uint32 status bits in the low half
 constexpr int kMiscResult = 1;   // [1..3] count lo, count hi, sum
 constexpr int kMiscTotals = 4;   // [4..5] matching probe rows, output tuples
-constexpr int kMiscNuniq = 6;    // uint32 distinct-key counter in the low half
 constexpr int kMiscSteps = 8;    // [8 .. 8 + kMaxSlots) per-step row counts
 constexpr int kMaxSlots = 120;
 constexpr int kMiscWords = kMiscSteps + kMaxSlots;
@@ -1061,22 +1060,21 @@ sj_status make_table(sj_ctx* c, Temps& tmp, int64_t nrows, Table2* out) {
   return SJ_OK;
 }
 
-// Multimap of row ids keyed by `keys` (the same build as a join level):
-// distinct keys get dense ids, rows are grouped by key id.
+// Multimap of row ids keyed by `keys` (the same build as a join level): rows
+// are grouped by the table slot of their key.
 sj_status build_adjacency(sj_ctx* c, Temps& tmp, const int32_t* keys, int64_t n, Adjacency* g) {
   sj_status st = SJ_OK;
   Table2 tb;
   SJ_TRY(make_table(c, tmp, n, &tb));
-  uint32_t* cnt = tmp.get<uint32_t>(n, &st);
+  const int64_t ns = (int64_t)tb.nslots;
+  uint32_t* cnt = tmp.get<uint32_t>(ns, &st);
   uint32_t* rid = tmp.get<uint32_t>(n, &st);
   uint32_t* rank = tmp.get<uint32_t>(n, &st);
-  uint64_t* off = tmp.get<uint64_t>(n, &st);
+  uint64_t* off = tmp.get<uint64_t>(ns, &st);
   int32_t* rows = tmp.get<int32_t>(n, &st);
   if (st != SJ_OK) return fail(c, st, "adjacency allocation failed");
-  SJ_CUDA(c, cudaMemsetAsync(cnt, 0, (size_t)n * 4, c->stream));
-  SJ_CUDA(c, cudaMemsetAsync(c->d_misc + kMiscNuniq, 0, 8, c->stream));
-  uint32_t* nuniq = reinterpret_cast<uint32_t*>(c->d_misc + kMiscNuniq);
-  MMInsertArgs mi{keys, n, tb.t, nuniq, cnt, rid, rank, status_ptr(c)};
+  SJ_CUDA(c, cudaMemsetAsync(cnt, 0, (size_t)ns * 4, c->stream));
+  MMInsertArgs mi{keys, n, tb.t, cnt, rid, rank, status_ptr(c)};
   {
     Launch L(c, SJ_K_HT_BUILD, 12.0 * (double)n);
     launch_mm_insert(mi, c->num_sms, c->stream);
@@ -1085,13 +1083,13 @@ sj_status build_adjacency(sj_ctx* c, Temps& tmp, const int32_t* keys, int64_t n,
   ScanArgs sa;
   sa.in = cnt;
   sa.out = off;
-  sa.n_host = 0;
-  sa.n_dev = nuniq;
+  sa.n_host = ns;
+  sa.n_dev = nullptr;
   sa.total = nullptr;
-  SJ_TRY(scratch_for<1>(c, (n + kScanTile - 1) / kScanTile, &sa.tile_counter, &sa.lb));
+  SJ_TRY(scratch_for<1>(c, (ns + kScanTile - 1) / kScanTile, &sa.tile_counter, &sa.lb));
   {
-    Launch L(c, SJ_K_HT_BUILD, 12.0 * (double)n);
-    launch_scan_u32(sa, n, c->stream);
+    Launch L(c, SJ_K_HT_BUILD, 12.0 * (double)ns);
+    launch_scan_u32(sa, ns, c->num_sms, c->stream);
   }
   SJ_TRY(check_launch(c, "k_scan_u32"));
   MMScatterArgs ms{rid, rank, off, n, rows};
@@ -1262,14 +1260,12 @@ sj_status join_impl(sj_ctx* c, const sj_path* path, const sj_rel* inputs, int mo
       const int64_t n_build = swap ? np : nb;
       Table2 tb;
       if ((st = make_table(c, tmp, n_build, &tb)) != SJ_OK) break;
-      unsigned long long* cnt = tmp.get<unsigned long long>(tb.nslots, &st);
-      unsigned long long* sum = tmp.get<unsigned long long>(tb.nslots, &st);
+      ulonglong2* cs = tmp.get<ulonglong2>(tb.nslots, &st);
       if (st != SJ_OK) {
         fail(c, st, "aggregate table allocation failed");
         break;
       }
-      cudaMemsetAsync(cnt, 0, tb.nslots * 8, c->stream);
-      cudaMemsetAsync(sum, 0, tb.nslots * 8, c->stream);
+      cudaMemsetAsync(cs, 0, tb.nslots * 16, c->stream);
       cudaMemsetAsync(c->d_misc + kMiscResult, 0, 3 * 8, c->stream);
       Terms none;
       memset(&none, 0, sizeof(none));
@@ -1282,8 +1278,7 @@ sj_status join_impl(sj_ctx* c, const sj_path* path, const sj_rel* inputs, int mo
       ai.t = tb.t;
       ai.terms = swap ? base_terms : rel_terms;
       ai.vals = swap ? inter_vals : nullptr;
-      ai.cnt = cnt;
-      ai.sum = sum;
+      ai.cs = cs;
       ai.status = status_ptr(c);
       {
         Launch Lk(c, SJ_K_AGG, (4.0 + 4.0 * ai.terms.n + (ai.vals ? 8.0 : 0.0)) * (double)n_build);
@@ -1294,8 +1289,7 @@ sj_status join_impl(sj_ctx* c, const sj_path* path, const sj_rel* inputs, int mo
       ap.keys = swap ? B->cols[lp.rel_col] : pk;
       ap.n = swap ? nb : np;
       ap.t = tb.t;
-      ap.cnt = cnt;
-      ap.sum = sum;
+      ap.cs = cs;
       ap.probe_terms = swap ? rel_terms : base_terms;
       ap.psum_in = swap ? nullptr : inter_vals;
       ap.result = reinterpret_cast<unsigned long long*>(c->d_misc + kMiscResult);
@@ -1360,7 +1354,7 @@ sj_status join_impl(sj_ctx* c, const sj_path* path, const sj_rel* inputs, int mo
         break;
       {
         Launch Lk(c, SJ_K_HT_PROBE, 4.0 * (double)np);
-        launch_mm_probe(mp, c->stream);
+        launch_mm_probe(mp, c->num_sms, c->stream);
       }
       if ((st = check_launch(c, "k_mm_probe")) != SJ_OK) break;
       // read the level's totals at an event, and let the next level's table
@@ -1517,19 +1511,19 @@ struct AsyncInter {
 // Multimap build whose row count may be known on the device only: the table
 // is allocated for `cap` rows and sized and cleared by k_table_init.
 sj_status build_adjacency_dev(sj_ctx* c, Temps& tmp, const int32_t* keys, const uint64_t* n_dev,
-                              int64_t n_host, int64_t cap, uint32_t* mask, uint32_t* nuniq,
+                              int64_t n_host, int64_t cap, uint32_t* mask, uint32_t* nslots_dev,
                               Adjacency* g) {
   sj_status st = SJ_OK;
   const int64_t capn = std::max<int64_t>(cap, 1);
   const uint64_t cap_slots = pow2_at_least(std::max<uint64_t>(64, 2 * (uint64_t)capn));
   unsigned long long* slots = tmp.get<unsigned long long>(cap_slots, &st);
-  uint32_t* cnt = tmp.get<uint32_t>(capn, &st);
+  uint32_t* cnt = tmp.get<uint32_t>(cap_slots, &st);
   uint32_t* rid = tmp.get<uint32_t>(capn, &st);
   uint32_t* rank = tmp.get<uint32_t>(capn, &st);
-  uint64_t* off = tmp.get<uint64_t>(capn, &st);
+  uint64_t* off = tmp.get<uint64_t>(cap_slots, &st);
   int32_t* rows = tmp.get<int32_t>(capn, &st);
   if (st != SJ_OK) return fail(c, st, "adjacency allocation failed");
-  TableInitArgs ti{slots, mask, n_dev, n_host, nullptr, nullptr, cnt, nuniq};
+  TableInitArgs ti{slots, mask, n_dev, n_host, nullptr, cnt, nslots_dev};
   {
     Launch L(c, SJ_K_HT_BUILD, 0.0);
     launch_table_init(ti, (int64_t)cap_slots, c->num_sms, c->stream);
@@ -1539,7 +1533,7 @@ sj_status build_adjacency_dev(sj_ctx* c, Temps& tmp, const int32_t* keys, const 
   t.slots = slots;
   t.bucket_mask = 0;
   t.mask_dev = mask;
-  MMInsertArgs mi{keys, cap, t, nuniq, cnt, rid, rank, status_ptr(c)};
+  MMInsertArgs mi{keys, cap, t, cnt, rid, rank, status_ptr(c)};
   mi.n_dev = n_dev;
   if (!n_dev) mi.n = n_host;
   {
@@ -1551,12 +1545,12 @@ sj_status build_adjacency_dev(sj_ctx* c, Temps& tmp, const int32_t* keys, const 
   sa.in = cnt;
   sa.out = off;
   sa.n_host = 0;
-  sa.n_dev = nuniq;
+  sa.n_dev = nslots_dev;
   sa.total = nullptr;
-  SJ_TRY(scratch_for<1>(c, (capn + kScanTile - 1) / kScanTile, &sa.tile_counter, &sa.lb));
+  SJ_TRY(scratch_for<1>(c, ((int64_t)cap_slots + kScanTile - 1) / kScanTile, &sa.tile_counter, &sa.lb));
   {
     Launch L(c, SJ_K_HT_BUILD, 12.0 * (double)cap);
-    launch_scan_u32(sa, capn, c->stream);
+    launch_scan_u32(sa, (int64_t)cap_slots, c->num_sms, c->stream);
   }
   SJ_TRY(check_launch(c, "k_scan_u32"));
   MMScatterArgs ms{rid, rank, off, n_dev ? cap : n_host, rows};
@@ -1614,11 +1608,10 @@ sj_status join_async(sj_ctx* c, const sj_path* path, const sj_rel* in_rels, int 
       const int64_t cap_build = swap ? in.cap : capB;
       const uint64_t cap_slots = pow2_at_least(std::max<uint64_t>(64, 2 * (uint64_t)std::max<int64_t>(cap_build, 1)));
       unsigned long long* slots = keep.get<unsigned long long>(cap_slots, &st);
-      unsigned long long* cnt = keep.get<unsigned long long>(cap_slots, &st);
-      unsigned long long* sum = keep.get<unsigned long long>(cap_slots, &st);
+      ulonglong2* cs = keep.get<ulonglong2>(cap_slots, &st);
       if (st != SJ_OK) return fail(c, st, "aggregate table allocation failed");
       TableInitArgs ti{slots, small + 2 * L, swap ? in.n_dev : B->d_n, swap ? in.n_host : B->nrows,
-                       cnt, sum, nullptr, nullptr};
+                       cs, nullptr, nullptr};
       {
         Launch Lk(c, SJ_K_AGG, 0.0);
         launch_table_init(ti, (int64_t)cap_slots, c->num_sms, c->stream);
@@ -1635,8 +1628,7 @@ sj_status join_async(sj_ctx* c, const sj_path* path, const sj_rel* in_rels, int 
       ai.t = t;
       ai.terms = swap ? base_terms : rel_terms;
       ai.vals = swap ? inter_vals : nullptr;
-      ai.cnt = cnt;
-      ai.sum = sum;
+      ai.cs = cs;
       ai.status = status_ptr(c);
       {
         Launch Lk(c, SJ_K_AGG, 4.0 * (double)ai.n);
@@ -1648,8 +1640,7 @@ sj_status join_async(sj_ctx* c, const sj_path* path, const sj_rel* in_rels, int 
       ap.n = swap ? (B->d_n ? capB : B->nrows) : (in.n_dev ? in.cap : in.n_host);
       ap.n_dev = swap ? B->d_n : in.n_dev;
       ap.t = t;
-      ap.cnt = cnt;
-      ap.sum = sum;
+      ap.cs = cs;
       ap.probe_terms = swap ? rel_terms : base_terms;
       ap.psum_in = swap ? nullptr : inter_vals;
       ap.result = reinterpret_cast<unsigned long long*>(c->d_misc + kMiscResult);
@@ -1684,7 +1675,7 @@ sj_status join_async(sj_ctx* c, const sj_path* path, const sj_rel* in_rels, int 
     SJ_TRY(scratch_for<2>(c, (capP + kProbeTile - 1) / kProbeTile, &mp.tile_counter, &mp.lb));
     {
       Launch Lk(c, SJ_K_HT_PROBE, 4.0 * (double)mp.n);
-      launch_mm_probe(mp, c->stream);
+      launch_mm_probe(mp, c->num_sms, c->stream);
     }
     SJ_TRY(check_launch(c, "k_mm_probe"));
     std::map<ColKey, int> need;

@@ -306,4 +306,13 @@ __device__ __forceinline__ uint32_t draw_ticket(uint32_t* counter) {
   return t;
 }
 
+// Ticket for a grid whose CTAs loop over `ntiles` tiles: every CTA draws
+// until it gets a ticket >= ntiles, so the launch draws ntiles + gridDim.x
+// tickets in all, and the CTA that draws the last one resets the counter.
+__device__ __forceinline__ uint32_t draw_ticket_loop(uint32_t* counter, uint64_t ntiles) {
+  const uint32_t t = atomicAdd(counter, 1u);
+  if ((uint64_t)t == ntiles + gridDim.x - 1) atomicExch(counter, 0u);
+  return t;
+}
+
 }  // namespace sj

@@ -188,14 +188,23 @@ __global__ void __launch_bounds__(kBlock, 3) k_bloom_build(BloomBuildArgs a) {
     // rounds of kBuildKeys keys per thread: vector v of a round is key vector
     // base + v * stride, so every warp load is one contiguous 512 B
     const int64_t nvec = (n + 3) >> 2;
+    const int64_t nfull = n >> 2;  // vectors of 4 valid keys
+    // the next round's key vectors are loaded before this round's inserts, so
+    // a round waits on the filter words only
+    int4 xv[kBuildVecs];
+#pragma unroll
+    for (int v = 0; v < kBuildVecs; ++v) {
+      const int64_t i = gid + v * stride;
+      xv[v] = i < nfull ? __ldcs(kv + i) : make_int4(0, 0, 0, 0);
+    }
     for (int64_t base = gid; base < nvec; base += kBuildVecs * stride) {
       int32_t k16[kBuildKeys];
       uint32_t live = 0;
 #pragma unroll
       for (int v = 0; v < kBuildVecs; ++v) {
         const int64_t i = base + v * stride;
-        if (i < nvec && (i << 2) + 4 <= n) {
-          const int4 x = __ldcs(kv + i);
+        if (i < nfull) {
+          const int4 x = xv[v];
           k16[4 * v] = x.x;
           k16[4 * v + 1] = x.y;
           k16[4 * v + 2] = x.z;
@@ -211,6 +220,11 @@ __global__ void __launch_bounds__(kBlock, 3) k_bloom_build(BloomBuildArgs a) {
             }
           }
         }
+      }
+#pragma unroll
+      for (int v = 0; v < kBuildVecs; ++v) {
+        const int64_t i = base + kBuildVecs * stride + v * stride;
+        xv[v] = i < nfull ? __ldcs(kv + i) : make_int4(0, 0, 0, 0);
       }
       switch (a.k) {
         case 3: bloom_insert_regN<3>(a, nwords, k16, live, s_seen); break;
@@ -757,19 +771,22 @@ __global__ void __launch_bounds__(kBlock) k_sieve_move(SieveMoveArgs a) {
 }
 
 // ---------------------------------------------------------------- scan
+// CTAs loop over tiles in ticket order (a grid of a few CTAs per SM serves any
+// n, including a count known on the device only).
 __global__ void __launch_bounds__(kBlock) k_scan_u32(ScanArgs a) {
   __shared__ uint32_t s_tile;
   __shared__ Vec<2> s_warp[kBlock / 32];
   __shared__ uint64_t s_prefix;
   const int tid = threadIdx.x;
-  if (tid == 0) s_tile = draw_ticket(a.tile_counter);
-  __syncthreads();
-  const uint32_t tile = s_tile;
   const int64_t n = a.n_dev ? (int64_t)(*a.n_dev) : a.n_host;
   const int64_t ntiles = (n + kScanTile - 1) / kScanTile;
+  for (;;) {
+  if (tid == 0) s_tile = draw_ticket_loop(a.tile_counter, (uint64_t)ntiles);
+  __syncthreads();
+  const uint32_t tile = s_tile;
   if ((int64_t)tile >= ntiles) {
     if (tile == 0 && tid == 0 && a.total) *a.total = 0;
-    return;
+    break;
   }
   const int64_t base = (int64_t)tile * kScanTile;
   uint32_t x[8];
@@ -825,44 +842,29 @@ __global__ void __launch_bounds__(kBlock) k_scan_u32(ScanArgs a) {
       run += x[4 * v + e];
     }
   }
+  }  // tile loop (the scan's barriers order s_tile / s_prefix reuse)
 }
 
 // ---------------------------------------------------------------- hash tables
-// Find the slot holding `key`; insert it if absent.  Multimap variant: the
-// inserting thread assigns the key a dense id (published in the slot's high
-// word, id + 1; 0xffffffff marks "id pending").  Returns the id, or -1 with
-// kErrTableFull when the probe sequence is exhausted.
-__device__ __forceinline__ int32_t mm_find_or_insert(const Table& t, int32_t key, uint32_t* nuniq,
-                                                     uint32_t* status) {
+// Slot holding `key` (the key in the low word, 1 in the high word so that key
+// 0 differs from an empty slot); inserted if absent.  Returns -1 with
+// kErrTableFull when the probe sequence is exhausted.  A multimap groups its
+// rows by this slot index, so no dense key ids (and no shared id counter) are
+// needed.
+__device__ __forceinline__ int64_t table_find_or_insert(const Table& t, int32_t key,
+                                                      uint32_t* status) {
   uint32_t b = table_bucket(key, t.bucket_mask);
-  const uint64_t lo = (uint32_t)key;
+  const unsigned long long want = (1ull << 32) | (uint32_t)key;
   for (uint32_t step = 0; step <= t.bucket_mask; ++step) {
     unsigned long long* bk = t.slots + (uint64_t)b * 4;
 #pragma unroll 1
     for (int s = 0; s < 4; ++s) {
-      uint64_t v = ld_volatile_u64(reinterpret_cast<const uint64_t*>(bk + s));
+      unsigned long long v = ld_volatile_u64(reinterpret_cast<const uint64_t*>(bk + s));
       if (v == 0) {
-        const unsigned long long pend = (0xffffffffull << 32) | lo;
-        const unsigned long long old = atomicCAS(bk + s, 0ull, pend);
-        if (old == 0) {
-          const uint32_t id = atomicAdd(nuniq, 1u);
-          st_volatile_u64(reinterpret_cast<uint64_t*>(bk + s), ((uint64_t)(id + 1) << 32) | lo);
-          return (int32_t)id;
-        }
-        v = old;
+        v = atomicCAS(bk + s, 0ull, want);
+        if (v == 0) return (int64_t)b * 4 + s;
       }
-      if ((v & 0xffffffffull) == lo) {
-        uint32_t spins = 0;
-        while ((v >> 32) == 0xffffffffull) {
-          if (++spins > kSpinLimit) {
-            atomicOr(status, kErrTimeout);
-            return -1;
-          }
-          __nanosleep(32);
-          v = ld_volatile_u64(reinterpret_cast<const uint64_t*>(bk + s));
-        }
-        return (int32_t)((v >> 32) - 1);
-      }
+      if (v == want) return (int64_t)b * 4 + s;
     }
     b = (b + 1) & t.bucket_mask;
   }
@@ -889,28 +891,71 @@ __device__ __forceinline__ int64_t table_find(const Table& t, int32_t key) {
   return -1;
 }
 
+// Per-CTA aggregation of skewed keys: a CTA takes kAggRows rows per round and
+// combines the rows of each key (dense id or table slot) in a shared-memory
+// table before touching global memory, so a key repeated r times in a round
+// costs one global atomic instead of r (Zipf-hot keys would otherwise
+// serialise on one address).
+constexpr int kAggPerThread = 2;
+constexpr int kAggRows = kBlock * kAggPerThread;
+constexpr int kAggSlotsLog2 = 10;
+constexpr int kAggSlots = 1 << kAggSlotsLog2;  // 2x the rows of a round: never full
+static_assert(kAggSlots >= 2 * kAggRows, "per-CTA table must hold every key of a round");
+
+// Shared-memory slot of `v` (inserted if absent), or -1 if the table is full.
+__device__ __forceinline__ int smem_slot(uint32_t* s_key, uint32_t v) {
+  uint32_t h = (v * 2654435761u) >> (32 - kAggSlotsLog2);
+  for (int p = 0; p < kAggSlots; ++p) {
+    const uint32_t cur = s_key[h];
+    if (cur == v) return (int)h;
+    if (cur == 0xffffffffu) {
+      const uint32_t old = atomicCAS(s_key + h, 0xffffffffu, v);
+      if (old == 0xffffffffu || old == v) return (int)h;
+    }
+    h = (h + 1) & (kAggSlots - 1);
+  }
+  return -1;
+}
+
 __global__ void __launch_bounds__(kBlock) k_mm_insert(MMInsertArgs a) {
+  __shared__ uint32_t s_key[kAggSlots];  // table slot, 0xffffffff = empty
+  __shared__ uint32_t s_cnt[kAggSlots];  // rows of the round, then their global base
   a.t = resolve(a.t);
   a.n = dev_n(a.n_dev, a.n);
-  const int lane = threadIdx.x & 31;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  // every lane of a warp runs the same number of iterations (warp-collective match)
-  const int64_t first = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31);
-  for (int64_t w0 = first; w0 < a.n; w0 += stride) {
-    const int64_t row = w0 + lane;
-    const bool active = row < a.n;
-    int32_t id = -1;
-    if (active) id = mm_find_or_insert(a.t, __ldcs(a.keys + row), a.nuniq, a.status);
-    const int32_t gkey = (active && id >= 0) ? id : -2 - lane;
-    const uint32_t group = __match_any_sync(0xffffffffu, gkey);
-    const int leader = __ffs(group) - 1;
-    uint32_t base = 0;
-    if (lane == leader && gkey >= 0) base = atomicAdd(a.cnt + gkey, (uint32_t)__popc(group));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (active && id >= 0) {
-      a.rid[row] = (uint32_t)id;
-      a.rank[row] = base + __popc(group & ((1u << lane) - 1u));
+  const int tid = threadIdx.x;
+  for (int64_t r0 = (int64_t)blockIdx.x * kAggRows; r0 < a.n; r0 += (int64_t)gridDim.x * kAggRows) {
+    for (int i = tid; i < kAggSlots; i += kBlock) {
+      s_key[i] = 0xffffffffu;
+      s_cnt[i] = 0;
     }
+    __syncthreads();
+    int64_t sl[kAggPerThread];
+    int j[kAggPerThread];
+    uint32_t lr[kAggPerThread];
+#pragma unroll
+    for (int e = 0; e < kAggPerThread; ++e) {
+      const int64_t row = r0 + e * kBlock + tid;
+      sl[e] = row < a.n ? table_find_or_insert(a.t, __ldcs(a.keys + row), a.status) : -1;
+      j[e] = -1;
+      lr[e] = 0;
+      if (sl[e] >= 0) {
+        j[e] = smem_slot(s_key, (uint32_t)sl[e]);
+        lr[e] = j[e] >= 0 ? atomicAdd(s_cnt + j[e], 1u) : atomicAdd(a.cnt + sl[e], 1u);
+      }
+    }
+    __syncthreads();
+    for (int i = tid; i < kAggSlots; i += kBlock)
+      if (s_key[i] != 0xffffffffu) s_cnt[i] = atomicAdd(a.cnt + s_key[i], s_cnt[i]);
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < kAggPerThread; ++e) {
+      const int64_t row = r0 + e * kBlock + tid;
+      if (sl[e] >= 0) {
+        a.rid[row] = (uint32_t)sl[e];
+        a.rank[row] = (j[e] >= 0 ? s_cnt[j[e]] : 0u) + lr[e];
+      }
+    }
+    __syncthreads();  // the table is cleared by the next round
   }
 }
 
@@ -926,18 +971,19 @@ __global__ void __launch_bounds__(kBlock) k_mm_probe(MMProbeArgs a) {
   __shared__ Vec<3> s_warp[kBlock / 32];
   __shared__ uint64_t s_prefix[2];
   const int tid = threadIdx.x;
-  if (tid == 0) s_tile = draw_ticket(a.tile_counter);
-  __syncthreads();
-  const uint32_t tile = s_tile;
   a.t = resolve(a.t);
   const int64_t n = dev_n(a.n_dev, a.n);
   const int64_t ntiles = (n + kProbeTile - 1) / kProbeTile;
+  for (;;) {
+  if (tid == 0) s_tile = draw_ticket_loop(a.tile_counter, (uint64_t)ntiles);
+  __syncthreads();
+  const uint32_t tile = s_tile;
   if ((int64_t)tile >= ntiles) {
     if (tile == 0 && tid == 0) {
       a.totals[0] = 0;
       a.totals[1] = 0;
     }
-    return;
+    break;
   }
   const int64_t base = (int64_t)tile * kProbeTile;
   int32_t id[8];
@@ -965,9 +1011,8 @@ __global__ void __launch_bounds__(kBlock) k_mm_probe(MMProbeArgs a) {
       if (ok4[e]) {
         const int64_t s = table_find(a.t, k4[e]);
         if (s >= 0) {
-          const uint32_t kid = (uint32_t)(__ldg(a.t.slots + s) >> 32) - 1u;
-          id[4 * v + e] = (int32_t)kid;
-          m[4 * v + e] = __ldg(a.cnt + kid);
+          id[4 * v + e] = (int32_t)s;
+          m[4 * v + e] = __ldg(a.cnt + s);
         }
       }
     }
@@ -1035,6 +1080,7 @@ __global__ void __launch_bounds__(kBlock) k_mm_probe(MMProbeArgs a) {
       }
     }
   }
+  }  // tile loop (the scan's barriers order s_tile / s_prefix reuse)
 }
 
 // Largest q in [lo, hi] with o[q] <= j (o strictly increasing, o[lo] <= j).
@@ -1103,71 +1149,60 @@ __global__ void __launch_bounds__(kBlock) k_table_init(TableInitArgs a) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   if (gid == 0) {
     *a.mask_out = (uint32_t)(nslots / 4 - 1);
-    if (a.zero32) *a.zero32 = 0;
+    if (a.nslots_out) *a.nslots_out = (uint32_t)nslots;
   }
   for (int64_t i = gid; i < (int64_t)nslots; i += stride) {
     a.slots[i] = 0ull;
-    if (a.per_slot0) a.per_slot0[i] = 0ull;
-    if (a.per_slot1) a.per_slot1[i] = 0ull;
+    if (a.pairs) a.pairs[i] = make_ulonglong2(0ull, 0ull);
   }
   if (a.cnt)
-    for (int64_t i = gid; i < n; i += stride) a.cnt[i] = 0u;
+    for (int64_t i = gid; i < (int64_t)nslots; i += stride) a.cnt[i] = 0u;
 }
 
 // ---------------------------------------------------------------- aggregate level
-__device__ __forceinline__ int64_t agg_find_or_insert(const Table& t, int32_t key,
-                                                      uint32_t* status) {
-  uint32_t b = table_bucket(key, t.bucket_mask);
-  const unsigned long long want = (1ull << 32) | (uint32_t)key;
-  for (uint32_t step = 0; step <= t.bucket_mask; ++step) {
-    unsigned long long* bk = t.slots + (uint64_t)b * 4;
-#pragma unroll 1
-    for (int s = 0; s < 4; ++s) {
-      unsigned long long v = ld_volatile_u64(reinterpret_cast<const uint64_t*>(bk + s));
-      if (v == 0) {
-        v = atomicCAS(bk + s, 0ull, want);
-        if (v == 0) return (int64_t)b * 4 + s;
-      }
-      if (v == want) return (int64_t)b * 4 + s;
-    }
-    b = (b + 1) & t.bucket_mask;
-  }
-  atomicOr(status, kErrTableFull);
-  return -1;
-}
 
 __global__ void __launch_bounds__(kBlock) k_agg_insert(AggInsertArgs a) {
+  __shared__ uint32_t s_key[kAggSlots];          // global slot, 0xffffffff = empty
+  __shared__ uint32_t s_cnt[kAggSlots];
+  __shared__ unsigned long long s_sum[kAggSlots];
   a.t = resolve(a.t);
   a.n = dev_n(a.n_dev, a.n);
-  const int lane = threadIdx.x & 31;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t first = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31);
-  for (int64_t w0 = first; w0 < a.n; w0 += stride) {
-    const int64_t row = w0 + lane;
-    const bool active = row < a.n;
-    int64_t s = -1;
-    uint64_t val = 0;
-    if (active) {
-      s = agg_find_or_insert(a.t, __ldcs(a.keys + row), a.status);
-      val = a.vals ? __ldg(a.vals + row) : term_sum(a.terms, row);
+  const bool with_sum = a.terms.n || a.vals;
+  const int tid = threadIdx.x;
+  for (int64_t r0 = (int64_t)blockIdx.x * kAggRows; r0 < a.n; r0 += (int64_t)gridDim.x * kAggRows) {
+    for (int i = tid; i < kAggSlots; i += kBlock) {
+      s_key[i] = 0xffffffffu;
+      s_cnt[i] = 0;
+      s_sum[i] = 0ull;
     }
-    // combine rows of the same key within the warp, then one atomic pair per key
-    const long long gk = (s >= 0) ? s : (-2 - lane);
-    const uint32_t group = __match_any_sync(0xffffffffu, gk);
-    uint64_t gsum = 0;
-    if (__any_sync(0xffffffffu, __popc(group) > 1)) {
-#pragma unroll 4
-      for (int l = 0; l < 32; ++l) {
-        const uint64_t x = __shfl_sync(0xffffffffu, val, l);
-        if ((group >> l) & 1u) gsum += x;
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < kAggPerThread; ++e) {
+      const int64_t row = r0 + e * kBlock + tid;
+      if (row < a.n) {
+        const int64_t sl = table_find_or_insert(a.t, __ldcs(a.keys + row), a.status);
+        if (sl >= 0) {
+          const uint64_t val = with_sum ? (a.vals ? __ldg(a.vals + row) : term_sum(a.terms, row)) : 0ull;
+          const int j = smem_slot(s_key, (uint32_t)sl);
+          if (j >= 0) {
+            atomicAdd(s_cnt + j, 1u);
+            if (with_sum) atomicAdd(s_sum + j, (unsigned long long)val);
+          } else {
+            atomicAdd(&a.cs[sl].x, 1ull);
+            if (with_sum) atomicAdd(&a.cs[sl].y, (unsigned long long)val);
+          }
+        }
       }
-    } else {
-      gsum = val;
     }
-    if (s >= 0 && lane == __ffs(group) - 1) {
-      atomicAdd(a.cnt + s, (unsigned long long)__popc(group));
-      if (a.terms.n || a.vals) atomicAdd(a.sum + s, (unsigned long long)gsum);
+    __syncthreads();
+    for (int i = tid; i < kAggSlots; i += kBlock) {
+      const uint32_t sl = s_key[i];
+      if (sl != 0xffffffffu) {
+        atomicAdd(&a.cs[sl].x, (unsigned long long)s_cnt[i]);
+        if (with_sum) atomicAdd(&a.cs[sl].y, s_sum[i]);
+      }
     }
+    __syncthreads();  // the table is cleared by the next round
   }
 }
 
@@ -1183,20 +1218,83 @@ __device__ __forceinline__ void add128(U128& x, uint64_t lo, uint64_t hi) {
 // One probe row per thread and iteration: the table is small and cache
 // resident here, so occupancy (32 registers, 8 CTAs per SM) hides latency
 // better than batching rows per thread.
-__global__ void __launch_bounds__(kBlock) k_agg_probe(AggProbeArgs a) {
+// Slot of `key` when it sits in one of the first two slots of its home
+// bucket (the common case at load <= 1/2), -1 when that half-bucket shows it
+// absent, else the full probe.
+__device__ __forceinline__ int64_t table_find_first(const Table& t, int32_t key, uint32_t b,
+                                                    ulonglong2 q) {
+  const uint64_t lo = (uint32_t)key;
+  if (q.x == 0) return -1;
+  if ((q.x & 0xffffffffull) == lo) return (int64_t)b * 4;
+  if (q.y == 0) return -1;
+  if ((q.y & 0xffffffffull) == lo) return (int64_t)b * 4 + 1;
+  return table_find(t, key);
+}
+
+// Probe of the final level's (count, sum) table.  The common shape -- a long
+// probe relation whose SUM term is at most one int32 column -- takes 4 rows per
+// thread with the next 4 keys and terms already in flight, so each iteration
+// waits on two table round trips only.
+__global__ void __launch_bounds__(kBlock, 4) k_agg_probe(AggProbeArgs a) {
   __shared__ uint64_t s_red[3][kBlock / 32];
   a.t = resolve(a.t);
   a.n = dev_n(a.n_dev, a.n);
   U128 cnt = {0, 0};
   uint64_t sum = 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int32_t* tcol = a.probe_terms.n == 1 ? a.probe_terms.col[0] : nullptr;
+  const bool fast = ((reinterpret_cast<uintptr_t>(a.keys) & 15u) == 0) && !a.psum_in &&
+                    a.probe_terms.n <= 1 &&
+                    (!tcol || (!a.probe_terms.col_hi[0] && (reinterpret_cast<uintptr_t>(tcol) & 15u) == 0));
+  int64_t tail = 0;
+  if (fast) {
+    const int64_t n4 = a.n / 4;
+    tail = n4 * 4;
+    const int4* k4 = reinterpret_cast<const int4*>(a.keys);
+    const int4* v4 = reinterpret_cast<const int4*>(tcol);
+    int4 k = make_int4(0, 0, 0, 0), v = make_int4(0, 0, 0, 0);
+    if (tid < n4) {
+      k = __ldcs(k4 + tid);
+      if (tcol) v = __ldcs(v4 + tid);
+    }
+    for (int64_t g = tid; g < n4; g += stride) {
+      int4 kn = make_int4(0, 0, 0, 0), vn = make_int4(0, 0, 0, 0);
+      if (g + stride < n4) {
+        kn = __ldcs(k4 + g + stride);
+        if (tcol) vn = __ldcs(v4 + g + stride);
+      }
+      const int32_t kk[4] = {k.x, k.y, k.z, k.w};
+      const int32_t vv[4] = {v.x, v.y, v.z, v.w};
+      uint32_t b[4];
+      ulonglong2 q[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        b[e] = table_bucket(kk[e], a.t.bucket_mask);
+        q[e] = __ldg(reinterpret_cast<const ulonglong2*>(a.t.slots + (uint64_t)b[e] * 4));
+      }
+      int64_t sl[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) sl[e] = table_find_first(a.t, kk[e], b[e], q[e]);
+      ulonglong2 cs[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) cs[e] = sl[e] >= 0 ? __ldg(a.cs + sl[e]) : make_ulonglong2(0ull, 0ull);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        add128(cnt, cs[e].x, 0);
+        sum += (uint64_t)(int64_t)vv[e] * cs[e].x + cs[e].y;
+      }
+      k = kn;
+      v = vn;
+    }
+  }
+  for (int64_t i = tail + tid; i < a.n; i += stride) {
     const int64_t s = table_find(a.t, __ldcs(a.keys + i));
     if (s < 0) continue;
-    const uint64_t c = __ldg(a.cnt + s);
+    const ulonglong2 cs = __ldg(a.cs + s);  // count and sum share a sector
     const uint64_t ps = a.psum_in ? __ldg(a.psum_in + i) : term_sum(a.probe_terms, i);
-    add128(cnt, c, 0);
-    sum += ps * c + __ldg(a.sum + s);
+    add128(cnt, cs.x, 0);
+    sum += ps * cs.x + cs.y;
   }
   // block reduction of (count lo, count hi, sum)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1317,9 +1415,8 @@ __device__ __forceinline__ void adj_of(const Adjacency& g, int32_t v, uint64_t* 
     *len = 0;
     return;
   }
-  const uint32_t id = (uint32_t)(__ldg(g.t.slots + s) >> 32) - 1u;
-  *off = __ldg(g.off + id);
-  *len = __ldg(g.cnt + id);
+  *off = __ldg(g.off + s);
+  *len = __ldg(g.cnt + s);
 }
 
 // Persistent warps take 32 edges (a, b) at a time.  For each edge the warp
@@ -1459,20 +1556,20 @@ void launch_sieve_two_pass(const SieveArgs& a, const SieveMoveArgs& m, int64_t n
   k_sieve_move<<<g < 4 * num_sms ? g : 4 * num_sms, kBlock, 0, s>>>(m);
 }
 
-void launch_scan_u32(const ScanArgs& a, int64_t n_upper, cudaStream_t s) {
-  k_scan_u32<<<host_grid(n_upper, kScanTile, 1 << 30), kBlock, 0, s>>>(a);
+void launch_scan_u32(const ScanArgs& a, int64_t n_upper, int num_sms, cudaStream_t s) {
+  k_scan_u32<<<host_grid(n_upper, kScanTile, 4 * num_sms), kBlock, 0, s>>>(a);
 }
 
 void launch_mm_insert(const MMInsertArgs& a, int num_sms, cudaStream_t s) {
-  k_mm_insert<<<host_grid(a.n, kBlock, num_sms * 8), kBlock, 0, s>>>(a);
+  k_mm_insert<<<host_grid(a.n, kAggRows, num_sms * 4), kBlock, 0, s>>>(a);
 }
 
 void launch_mm_scatter(const MMScatterArgs& a, int num_sms, cudaStream_t s) {
   k_mm_scatter<<<host_grid(a.n, kBlock, num_sms * 8), kBlock, 0, s>>>(a);
 }
 
-void launch_mm_probe(const MMProbeArgs& a, cudaStream_t s) {
-  k_mm_probe<<<host_grid(a.n, kProbeTile, 1 << 30), kBlock, 0, s>>>(a);
+void launch_mm_probe(const MMProbeArgs& a, int num_sms, cudaStream_t s) {
+  k_mm_probe<<<host_grid(a.n, kProbeTile, 4 * num_sms), kBlock, 0, s>>>(a);
 }
 
 void launch_mm_expand(const MMExpandArgs& a, cudaStream_t s) {
@@ -1488,7 +1585,7 @@ void launch_table_init(const TableInitArgs& a, int64_t cap_slots, int num_sms, c
 }
 
 void launch_agg_insert(const AggInsertArgs& a, int num_sms, cudaStream_t s) {
-  k_agg_insert<<<host_grid(a.n, kBlock, num_sms * 8), kBlock, 0, s>>>(a);
+  k_agg_insert<<<host_grid(a.n, kAggRows, num_sms * 4), kBlock, 0, s>>>(a);
 }
 
 void launch_agg_probe(const AggProbeArgs& a, int num_sms, cudaStream_t s) {

@@ -99,7 +99,7 @@ struct ScanArgs {
   LookBack<1> lb;
 };
 constexpr int kScanTile = kBlock * 8;
-void launch_scan_u32(const ScanArgs& a, int64_t n_upper, cudaStream_t s);
+void launch_scan_u32(const ScanArgs& a, int64_t n_upper, int num_sms, cudaStream_t s);
 
 // ------------------------------------------------------------------ hash tables
 // Open addressing, linear probing over buckets of four 8-byte slots (one
@@ -118,20 +118,18 @@ struct TableInitArgs {
   uint32_t* mask_out;
   const uint64_t* n_dev;
   int64_t n_host;
-  unsigned long long* per_slot0;  // optional, nslots entries
-  unsigned long long* per_slot1;  // optional, nslots entries
-  uint32_t* cnt;                  // optional, n entries
-  uint32_t* zero32;               // optional counter to clear
+  ulonglong2* pairs;              // optional, nslots entries
+  uint32_t* cnt;                  // optional, nslots entries to clear
+  uint32_t* nslots_out;           // optional: receives nslots
 };
 void launch_table_init(const TableInitArgs& a, int64_t cap_slots, int num_sms, cudaStream_t s);
 
-struct MMInsertArgs {       // multimap build, pass 1: distinct keys and per-row rank
+struct MMInsertArgs {       // multimap build, pass 1: key slots and per-row rank
   const int32_t* keys;
   int64_t n;
   Table t;
-  uint32_t* nuniq;
-  uint32_t* cnt;            // [n] zeroed
-  uint32_t* rid;            // [n] row -> key id
+  uint32_t* cnt;            // [nslots] zeroed: rows per key slot
+  uint32_t* rid;            // [n] row -> key slot
   uint32_t* rank;           // [n] row -> rank among rows of its key
   uint32_t* status;
   const uint64_t* n_dev = nullptr;  // device row count (overrides n)
@@ -162,7 +160,7 @@ struct MMProbeArgs {        // probe + compaction of matching probe rows
   const uint64_t* n_dev = nullptr;
 };
 constexpr int kProbeTile = kBlock * 8;
-void launch_mm_probe(const MMProbeArgs& a, cudaStream_t s);
+void launch_mm_probe(const MMProbeArgs& a, int num_sms, cudaStream_t s);
 
 struct Terms {              // SUM terms read from one side's columns
   const int32_t* col[kMaxTerms];     // int32 term, or low word of an int64 term
@@ -203,8 +201,7 @@ struct AggInsertArgs {
   Table t;
   Terms terms;
   const uint64_t* vals;     // per-row value instead of terms, or null
-  unsigned long long* cnt;  // [nslots] zeroed
-  unsigned long long* sum;  // [nslots] zeroed
+  ulonglong2* cs;           // [nslots] (count, sum) per slot, zeroed
   uint32_t* status;
   const uint64_t* n_dev = nullptr;
 };
@@ -214,8 +211,7 @@ struct AggProbeArgs {
   const int32_t* keys;
   int64_t n;
   Table t;
-  const unsigned long long* cnt;
-  const unsigned long long* sum;
+  const ulonglong2* cs;     // [nslots] (count, sum) per slot
   const uint64_t* psum_in;
   Terms probe_terms;
   unsigned long long* result;  // [0] count lo, [1] count hi, [2] sum; zeroed
