@@ -60,6 +60,14 @@ struct sj_ctx {
   size_t scratch_bytes = 0;
   uint32_t epoch = 0;  // look-back flag epoch of the last scan launch
   cudaEvent_t ev_wait = nullptr;  // host waits on one point of the stream
+  // second stream: the device-sized join builds its multimaps there while the
+  // main stream probes; it has its own look-back scratch
+  cudaStream_t side = nullptr;
+  uint8_t* scratch2 = nullptr;
+  size_t scratch2_bytes = 0;
+  uint32_t epoch2 = 0;
+  cudaEvent_t ev_ready = nullptr;
+  cudaEvent_t ev_built[SJ_MAX_REL] = {};
   // per query shape: output tuples of each join level in the last exact run,
   // used to size the buffers of the device-sized (host-sync-free) join
   std::map<uint64_t, std::vector<uint64_t>> plan_caps;
@@ -679,6 +687,19 @@ sj_status sj_create(sj_ctx** out, int device, void* stream, sj_alloc_fn alloc, s
 sj_status sj_destroy(sj_ctx* c) {
   if (!c) return SJ_EINVAL;
   cudaStreamSynchronize(c->stream);
+  if (c->side) {
+    cudaStreamSynchronize(c->side);
+    if (c->scratch2) {
+      std::swap(c->stream, c->side);
+      raw_free(c, c->scratch2, c->scratch2_bytes);
+      std::swap(c->stream, c->side);
+      cudaStreamSynchronize(c->side);
+    }
+    cudaStreamDestroy(c->side);
+  }
+  if (c->ev_ready) cudaEventDestroy(c->ev_ready);
+  for (auto e : c->ev_built)
+    if (e) cudaEventDestroy(e);
   raw_free(c, c->scratch, c->scratch_bytes);
   raw_free(c, c->arena.base, c->arena.size);
   raw_free(c, c->d_misc, kMiscWords * sizeof(uint64_t));
@@ -1567,6 +1588,39 @@ sj_status build_adjacency_dev(sj_ctx* c, Temps& tmp, const int32_t* keys, const 
   return SJ_OK;
 }
 
+// Enqueue on the side stream (with its own scratch) while in scope.
+struct OnSide {
+  sj_ctx* c;
+  explicit OnSide(sj_ctx* cc) : c(cc) { flip(); }
+  ~OnSide() { flip(); }
+  void flip() {
+    std::swap(c->stream, c->side);
+    std::swap(c->scratch, c->scratch2);
+    std::swap(c->scratch_bytes, c->scratch2_bytes);
+    std::swap(c->epoch, c->epoch2);
+  }
+};
+
+// Waits for the side stream when a call leaves early (on success the main
+// stream has already waited for all of its work).
+struct SideDrain {
+  sj_ctx* c;
+  ~SideDrain() {
+    if (c->side) cudaStreamSynchronize(c->side);
+  }
+};
+
+sj_status ensure_side(sj_ctx* c, int nlev) {
+  if (!c->side && cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess)
+    return fail(c, SJ_ECUDA, "side stream creation failed");
+  if (!c->ev_ready && cudaEventCreateWithFlags(&c->ev_ready, cudaEventDisableTiming) != cudaSuccess)
+    return fail(c, SJ_ECUDA, "event creation failed");
+  for (int L = 0; L < nlev; ++L)
+    if (!c->ev_built[L] && cudaEventCreateWithFlags(&c->ev_built[L], cudaEventDisableTiming) != cudaSuccess)
+      return fail(c, SJ_ECUDA, "event creation failed");
+  return SJ_OK;
+}
+
 // COUNT/SUM join with every size kept on the device: no host round trip
 // until the one synchronisation at the end.  caps[L] bounds the output of
 // multimap level L; a level that outgrows it records kErrCapacity and the call
@@ -1593,6 +1647,23 @@ sj_status join_async(sj_ctx* c, const sj_path* path, const sj_rel* in_rels, int 
   joined[0] = 1;
   Terms none;
   memset(&none, 0, sizeof(none));
+  // the multimap of every non-final level depends only on its relation:
+  // all of them are built on the side stream while the main stream probes
+  const int nlev = (int)plan.size() - 1;
+  std::vector<Adjacency> built(std::max(nlev, 0));
+  SideDrain drain{c};
+  if (nlev > 0) {
+    SJ_TRY(ensure_side(c, nlev));
+    SJ_CUDA(c, cudaEventRecord(c->ev_ready, c->stream));
+    OnSide side(c);
+    SJ_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_ready, 0));
+    for (int L = 0; L < nlev; ++L) {
+      const sj_rel_s* B = rels[plan[L].rel];
+      SJ_TRY(build_adjacency_dev(c, keep, B->cols[plan[L].rel_col], B->d_n, B->nrows, rel_cap(B),
+                                 small + 2 * L, small + 2 * L + 1, &built[L]));
+      SJ_CUDA(c, cudaEventRecord(c->ev_built[L], c->stream));
+    }
+  }
   for (size_t L = 0; L < plan.size(); ++L) {
     const LevelPlan& lp = plan[L];
     const sj_rel_s* B = rels[lp.rel];
@@ -1653,9 +1724,8 @@ sj_status join_async(sj_ctx* c, const sj_path* path, const sj_rel* in_rels, int 
       break;
     }
     // ---- multimap level
-    Adjacency G{};
-    SJ_TRY(build_adjacency_dev(c, keep, B->cols[lp.rel_col], B->d_n, B->nrows, capB,
-                               small + 2 * L, small + 2 * L + 1, &G));
+    const Adjacency G = built[L];
+    SJ_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_built[L], 0));
     const int64_t capP = std::max<int64_t>(in.cap, 1);
     int32_t* prow = keep.get<int32_t>(capP, &st);
     int32_t* pid = keep.get<int32_t>(capP, &st);
