@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <functional>
 #include <map>
 #include <string>
 #include <utility>
@@ -863,8 +864,10 @@ sj_status sj_sieve(sj_ctx* c, sj_rel rel, int nprobe, const int* key_cols, const
 }  // extern "C"
 
 namespace {
+// Called once per relation as soon as its last sieve step is enqueued.
+using FinalHook = std::function<sj_status(int rel, const sj_rel_s* r)>;
 sj_status sieve_path_impl(sj_ctx* c, const sj_path* path, const sj_sieve_opts* opts, sj_rel* out_sieved,
-                          sj_sieve_stats* stats, bool sync_end);
+                          sj_sieve_stats* stats, bool sync_end, const FinalHook* on_final = nullptr);
 }
 
 extern "C" sj_status sj_sieve_path(sj_ctx* c, const sj_path* path, const sj_sieve_opts* opts,
@@ -877,7 +880,7 @@ namespace {
 // every output handle knows its row count; without it the outputs keep their
 // counts on the device only (nrows = -1) for a device-sized join to read.
 sj_status sieve_path_impl(sj_ctx* c, const sj_path* path, const sj_sieve_opts* opts, sj_rel* out_sieved,
-                          sj_sieve_stats* stats, bool sync_end) {
+                          sj_sieve_stats* stats, bool sync_end, const FinalHook* on_final) {
   if (!c || !path || !out_sieved) return fail(c, SJ_EINVAL, "null argument");
   Tree tr;
   SJ_TRY(validate_path(c, path, path->rels, &tr));
@@ -927,10 +930,13 @@ sj_status sieve_path_impl(sj_ctx* c, const sj_path* path, const sj_sieve_opts* o
     return SJ_OK;
   };
 
+  auto final_of = [&](int i) -> sj_status { return on_final ? (*on_final)(i, rel_of(i)) : SJ_OK; };
   sj_status st = SJ_OK;
   for (int i = 0; i < n && st == SJ_OK; ++i)
     if (has_pred(path, i))
       st = do_step(i, 0, {{path->preds[i].col, true, path->preds[i].lo, path->preds[i].hi, nullptr}});
+  if (o.passes == SJ_NO_SIEVE || n == 1)
+    for (int i = 0; i < n && st == SJ_OK; ++i) st = final_of(i);
   if (st == SJ_OK && o.passes != SJ_NO_SIEVE && n > 1) {
     std::vector<sj_filter> up(n, nullptr), down(n, nullptr);
     if (o.passes == SJ_FWD_BWD) {
@@ -959,6 +965,7 @@ sj_status sieve_path_impl(sj_ctx* c, const sj_path* path, const sj_sieve_opts* o
       if (st != SJ_OK) break;
       if (tr.parent[v] >= 0)
         st = do_step(v, 2, {{edge_col(path->edges[tr.pedge[v]], v), false, 0, 0, down[v]}});
+      if (st == SJ_OK) st = final_of(v);  // v is not sieved again
       for (int ch : tr.children[v]) {
         if (st != SJ_OK) break;
         st = do_build(v, edge_col(path->edges[tr.pedge[ch]], v), &down[ch]);
@@ -1627,7 +1634,7 @@ sj_status ensure_side(sj_ctx* c, int nlev) {
 // returns kRetry (the caller reruns the exact, synchronising join).
 sj_status join_async(sj_ctx* c, const sj_path* path, const sj_rel* in_rels, int nrefs,
                      const sj_colref* refs, const std::vector<uint64_t>& caps, sj_result* result,
-                     std::vector<uint64_t>* levelT) {
+                     std::vector<uint64_t>* levelT, const std::vector<Adjacency>* prebuilt) {
   const int n = path->nrel;
   std::vector<const sj_rel_s*> rels(in_rels, in_rels + n);
   const std::vector<LevelPlan> plan = join_order(path);
@@ -1652,7 +1659,10 @@ sj_status join_async(sj_ctx* c, const sj_path* path, const sj_rel* in_rels, int 
   const int nlev = (int)plan.size() - 1;
   std::vector<Adjacency> built(std::max(nlev, 0));
   SideDrain drain{c};
-  if (nlev > 0) {
+  if (prebuilt) {
+    if ((int)prebuilt->size() != nlev) return kRetry;
+    built = *prebuilt;  // enqueued on the side stream during the pruning phase
+  } else if (nlev > 0) {
     SJ_TRY(ensure_side(c, nlev));
     SJ_CUDA(c, cudaEventRecord(c->ev_ready, c->stream));
     OnSide side(c);
@@ -2082,8 +2092,32 @@ extern "C" sj_status sj_sieve_join(sj_ctx* c, const sj_path* path, const sj_siev
     std::vector<uint64_t> caps;
     for (uint64_t t : it->second) caps.push_back(2 * t + 4096);
     const size_t p0 = c->prof.size();
-    st = sieve_path_impl(c, path, opts, sieved, nullptr, false);
-    if (st == SJ_OK) st = join_async(c, path, sieved, nrefs, refs, caps, result, &T);
+    // each multimap level's relation is final as soon as its last sieve step is
+    // enqueued: its build starts then, on the side stream, overlapping the
+    // remaining sieve steps
+    const std::vector<LevelPlan> plan = join_order(path);
+    const int nlev = (int)plan.size() - 1;
+    std::vector<int> level_of(path->nrel, -1);
+    for (int L = 0; L < nlev; ++L) level_of[plan[L].rel] = L;
+    std::vector<Adjacency> built(std::max(nlev, 0));
+    Temps bt(c);  // arena memory: lives until the scope ends
+    st = SJ_OK;
+    uint32_t* smallb = bt.get<uint32_t>(2 * SJ_MAX_REL, &st);
+    if (st == SJ_OK) st = ensure_side(c, nlev);
+    const FinalHook hook = [&](int i, const sj_rel_s* r) -> sj_status {
+      const int L = level_of[i];
+      if (L < 0) return SJ_OK;
+      SJ_CUDA(c, cudaEventRecord(c->ev_ready, c->stream));
+      OnSide side(c);
+      SJ_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_ready, 0));
+      SJ_TRY(build_adjacency_dev(c, bt, r->cols[plan[L].rel_col], r->d_n, r->nrows, rel_cap(r),
+                                 smallb + 2 * L, smallb + 2 * L + 1, &built[L]));
+      SJ_CUDA(c, cudaEventRecord(c->ev_built[L], c->stream));
+      return SJ_OK;
+    };
+    if (st == SJ_OK) st = sieve_path_impl(c, path, opts, sieved, nullptr, false, &hook);
+    if (st == SJ_OK) st = join_async(c, path, sieved, nrefs, refs, caps, result, &T, &built);
+    if (c->side) cudaStreamSynchronize(c->side);  // before the arena is released
     if (st == SJ_OK) prof_resolve(c, p0);
     if (st == kRetry) {
       // an intermediate outgrew its buffer: take the sizes to the host and rerun
