@@ -69,6 +69,24 @@ struct sj_ctx {
   uint32_t epoch2 = 0;
   cudaEvent_t ev_ready = nullptr;
   cudaEvent_t ev_built[SJ_MAX_REL] = {};
+  // CUDA graphs of the device-sized sieved join, per query shape: a repeated
+  // query replays one graph instead of enqueueing ~40 operations.  A graph
+  // bakes in arena addresses (valid while arena_gen is unchanged) and the
+  // intermediate buffer sizes it was captured with.
+  struct GraphEntry {
+    cudaGraphExec_t exec = nullptr;
+    std::vector<uint64_t> caps;
+    uint64_t gen = 0;
+    int64_t nkernels = 0;
+    bool failed = false;        // capture not possible for this shape
+    std::vector<ProfRec> prof;  // launch events inside the graph (profiled capture); owned
+  };
+  std::map<uint64_t, GraphEntry> graphs;  // key: query signature, profiling flag
+  int64_t graph_replays = 0, graph_captures = 0, graph_failures = 0;
+  std::string graph_why;
+  bool capturing = false;  // no allocator calls while a graph is captured
+  cudaStream_t cap_stream = nullptr;  // captures run here (the user's stream may be the legacy one)
+  uint64_t arena_gen = 0;
   // per query shape: output tuples of each join level in the last exact run,
   // used to size the buffers of the device-sized (host-sync-free) join
   std::map<uint64_t, std::vector<uint64_t>> plan_caps;
@@ -77,7 +95,7 @@ struct sj_ctx {
   struct {
     bool on = false;
     uint8_t* base = nullptr;
-    size_t size = 0, off = 0, peak = 0;
+    size_t size = 0, off = 0, peak = 0, spilled = 0;
     std::vector<std::pair<void*, size_t>> overflow;
   } arena;
   int64_t launches = 0;
@@ -134,6 +152,7 @@ sj_status fail(sj_ctx* c, sj_status s, const std::string& msg) {
 
 void* raw_alloc(sj_ctx* c, size_t bytes) {
   void* p = nullptr;
+  if (c->capturing) return nullptr;  // the capture is abandoned instead
   if (c->alloc) {
     p = c->alloc(bytes, c->user);
   } else if (cudaMallocAsync(&p, bytes, c->stream) != cudaSuccess) {
@@ -165,10 +184,12 @@ void* dalloc(sj_ctx* c, size_t bytes, bool persistent = false) {
     if (A.off + bytes <= A.size) {
       void* p = A.base + A.off;
       A.off += bytes;
-      A.peak = std::max(A.peak, A.off);
+      A.peak = std::max(A.peak, A.off + A.spilled);
       return p;
     }
-    A.peak = std::max(A.peak, A.off + bytes);
+    // counted in full, so that the arena grows to hold every block of the scope
+    A.spilled += bytes;
+    A.peak = std::max(A.peak, A.off + A.spilled);
     void* p = raw_alloc(c, bytes);
     if (p) A.overflow.emplace_back(p, bytes);
     return p;
@@ -191,6 +212,7 @@ void arena_begin(sj_ctx* c) {
   c->arena.on = true;
   c->arena.off = 0;
   c->arena.peak = 0;
+  c->arena.spilled = 0;
 }
 
 // End the scope: release overflow blocks and grow the arena to the peak seen,
@@ -206,6 +228,7 @@ void arena_end(sj_ctx* c) {
     const size_t nb = round_up(A.peak + A.peak / 4, 1 << 20);
     A.base = static_cast<uint8_t*>(raw_alloc(c, nb));
     A.size = A.base ? nb : 0;
+    c->arena_gen++;  // graphs holding the old addresses are stale
   }
   A.off = 0;
 }
@@ -230,6 +253,46 @@ struct Temps {
     return static_cast<T*>(p);
   }
 };
+
+// Reasons of failed captures, each kept once.
+void note_graph_failure(sj_ctx* c, const std::string& why) {
+  if (c->graph_why.find(why) != std::string::npos || c->graph_why.size() > 400) return;
+  if (!c->graph_why.empty()) c->graph_why += "; ";
+  c->graph_why += why;
+}
+
+void drop_graph(sj_ctx::GraphEntry& G) {
+  if (G.exec) cudaGraphExecDestroy(G.exec);
+  for (auto& r : G.prof) {
+    cudaEventDestroy(r.e0);
+    cudaEventDestroy(r.e1);
+  }
+  G = sj_ctx::GraphEntry{};
+}
+
+// Profiling of one replay: the graph's own launch events, resolved with the
+// per-step counts the replay copied back.
+void prof_replay(sj_ctx* c, const sj_ctx::GraphEntry& G) {
+  for (size_t i = 0; i < G.prof.size(); ++i) {
+    const ProfRec& r = G.prof[i];
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.e0, r.e1) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    double bytes = r.bytes;
+    if (r.slot_a >= 0) bytes += r.per_a * (double)c->h_misc[kMiscSteps + r.slot_a];
+    if (r.slot_b >= 0) bytes += r.per_b * (double)c->h_misc[kMiscSteps + r.slot_b];
+    c->prof_ms[r.kind] += ms;
+    c->prof_bytes[r.kind] += bytes;
+    c->prof_n[r.kind] += 1;
+    float gap = 0.f;
+    if (i + 1 < G.prof.size() && cudaEventElapsedTime(&gap, r.e1, G.prof[i + 1].e0) == cudaSuccess &&
+        gap > 0.f)
+      c->prof_gap_ms[r.kind] += gap;
+    cudaGetLastError();
+  }
+}
 
 cudaEvent_t take_event(sj_ctx* c) {
   if (c->ev_used == c->ev_pool.size()) {
@@ -258,12 +321,18 @@ struct Launch {
     rec.per_b = per_b;
     rec.e0 = take_event(c);
     rec.e1 = take_event(c);
-    if (rec.e0) cudaEventRecord(rec.e0, c->stream);
+    if (rec.e0) record(rec.e0);
   }
   ~Launch() {
     if (!on || !rec.e0 || !rec.e1) return;
-    cudaEventRecord(rec.e1, c->stream);
+    record(rec.e1);
     c->prof.push_back(rec);
+  }
+  // inside a graph capture the record must become a node of its own, so that
+  // every replay records the event
+  void record(cudaEvent_t e) {
+    if (c->capturing) cudaEventRecordWithFlags(e, c->stream, cudaEventRecordExternal);
+    else cudaEventRecord(e, c->stream);
   }
 };
 
@@ -274,11 +343,8 @@ sj_status check_launch(sj_ctx* c, const char* what) {
 }
 
 // Synchronise, read the misc block back and turn device status bits into errors.
-sj_status sync_read(sj_ctx* c) {
-  SJ_CUDA(c, cudaMemcpyAsync(c->h_misc, c->d_misc, kMiscWords * sizeof(uint64_t),
-                             cudaMemcpyDeviceToHost, c->stream));
-  c->d2h_bytes += kMiscWords * sizeof(uint64_t);
-  SJ_CUDA(c, cudaStreamSynchronize(c->stream));
+// Status bits of h_misc (already copied back and synchronised).
+sj_status read_status(sj_ctx* c) {
   const uint32_t st = (uint32_t)(c->h_misc[kMiscStatus] & 0xffffffffu);
   if (st) {
     SJ_CUDA(c, cudaMemsetAsync(c->d_misc + kMiscStatus, 0, sizeof(uint64_t), c->stream));
@@ -288,6 +354,19 @@ sj_status sync_read(sj_ctx* c) {
     return fail(c, SJ_ECUDA, "device status word set");
   }
   return SJ_OK;
+}
+
+sj_status enqueue_readback(sj_ctx* c) {
+  SJ_CUDA(c, cudaMemcpyAsync(c->h_misc, c->d_misc, kMiscWords * sizeof(uint64_t),
+                             cudaMemcpyDeviceToHost, c->stream));
+  c->d2h_bytes += kMiscWords * sizeof(uint64_t);
+  return SJ_OK;
+}
+
+sj_status sync_read(sj_ctx* c) {
+  SJ_TRY(enqueue_readback(c));
+  SJ_CUDA(c, cudaStreamSynchronize(c->stream));
+  return read_status(c);
 }
 
 uint32_t* status_ptr(sj_ctx* c) { return reinterpret_cast<uint32_t*>(c->d_misc + kMiscStatus); }
@@ -306,6 +385,7 @@ sj_status scratch_for(sj_ctx* c, int64_t ntiles, uint32_t** counter, LookBack<NC
     const size_t nb = round_up(std::max(need, c->scratch_bytes * 2));
     c->scratch = static_cast<uint8_t*>(dalloc(c, nb, true));
     c->scratch_bytes = c->scratch ? nb : 0;
+    c->arena_gen++;  // graphs holding the old scratch are stale
     if (!c->scratch) return fail(c, SJ_ENOMEM, "scratch allocation failed");
     SJ_CUDA(c, cudaMemsetAsync(c->scratch, 0, nb, c->stream));
     c->epoch = 0;
@@ -698,6 +778,8 @@ sj_status sj_destroy(sj_ctx* c) {
     }
     cudaStreamDestroy(c->side);
   }
+  for (auto& kv : c->graphs) drop_graph(kv.second);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->ev_ready) cudaEventDestroy(c->ev_ready);
   for (auto e : c->ev_built)
     if (e) cudaEventDestroy(e);
@@ -1613,7 +1695,7 @@ struct OnSide {
 struct SideDrain {
   sj_ctx* c;
   ~SideDrain() {
-    if (c->side) cudaStreamSynchronize(c->side);
+    if (c->side && !c->capturing) cudaStreamSynchronize(c->side);
   }
 };
 
@@ -1628,13 +1710,16 @@ sj_status ensure_side(sj_ctx* c, int nlev) {
   return SJ_OK;
 }
 
+sj_status device_sized_result(sj_ctx* c, int nlev, sj_result* result, std::vector<uint64_t>* levelT);
+
 // COUNT/SUM join with every size kept on the device: no host round trip
 // until the one synchronisation at the end.  caps[L] bounds the output of
 // multimap level L; a level that outgrows it records kErrCapacity and the call
 // returns kRetry (the caller reruns the exact, synchronising join).
 sj_status join_async(sj_ctx* c, const sj_path* path, const sj_rel* in_rels, int nrefs,
                      const sj_colref* refs, const std::vector<uint64_t>& caps, sj_result* result,
-                     std::vector<uint64_t>* levelT, const std::vector<Adjacency>* prebuilt) {
+                     std::vector<uint64_t>* levelT, const std::vector<Adjacency>* prebuilt,
+                     bool finish = true) {
   const int n = path->nrel;
   std::vector<const sj_rel_s*> rels(in_rels, in_rels + n);
   const std::vector<LevelPlan> plan = join_order(path);
@@ -1808,13 +1893,19 @@ sj_status join_async(sj_ctx* c, const sj_path* path, const sj_rel* in_rels, int 
     }
     in = std::move(nx);
   }
+  if (!finish) return enqueue_readback(c);  // graph capture: results read at replay
   SJ_TRY(sync_read(c));
+  return device_sized_result(c, (int)plan.size() - 1, result, levelT);
+}
+
+// COUNT, SUM and per-level sizes of a finished device-sized join, from h_misc.
+sj_status device_sized_result(sj_ctx* c, int nlev, sj_result* result, std::vector<uint64_t>* levelT) {
   const uint64_t lo = c->h_misc[kMiscResult], hi = c->h_misc[kMiscResult + 1];
   if (hi != 0 || lo >= (1ull << 63)) return fail(c, SJ_EOVERFLOW, "COUNT(*) reached 2^63");
   memset(result, 0, sizeof(*result));
   result->count = lo;
   result->sum = c->h_misc[kMiscResult + 2];
-  for (size_t L = 0; L + 1 < plan.size(); ++L) {
+  for (int L = 0; L < nlev; ++L) {
     const uint64_t T = c->h_misc[kMiscLevelTotals + 2 * L + 1];
     result->intermediate += T;
     if (levelT) levelT->push_back(T);
@@ -1834,8 +1925,12 @@ uint64_t path_signature(const sj_path* p, const sj_sieve_opts* o, int mode, int 
   h = mix_in(h, (uint64_t)p->nrel);
   h = mix_in(h, (uint64_t)(int64_t)p->root);
   for (int i = 0; i < p->nrel; ++i) {
-    h = mix_in(h, (uint64_t)reinterpret_cast<uintptr_t>(p->rels[i]));
-    h = mix_in(h, (uint64_t)p->rels[i]->nrows);
+    // the device addresses too: a graph of this shape reads them directly
+    const sj_rel_s* r = p->rels[i];
+    h = mix_in(h, (uint64_t)reinterpret_cast<uintptr_t>(r));
+    h = mix_in(h, (uint64_t)r->nrows);
+    h = mix_in(h, (uint64_t)reinterpret_cast<uintptr_t>(r->d_n));
+    for (int j = 0; j < r->ncols; ++j) h = mix_in(h, (uint64_t)reinterpret_cast<uintptr_t>(r->cols[j]));
     if (p->preds)
       h = mix_in(h, ((uint64_t)(uint32_t)p->preds[i].col << 40) ^ ((uint64_t)(uint32_t)p->preds[i].lo << 20) ^
                         (uint64_t)(uint32_t)p->preds[i].hi);
@@ -1848,8 +1943,14 @@ uint64_t path_signature(const sj_path* p, const sj_sieve_opts* o, int mode, int 
     h = mix_in(h, ((uint64_t)o->filter.bits_per_key << 32) ^ ((uint64_t)o->filter.k << 8) ^ o->filter.layout);
     h = mix_in(h, o->filter.seed);
     if (o->leaf_filters)
-      for (int i = 0; i < p->nrel; ++i)
-        h = mix_in(h, (uint64_t)reinterpret_cast<uintptr_t>(o->leaf_filters[i]));
+      for (int i = 0; i < p->nrel; ++i) {
+        const sj_filter_s* f = o->leaf_filters[i];
+        h = mix_in(h, (uint64_t)reinterpret_cast<uintptr_t>(f));
+        if (f) {
+          h = mix_in(h, (uint64_t)reinterpret_cast<uintptr_t>(f->words));
+          h = mix_in(h, (uint64_t)reinterpret_cast<uintptr_t>(f->hdr));
+        }
+      }
   }
   h = mix_in(h, (uint64_t)mode);
   for (int k = 0; k < nrefs; ++k)
@@ -1921,6 +2022,19 @@ sj_status sj_prof_gaps(sj_ctx* c, double* gap_ms) {
   if (!c || !gap_ms) return SJ_EINVAL;
   SJ_TRY(prof_collect(c));
   for (int k = 0; k < SJ_K_COUNT; ++k) gap_ms[k] = c->prof_gap_ms[k];
+  return SJ_OK;
+}
+
+sj_status sj_graph_stats(sj_ctx* c, int64_t* replays, int64_t* captures, int64_t* failures, char* why,
+                         int len) {
+  if (!c) return SJ_EINVAL;
+  if (replays) *replays = c->graph_replays;
+  if (captures) *captures = c->graph_captures;
+  if (failures) *failures = c->graph_failures;
+  if (why && len > 0) {
+    strncpy(why, c->graph_why.c_str(), (size_t)len - 1);
+    why[len - 1] = 0;
+  }
   return SJ_OK;
 }
 
@@ -2073,6 +2187,118 @@ extern "C" sj_status sj_triangles(sj_ctx* c, sj_rel edges, int nsub, const int32
   return SJ_OK;
 }
 
+namespace {
+
+// Pruning phase and device-sized join enqueued back to back.  Each multimap
+// level's relation is final as soon as its last sieve step is enqueued: its
+// build starts then, on the side stream, overlapping the remaining sieve
+// steps.  With finish = false nothing waits (graph capture).
+sj_status run_device_sized(sj_ctx* c, const sj_path* path, const sj_sieve_opts* opts, int nrefs,
+                           const sj_colref* refs, const std::vector<uint64_t>& caps, sj_rel* sieved,
+                           sj_result* result, std::vector<uint64_t>* T, bool finish) {
+  const std::vector<LevelPlan> plan = join_order(path);
+  const int nlev = (int)plan.size() - 1;
+  std::vector<int> level_of(path->nrel, -1);
+  for (int L = 0; L < nlev; ++L) level_of[plan[L].rel] = L;
+  std::vector<Adjacency> built(std::max(nlev, 0));
+  Temps bt(c);  // arena memory: lives until the arena scope ends
+  sj_status st = SJ_OK;
+  uint32_t* smallb = bt.get<uint32_t>(2 * SJ_MAX_REL, &st);
+  if (st != SJ_OK) return fail(c, st, "allocation failed");
+  SJ_TRY(ensure_side(c, nlev));
+  const FinalHook hook = [&](int i, const sj_rel_s* r) -> sj_status {
+    const int L = level_of[i];
+    if (L < 0) return SJ_OK;
+    SJ_CUDA(c, cudaEventRecord(c->ev_ready, c->stream));
+    OnSide side(c);
+    SJ_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_ready, 0));
+    SJ_TRY(build_adjacency_dev(c, bt, r->cols[plan[L].rel_col], r->d_n, r->nrows, rel_cap(r),
+                               smallb + 2 * L, smallb + 2 * L + 1, &built[L]));
+    SJ_CUDA(c, cudaEventRecord(c->ev_built[L], c->stream));
+    return SJ_OK;
+  };
+  st = sieve_path_impl(c, path, opts, sieved, nullptr, false, &hook);
+  if (st == SJ_OK) st = join_async(c, path, sieved, nrefs, refs, caps, result, T, &built, finish);
+  if (c->side && !c->capturing) cudaStreamSynchronize(c->side);  // before the arena is released
+  return st;
+}
+
+// Capture the device-sized query as a CUDA graph for later calls of the same
+// shape.  Runs in its own arena scope, after a plain run sized the arena.
+void capture_graph(sj_ctx* c, uint64_t key, const sj_path* path, const sj_sieve_opts* opts, int nrefs,
+                   const sj_colref* refs, const std::vector<uint64_t>& caps) {
+  auto& G = c->graphs[key];
+  drop_graph(G);
+  G.failed = true;
+  const int64_t launches0 = c->launches, d2h0 = c->d2h_bytes;
+  const size_t prof0 = c->prof.size(), ev0 = c->ev_used;
+  arena_begin(c);
+  const uint64_t gen = c->arena_gen;
+  sj_rel sieved[SJ_MAX_REL] = {};
+  cudaGraph_t graph = nullptr;
+  if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    c->cap_stream = nullptr;
+  }
+  // the user's stream (possibly the legacy default stream, which cannot be
+  // captured) is set aside while the capture runs on the private stream
+  const bool swapped = c->cap_stream != nullptr;
+  if (swapped) std::swap(c->stream, c->cap_stream);
+  if (swapped && cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+    c->capturing = true;
+    // look-back flags and tile tickets start from zero in every replay
+    sj_status st = SJ_OK;
+    if (c->scratch && cudaMemsetAsync(c->scratch, 0, c->scratch_bytes, c->stream) != cudaSuccess)
+      st = SJ_ECUDA;
+    if (st == SJ_OK && c->scratch2 &&
+        cudaMemsetAsync(c->scratch2, 0, c->scratch2_bytes, c->stream) != cudaSuccess)
+      st = SJ_ECUDA;
+    sj_result dummy;
+    if (st == SJ_OK) st = run_device_sized(c, path, opts, nrefs, refs, caps, sieved, &dummy, nullptr, false);
+    c->capturing = false;
+    if (st != SJ_OK) note_graph_failure(c, "enqueue: " + c->err);
+    const cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+    if (e != cudaSuccess) note_graph_failure(c, std::string("end capture: ") + cudaGetErrorString(e));
+    cudaError_t ei = cudaSuccess;
+    if (st == SJ_OK && e == cudaSuccess && graph &&
+        (ei = cudaGraphInstantiate(&G.exec, graph, 0)) == cudaSuccess) {
+      G.failed = false;
+      G.caps = caps;
+      G.nkernels = c->launches - launches0;
+    } else {
+      if (ei != cudaSuccess) note_graph_failure(c, std::string("instantiate: ") + cudaGetErrorString(ei));
+      G.exec = nullptr;
+    }
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+  } else {
+    note_graph_failure(c, "begin capture failed");
+    cudaGetLastError();
+  }
+  // the launch events recorded inside the graph now belong to it
+  G.prof.assign(c->prof.begin() + prof0, c->prof.end());
+  c->prof.resize(prof0);
+  c->ev_pool.erase(c->ev_pool.begin() + ev0, c->ev_pool.begin() + c->ev_used);
+  c->ev_used = ev0;
+  if (swapped) std::swap(c->stream, c->cap_stream);
+  for (int i = 0; i < path->nrel; ++i) free_rel(c, sieved[i]);
+  arena_end(c);
+  if (c->arena_gen != gen && G.exec) {  // the capture outgrew the arena
+    drop_graph(G);
+    G.failed = true;
+    note_graph_failure(c, "arena grew during capture");
+  }
+  // a capture that failed because the arena was too small is retried by the
+  // next call (the arena has grown since); other failures are final
+  G.gen = (G.failed && c->arena_gen != gen) ? gen : c->arena_gen;
+  if (G.failed) c->graph_failures++;
+  else c->graph_captures++;
+  c->launches = launches0;
+  c->d2h_bytes = d2h0;
+}
+
+}  // namespace
+
 extern "C" sj_status sj_sieve_join(sj_ctx* c, const sj_path* path, const sj_sieve_opts* opts,
                                    int mode, int nrefs, const sj_colref* refs, sj_result* result,
                                    sj_sieve_stats* stats) {
@@ -2085,67 +2311,90 @@ extern "C" sj_status sj_sieve_join(sj_ctx* c, const sj_path* path, const sj_siev
   auto it = c->plan_caps.find(sig);
   const bool device_sized = mode == SJ_COUNT_SUM && path->nrel >= 2 && !stats && it != c->plan_caps.end();
   std::vector<uint64_t> T;
-  arena_begin(c);
-  sj_status st;
+  sj_status st = SJ_OK;
+  bool exact = !device_sized;
   if (device_sized) {
     // sizes stay on the device: one synchronisation for the whole query
     std::vector<uint64_t> caps;
     for (uint64_t t : it->second) caps.push_back(2 * t + 4096);
-    const size_t p0 = c->prof.size();
-    // each multimap level's relation is final as soon as its last sieve step is
-    // enqueued: its build starts then, on the side stream, overlapping the
-    // remaining sieve steps
-    const std::vector<LevelPlan> plan = join_order(path);
-    const int nlev = (int)plan.size() - 1;
-    std::vector<int> level_of(path->nrel, -1);
-    for (int L = 0; L < nlev; ++L) level_of[plan[L].rel] = L;
-    std::vector<Adjacency> built(std::max(nlev, 0));
-    Temps bt(c);  // arena memory: lives until the scope ends
-    st = SJ_OK;
-    uint32_t* smallb = bt.get<uint32_t>(2 * SJ_MAX_REL, &st);
-    if (st == SJ_OK) st = ensure_side(c, nlev);
-    const FinalHook hook = [&](int i, const sj_rel_s* r) -> sj_status {
-      const int L = level_of[i];
-      if (L < 0) return SJ_OK;
-      SJ_CUDA(c, cudaEventRecord(c->ev_ready, c->stream));
-      OnSide side(c);
-      SJ_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_ready, 0));
-      SJ_TRY(build_adjacency_dev(c, bt, r->cols[plan[L].rel_col], r->d_n, r->nrows, rel_cap(r),
-                                 smallb + 2 * L, smallb + 2 * L + 1, &built[L]));
-      SJ_CUDA(c, cudaEventRecord(c->ev_built[L], c->stream));
-      return SJ_OK;
-    };
-    if (st == SJ_OK) st = sieve_path_impl(c, path, opts, sieved, nullptr, false, &hook);
-    if (st == SJ_OK) st = join_async(c, path, sieved, nrefs, refs, caps, result, &T, &built);
-    if (c->side) cudaStreamSynchronize(c->side);  // before the arena is released
-    if (st == SJ_OK) prof_resolve(c, p0);
-    if (st == kRetry) {
-      // an intermediate outgrew its buffer: take the sizes to the host and rerun
-      // the enumeration exactly
-      T.clear();
-      st = SJ_OK;
-      prof_resolve(c, p0);
-      for (int i = 0; i < path->nrel && st == SJ_OK; ++i) {
-        if (sieved[i] && sieved[i]->d_n && sieved[i]->nrows < 0) {
-          uint64_t v = 0;
-          if (cudaMemcpyAsync(&v, sieved[i]->d_n, 8, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
-              cudaStreamSynchronize(c->stream) != cudaSuccess)
-            st = fail(c, SJ_ECUDA, "row count readback failed");
-          sieved[i]->nrows = (int64_t)v;
-        }
+    const uint64_t gkey = sig * 2 + (c->prof_on ? 1 : 0);
+    auto g = c->graphs.find(gkey);
+    const bool replay = g != c->graphs.end() && g->second.exec && g->second.caps == caps &&
+                        g->second.gen == c->arena_gen;
+    if (replay) {
+      // the whole query is one graph launch and one synchronisation
+      if (cudaGraphLaunch(g->second.exec, c->stream) != cudaSuccess ||
+          cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, SJ_ECUDA, "graph replay failed");
       }
-      if (st == SJ_OK) st = join_impl(c, path, sieved, mode, nrefs, refs, result, &T);
+      c->launches += g->second.nkernels;
+      c->d2h_bytes += kMiscWords * sizeof(uint64_t);
+      c->graph_replays++;
+      if (c->prof_on) prof_replay(c, g->second);
+      st = read_status(c);
+      if (st == SJ_OK) st = device_sized_result(c, (int)caps.size(), result, &T);
+      if (st == kRetry) {
+        T.clear();
+        exact = true;  // an intermediate outgrew its buffer: exact rerun
+      } else if (st != SJ_OK) {
+        return st;
+      }
+    } else {
+      arena_begin(c);
+      const size_t p0 = c->prof.size();
+      st = run_device_sized(c, path, opts, nrefs, refs, caps, sieved, result, &T, true);
+      if (st == SJ_OK) prof_resolve(c, p0);
+      if (st == kRetry) {
+        // an intermediate outgrew its buffer: take the sizes to the host and
+        // rerun the enumeration exactly
+        T.clear();
+        st = SJ_OK;
+        prof_resolve(c, p0);
+        for (int i = 0; i < path->nrel && st == SJ_OK; ++i) {
+          if (sieved[i] && sieved[i]->d_n && sieved[i]->nrows < 0) {
+            uint64_t v = 0;
+            if (cudaMemcpyAsync(&v, sieved[i]->d_n, 8, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+                cudaStreamSynchronize(c->stream) != cudaSuccess)
+              st = fail(c, SJ_ECUDA, "row count readback failed");
+            sieved[i]->nrows = (int64_t)v;
+          }
+        }
+        if (st == SJ_OK) st = join_impl(c, path, sieved, mode, nrefs, refs, result, &T);
+      }
+      for (int i = 0; i < path->nrel; ++i) {
+        free_rel(c, sieved[i]);
+        sieved[i] = nullptr;
+      }
+      arena_end(c);
+      const bool capture = st == SJ_OK && (g == c->graphs.end() || !g->second.failed || g->second.gen != c->arena_gen);
+      if (st == SJ_OK) {
+        if (c->plan_caps.size() > 4096) c->plan_caps.clear();
+        c->plan_caps[sig] = T;
+      }
+      if (capture) {
+        std::vector<uint64_t> next;
+        for (uint64_t t : T) next.push_back(2 * t + 4096);
+        if (c->graphs.size() >= 64) {
+          for (auto& kv : c->graphs) drop_graph(kv.second);
+          c->graphs.clear();
+        }
+        capture_graph(c, gkey, path, opts, nrefs, refs, next);
+      }
+      return st;
     }
-  } else {
+  }
+  if (exact) {
+    arena_begin(c);
     st = sieve_path_impl(c, path, opts, sieved, stats, true);
     if (st == SJ_OK) st = join_impl(c, path, sieved, mode, nrefs, refs, result, &T);
+    for (int i = 0; i < path->nrel; ++i) free_rel(c, sieved[i]);
+    arena_end(c);
   }
   if (st == SJ_OK && mode == SJ_COUNT_SUM && path->nrel >= 2) {
     if (c->plan_caps.size() > 4096) c->plan_caps.clear();
     c->plan_caps[sig] = T;
   }
-  for (int i = 0; i < path->nrel; ++i) free_rel(c, sieved[i]);
-  arena_end(c);
   return st;
 }
 

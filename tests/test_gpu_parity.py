@@ -359,9 +359,14 @@ def test_sieve_join_device_sized_repeat(ctx, kind, passes):
         w = inputs.random_tree_join(g, 6, g.integers(3000, 40_000, 6), 5000)
     rels = load(ctx, w)
     exp = oracle.agg_propagation(w)
-    for _ in range(3):
+    g0 = ctx.graph_stats()
+    # call 1 exact, call 2 device-sized (and captured as a graph), then replays
+    for _ in range(5):
         got = ctx.sieve_join(rels, w["edges"], w["preds"], w["root"], refs=w["sum"], passes=passes)
         assert (got["count"], got["sum"]) == (exp["count"], exp["sum"])
+    g1 = ctx.graph_stats()
+    assert g1["replays"] - g0["replays"] == 3, g1
+    assert g1["failures"] == g0["failures"], g1
 
 
 def test_sieve_join_device_sized_overflow_falls_back(ctx):
@@ -388,6 +393,20 @@ def test_sieve_join_device_sized_overflow_falls_back(ctx):
             dev[r][j].copy_(torch.from_numpy(cols[r][j]))
     torch.cuda.synchronize()
     exp = oracle.agg_propagation(w)
-    for _ in range(2):
+    for _ in range(4):
         got = ctx.sieve_join(rels, w["edges"], w["preds"], w["root"], refs=w["sum"])
         assert (got["count"], got["sum"]) == (exp["count"], exp["sum"])
+
+
+def test_sieve_join_reloaded_relations_not_replayed(ctx):
+    """Relations freed and reloaded with the same sizes but other data: the
+    query shape cache must not replay work that read the old buffers."""
+    for seed in (41, 42, 43):
+        w = inputs.uniform_chain(nrel=3, nrows=30_000, domain=5_000, seed=seed)
+        rels = load(ctx, w)
+        exp = oracle.agg_propagation(w)
+        for _ in range(3):
+            got = ctx.sieve_join(rels, w["edges"], w["preds"], w["root"], refs=w["sum"])
+            assert (got["count"], got["sum"]) == (exp["count"], exp["sum"])
+        for r in rels:
+            r.free()
