@@ -493,7 +493,11 @@ def main():
     res0, steps0 = sieved_step(ctx, rels, w, stats=True)
 
     # ---- device-resident sieved join (the headline value)
+    # Only the roofline kernel class is timed with events inside the timed
+    # region (each profiled launch adds two event-record nodes to the replayed
+    # CUDA graph); the per-class breakdown comes from a separate pass below.
     ctx.prof_reset()
+    ctx.prof_kinds(["sieve"])
     ctx.prof_enable(True)
     with ClockSampler(local) as clk:
         # warm-up (profiled like the timed steps, so that the CUDA graph the
@@ -501,12 +505,21 @@ def main():
         for _ in range(args.warmup):
             sieved_step(ctx, rels, w)
         ctx.prof_reset()
-        ctx.prof_enable(True)
         total_ms, (res, st) = timed(torch, stream, lambda: sieved_step(ctx, rels, w),
                                     args.steps, 0, flush, ws)
         ctx.prof_enable(False)
     counters = ctx.counters()
     graphs = ctx.graph_stats()
+    sv_live = ctx.prof_read("sieve")
+    # per-class breakdown: every class profiled, its own graph, fewer steps
+    bsteps = max(1, min(args.steps, 50))
+    ctx.prof_kinds(None)
+    ctx.prof_enable(True)
+    for _ in range(args.warmup):
+        sieved_step(ctx, rels, w)
+    ctx.prof_reset()
+    bms, _ = timed(torch, stream, lambda: sieved_step(ctx, rels, w), bsteps, 0, flush, ws)
+    ctx.prof_enable(False)
     kstats = {k: ctx.prof_read(k) for k in sj.KERNEL_KINDS}
     gaps = ctx.prof_gaps()
     total_ms = max_over_ranks(total_ms, ws)
@@ -557,7 +570,7 @@ def main():
     if rank != 0:
         return
     peak, peak_kind = load_peaks()
-    sv = kstats["sieve"]
+    sv = sv_live
     achieved = sv["bytes"] / (sv["ms"] / 1000.0) / 1e9 if sv["ms"] > 0 else 0.0
     traffic = profiled_traffic("sieve", args.workload)
     clocks = clk.summary()
@@ -586,13 +599,14 @@ def main():
                      "avg_launch_ms": sv["ms"] / max(1, sv["launches"]),
                      "alg_bytes_per_launch": sv["bytes"] / max(1, sv["launches"]),
                      "share_of_step": sv["ms"] / total_ms if total_ms else None},
-        "kernels": {k: {"launches": v["launches"], "ms": v["ms"],
-                        "GBps": (v["bytes"] / (v["ms"] / 1000.0) / 1e9) if v["ms"] > 0 else None}
-                    for k, v in kstats.items() if v["launches"]},
+        "kernels": {"steps": bsteps, "ms_per_step_all_classes_profiled": bms / bsteps,
+                    **{k: {"launches": v["launches"], "ms_per_step": v["ms"] / bsteps,
+                           "GBps": (v["bytes"] / (v["ms"] / 1000.0) / 1e9) if v["ms"] > 0 else None}
+                       for k, v in kstats.items() if v["launches"]}},
         "serving": serving,
         "cyclic_triangles": cyclic,
         "star": star,
-        "device_idle_ms_per_step_after": {k: v / args.steps for k, v in gaps.items() if v},
+        "device_idle_ms_per_step_after": {k: v / bsteps for k, v in gaps.items() if v},
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)

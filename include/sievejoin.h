@@ -466,6 +466,11 @@ enum {
  * the bytes it copied host-to-device and device-to-host.
  */
 SJ_API sj_status sj_prof_enable(sj_ctx *ctx, int on);
+/* Restrict profiling to the kernel classes whose bit (1 << SJ_K_*) is set in
+ * `mask` (default: all).  Each profiled launch costs two event records, which
+ * inside a CUDA graph are nodes of their own: profiling one class keeps the
+ * timing of the others undisturbed. */
+SJ_API sj_status sj_prof_kinds(sj_ctx *ctx, uint32_t mask);
 SJ_API sj_status sj_prof_reset(sj_ctx *ctx);
 SJ_API sj_status sj_prof_read(sj_ctx *ctx, int kind, int64_t *launches, double *ms, double *bytes);
 SJ_API sj_status sj_counters(sj_ctx *ctx, int64_t *launches, int64_t *h2d_bytes, int64_t *d2h_bytes);

@@ -35,7 +35,7 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "out of device memory", 3: "hash ta
 EXPORTS = ["sj_create", "sj_destroy", "sj_sync", "sj_last_error", "sj_status_str", "sj_version",
            "sj_load_relation", "sj_rel_info", "sj_free_rel", "sj_build_filter", "sj_filter_info",
            "sj_filter_probe", "sj_free_filter", "sj_sieve", "sj_sieve_path", "sj_join",
-           "sj_prof_enable", "sj_prof_reset", "sj_prof_read", "sj_counters", "sj_graph_stats", "sj_sieve_noalloc",
+           "sj_prof_enable", "sj_prof_kinds", "sj_prof_reset", "sj_prof_read", "sj_counters", "sj_graph_stats", "sj_sieve_noalloc",
            "sj_server_create", "sj_server_add_relation", "sj_server_submit", "sj_server_poll",
            "sj_server_stats_get", "sj_server_destroy", "sj_triangles", "sj_sieve_join", "sj_prof_gaps",
            "sj_selftest_wait_timeout"]
@@ -158,7 +158,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "sj_sieve_path": [P, ctypes.POINTER(Path), ctypes.POINTER(SieveOpts), PP,
                           ctypes.POINTER(SieveStats)],
         "sj_join": [P, ctypes.POINTER(Path), PP, I, I, ctypes.POINTER(ColRef), ctypes.POINTER(Result)],
-        "sj_prof_enable": [P, I], "sj_prof_reset": [P],
+        "sj_prof_enable": [P, I], "sj_prof_kinds": [P, ctypes.c_uint32], "sj_prof_reset": [P],
         "sj_prof_read": [P, I, ctypes.POINTER(I64), ctypes.POINTER(ctypes.c_double),
                          ctypes.POINTER(ctypes.c_double)],
         "sj_counters": [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64)],
@@ -502,6 +502,11 @@ class Context:
     # --------------------------------------------------------------- profiling
     def prof_enable(self, on: bool = True):
         self._check(self.lib.sj_prof_enable(self.ctx, 1 if on else 0))
+
+    def prof_kinds(self, kinds=None):
+        """Profile only these kernel classes (names of KERNEL_KINDS; None = all)."""
+        mask = 0xFFFFFFFF if kinds is None else sum(1 << KERNEL_KINDS[k] for k in kinds)
+        self._check(self.lib.sj_prof_kinds(self.ctx, ctypes.c_uint32(mask)))
 
     def prof_reset(self):
         self._check(self.lib.sj_prof_reset(self.ctx))

@@ -102,6 +102,7 @@ struct sj_ctx {
   int64_t h2d_bytes = 0;
   int64_t d2h_bytes = 0;
   bool prof_on = false;
+  uint32_t prof_mask = 0xffffffffu;  // kernel classes profiled while prof_on
   std::vector<ProfRec> prof;
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
@@ -310,7 +311,7 @@ struct Launch {
   bool on;
   Launch(sj_ctx* cc, int kind, double bytes, int slot_a = -1, double per_a = 0, int slot_b = -1,
          double per_b = 0)
-      : c(cc), on(cc->prof_on) {
+      : c(cc), on(cc->prof_on && ((cc->prof_mask >> kind) & 1u)) {
     c->launches++;
     if (!on) return;
     rec.kind = kind;
@@ -1969,6 +1970,12 @@ sj_status sj_prof_enable(sj_ctx* c, int on) {
   return SJ_OK;
 }
 
+sj_status sj_prof_kinds(sj_ctx* c, uint32_t mask) {
+  if (!c) return SJ_EINVAL;
+  c->prof_mask = mask;
+  return SJ_OK;
+}
+
 static sj_status prof_collect(sj_ctx* c) {
   SJ_CUDA(c, cudaStreamSynchronize(c->stream));
   for (size_t i = 0; i < c->prof.size(); ++i) {
@@ -2317,7 +2324,7 @@ extern "C" sj_status sj_sieve_join(sj_ctx* c, const sj_path* path, const sj_siev
     // sizes stay on the device: one synchronisation for the whole query
     std::vector<uint64_t> caps;
     for (uint64_t t : it->second) caps.push_back(2 * t + 4096);
-    const uint64_t gkey = sig * 2 + (c->prof_on ? 1 : 0);
+    const uint64_t gkey = mix_in(sig, c->prof_on ? (uint64_t)c->prof_mask : 0ull);
     auto g = c->graphs.find(gkey);
     const bool replay = g != c->graphs.end() && g->second.exec && g->second.caps == caps &&
                         g->second.gen == c->arena_gen;

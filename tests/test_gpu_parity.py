@@ -410,3 +410,25 @@ def test_sieve_join_reloaded_relations_not_replayed(ctx):
             assert (got["count"], got["sum"]) == (exp["count"], exp["sum"])
         for r in rels:
             r.free()
+
+
+def test_profiled_graph_replays_report_kernel_times(ctx):
+    """With profiling on, replays of a captured query still report every
+    kernel class with positive device time."""
+    w = inputs.zipf_chain(nrows=100_000, domain=50_000, seed=51)
+    rels = load(ctx, w)
+    ctx.prof_enable(True)
+    try:
+        for _ in range(3):  # exact, device-sized + capture, replay
+            ctx.sieve_join(rels, w["edges"], w["preds"], w["root"], refs=w["sum"], passes=sj.BWD_ONLY)
+        ctx.prof_reset()
+        g0 = ctx.graph_stats()["replays"]
+        for _ in range(2):
+            ctx.sieve_join(rels, w["edges"], w["preds"], w["root"], refs=w["sum"], passes=sj.BWD_ONLY)
+        assert ctx.graph_stats()["replays"] - g0 == 2
+        sv = ctx.prof_read("sieve")
+        assert sv["launches"] == 2 * 3 and sv["ms"] > 0 and sv["bytes"] > 0
+        ag = ctx.prof_read("agg")
+        assert ag["launches"] > 0 and ag["ms"] > 0
+    finally:
+        ctx.prof_enable(False)
