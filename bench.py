@@ -56,7 +56,7 @@ WORKLOADS = {
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="sievejoin", choices=["sievejoin", "reference"])
     ap.add_argument("--workload", default="chain4_zipf", choices=sorted(WORKLOADS))
@@ -112,22 +112,63 @@ def max_over_ranks(x: float, ws: int) -> float:
 
 # ----------------------------------------------------------------------------- clocks
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    """SM clock and throttle reasons sampled during the timed region: NVML
+    queries every few milliseconds from a thread (read-only), or nvidia-smi's
+    query loop where NVML is unavailable."""
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    # NVML clocks-event reason bits
+    REASON_BITS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20,
+                   "hw_thermal_slowdown": 0x40}
 
     def __init__(self, device: int):
         self.device = device
         self.proc = None
         self.lines = []
         self.skip = 0
+        self.nvml = None
+        self.stop = False
+        self.source = None
+
+    def _nvml_handle(self):
+        import pynvml
+        pynvml.nvmlInit()
+        try:
+            import torch
+            uuid = str(torch.cuda.get_device_properties(self.device).uuid)
+            return pynvml, pynvml.nvmlDeviceGetHandleByUUID(("GPU-" + uuid).encode())
+        except Exception:
+            return pynvml, pynvml.nvmlDeviceGetHandleByIndex(self.device)
+
+    def _nvml_loop(self):
+        nv, h = self.nvml
+        mx = nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM)
+        while not self.stop:
+            try:
+                sm = nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM)
+                r = nv.nvmlDeviceGetCurrentClocksThrottleReasons(h)
+                flags = ["Active" if r & b else "Not Active" for b in
+                         (self.REASON_BITS["hw_slowdown"], self.REASON_BITS["hw_thermal_slowdown"],
+                          self.REASON_BITS["sw_thermal_slowdown"], self.REASON_BITS["sw_power_cap"])]
+                self.lines.append(", ".join([str(sm), str(mx), "", hex(r)] + flags))
+            except Exception:
+                pass
+            time.sleep(0.002)
 
     def __enter__(self):
         try:
+            self.nvml = self._nvml_handle()
+            self.th = threading.Thread(target=self._nvml_loop, daemon=True)
+            self.th.start()
+            self.source = "nvml"
+            return self
+        except Exception:
+            self.nvml = None
+        try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.th = threading.Thread(target=self._read, daemon=True)
             self.th.start()
@@ -135,6 +176,7 @@ class ClockSampler:
             while not self.lines and time.time() - t0 < 5.0:  # first sample before timing
                 time.sleep(0.02)
             self.skip = len(self.lines)
+            self.source = "nvidia-smi"
         except Exception:
             self.proc = None
         return self
@@ -144,6 +186,9 @@ class ClockSampler:
             self.lines.append(ln.strip())
 
     def __exit__(self, *a):
+        self.stop = True
+        if self.nvml:
+            self.th.join(timeout=2)
         if self.proc:
             self.proc.terminate()
             try:
@@ -170,7 +215,7 @@ class ClockSampler:
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "source": self.source}
 
 
 # ----------------------------------------------------------------------------- steps
@@ -484,7 +529,7 @@ def main():
     if not args.no_tune and not args.filter_params:
         from paper_2308_16370_b300 import autotune
         tr = autotune.tune(ctx, rels, w["edges"], w["preds"], w["root"], w["sum"], reps=3,
-                           use_cache=False)
+                           use_cache=False, flush=flush)
         TUNED.update(tr["params"])
         tune_info = {"params": tr["params"], "candidates": len(tr["timings"]),
                      "best_ms_untimed_loop": tr["ms"]}
@@ -587,7 +632,7 @@ def main():
                    "autotune": tune_info,
                    "default_params_ms_per_step": default_ms,
                    "sieved_intermediate_tuples": res["intermediate"]},
-        "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+        "clocks": {k: clocks.get(k) for k in ("sm_mhz", "sm_max_mhz", "reasons", "samples", "source")},
         "gpu_launches": counters["launches"],
         "cuda_graphs": graphs,
         "gpu_launches_per_step": counters["launches"] / args.steps,

@@ -474,10 +474,11 @@ SJ_API sj_status sj_prof_kinds(sj_ctx *ctx, uint32_t mask);
 SJ_API sj_status sj_prof_reset(sj_ctx *ctx);
 SJ_API sj_status sj_prof_read(sj_ctx *ctx, int kind, int64_t *launches, double *ms, double *bytes);
 SJ_API sj_status sj_counters(sj_ctx *ctx, int64_t *launches, int64_t *h2d_bytes, int64_t *d2h_bytes);
-/* CUDA-graph use of sj_sieve_join since the context was created: a query
- * shape (relations, their device buffers, edges, predicates, options) seen
- * for the third time replays a graph captured on the second call, whose
- * intermediate buffers are sized from the first.  `replays`, successful
+/* CUDA-graph use of sj_sieve_join since the context was created.  A query
+ * shape (relations, their device buffers, edges, predicates, options) runs
+ * exactly on its first call; later calls keep every size on the device, with
+ * intermediate buffers sized from the previous run; the third call captures a
+ * CUDA graph and the fourth and later calls replay it.  `replays`, successful
  * `captures` and failed `failures` (any may be null); `why` (optional, `len`
  * bytes, NUL-terminated) receives the reason of the last failed capture. */
 SJ_API sj_status sj_graph_stats(sj_ctx *ctx, int64_t *replays, int64_t *captures, int64_t *failures,

@@ -56,10 +56,12 @@ def _store(path, data):
 
 
 def tune(ctx, rels, edges, preds=None, root=-1, refs=(), candidates=None, reps=3,
-         use_cache=True, path=None):
+         use_cache=True, path=None, flush=None):
     """Return {"params": {...}, "ms": best, "timings": [...], "cached": bool}.
 
     ``params`` holds bits_per_key, k, layout and passes for ``sieve_join``.
+    ``flush``: a device tensor larger than L2, zeroed before every timed
+    repetition so that candidates are timed with inputs coming from HBM.
     """
     import torch
     path = path or cache_path()
@@ -78,11 +80,12 @@ def tune(ctx, rels, edges, preds=None, root=-1, refs=(), candidates=None, reps=3
         if layout == BLOCKED256 and k > 4:
             continue
         kw = dict(bits_per_key=bpk, k=k, layout=layout, passes=passes)
-        # warm-up: the first call of a shape is the exact path, the second
-        # sizes its buffers from the first and captures the CUDA graph that
-        # the timed repetitions replay
+        # warm-up: the first call of a shape is the exact path, the next ones
+        # size their buffers from the previous run; the third captures the
+        # CUDA graph that the timed repetitions replay
         res = ctx.sieve_join(rels, edges, preds, root, refs=refs, **kw)
-        ctx.sieve_join(rels, edges, preds, root, refs=refs, **kw)
+        for _ in range(2):
+            ctx.sieve_join(rels, edges, preds, root, refs=refs, **kw)
         got = (res["count"], res["sum"])
         if reference is None:
             reference = got
@@ -90,6 +93,8 @@ def tune(ctx, rels, edges, preds=None, root=-1, refs=(), candidates=None, reps=3
             raise RuntimeError(f"candidate {kw} changed the join result: {got} != {reference}")
         ts = []
         for _ in range(reps):
+            if flush is not None:
+                flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()

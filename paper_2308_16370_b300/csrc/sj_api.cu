@@ -90,6 +90,7 @@ struct sj_ctx {
   // per query shape: output tuples of each join level in the last exact run,
   // used to size the buffers of the device-sized (host-sync-free) join
   std::map<uint64_t, std::vector<uint64_t>> plan_caps;
+  std::map<uint64_t, int> plan_runs;  // device-sized runs per query shape (graph capture from the 2nd)
   // per-call arena (sj_sieve_join): temporaries are bump-allocated from one
   // device block and released together, instead of one allocator call each
   struct {
@@ -2374,9 +2375,16 @@ extern "C" sj_status sj_sieve_join(sj_ctx* c, const sj_path* path, const sj_siev
         sieved[i] = nullptr;
       }
       arena_end(c);
-      const bool capture = st == SJ_OK && (g == c->graphs.end() || !g->second.failed || g->second.gen != c->arena_gen);
+      // a shape is captured once it has run device-sized before: one-off
+      // shapes (common in serving) do not pay for a capture
+      const int runs = ++c->plan_runs[sig];
+      const bool capture = st == SJ_OK && runs >= 2 &&
+                           (g == c->graphs.end() || !g->second.failed || g->second.gen != c->arena_gen);
       if (st == SJ_OK) {
-        if (c->plan_caps.size() > 4096) c->plan_caps.clear();
+        if (c->plan_caps.size() > 4096) {
+          c->plan_caps.clear();
+          c->plan_runs.clear();
+        }
         c->plan_caps[sig] = T;
       }
       if (capture) {
@@ -2399,7 +2407,10 @@ extern "C" sj_status sj_sieve_join(sj_ctx* c, const sj_path* path, const sj_siev
     arena_end(c);
   }
   if (st == SJ_OK && mode == SJ_COUNT_SUM && path->nrel >= 2) {
-    if (c->plan_caps.size() > 4096) c->plan_caps.clear();
+    if (c->plan_caps.size() > 4096) {
+      c->plan_caps.clear();
+      c->plan_runs.clear();
+    }
     c->plan_caps[sig] = T;
   }
   return st;

@@ -360,8 +360,8 @@ def test_sieve_join_device_sized_repeat(ctx, kind, passes):
     rels = load(ctx, w)
     exp = oracle.agg_propagation(w)
     g0 = ctx.graph_stats()
-    # call 1 exact, call 2 device-sized (and captured as a graph), then replays
-    for _ in range(5):
+    # call 1 exact, 2 device-sized, 3 device-sized and captured, then replays
+    for _ in range(6):
         got = ctx.sieve_join(rels, w["edges"], w["preds"], w["root"], refs=w["sum"], passes=passes)
         assert (got["count"], got["sum"]) == (exp["count"], exp["sum"])
     g1 = ctx.graph_stats()
@@ -419,7 +419,7 @@ def test_profiled_graph_replays_report_kernel_times(ctx):
     rels = load(ctx, w)
     ctx.prof_enable(True)
     try:
-        for _ in range(3):  # exact, device-sized + capture, replay
+        for _ in range(4):  # exact, device-sized, device-sized + capture, replay
             ctx.sieve_join(rels, w["edges"], w["preds"], w["root"], refs=w["sum"], passes=sj.BWD_ONLY)
         ctx.prof_reset()
         g0 = ctx.graph_stats()["replays"]
