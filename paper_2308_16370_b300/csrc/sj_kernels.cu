@@ -162,13 +162,17 @@ __device__ __forceinline__ void bloom_insert_regN(const BloomBuildArgs& a, uint3
   }
 #pragma unroll
   for (int j = 0; j < kBuildKeys; ++j) cur[j] = __ldca(a.words + w[j]);
+  // the CTA cache is keyed by (word, mask): two keys with the same pair set
+  // the same bits, so skipping the second one's OR loses nothing, and the keys
+  // need not stay in registers
 #pragma unroll
   for (int j = 0; j < kBuildKeys; ++j)
-    if (((live >> j) & 1u) && (cur[j] & m[j]) != m[j] && !seen_before(seen, key_hash(key[j], a.seed)))
+    if (((live >> j) & 1u) && (cur[j] & m[j]) != m[j] &&
+        !seen_before(seen, ((uint64_t)w[j] << 32) | m[j]))
       atomicOr(a.words + w[j], m[j]);
 }
 
-__global__ void __launch_bounds__(kBlock, 3) k_bloom_build(BloomBuildArgs a) {
+__global__ void __launch_bounds__(kBlock, 4) k_bloom_build(BloomBuildArgs a) {
   __shared__ unsigned long long s_seen[kSeenSlots];
   for (int i = threadIdx.x; i < kSeenSlots; i += blockDim.x) s_seen[i] = 0ull;
   __syncthreads();
@@ -652,9 +656,12 @@ __global__ void __launch_bounds__(kSieveWarpBlock, K > 0 ? 6 : 4) k_sieve_warp(S
       }
     int32_t pay[8];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int64_t row = base + (int64_t)((i >> 2) * 32 + lane) * 4 + (i & 3);
-      pay[i] = (pf >= 0 && ((alive >> i) & 1u)) ? __ldcs(a.in[pf] + row) : 0;
+    for (int i = 0; i < 8; ++i) pay[i] = 0;
+    if (pf >= 0 && alive) {
+      const int32_t* pcol = a.in[pf] + base + lane * 4;  // this lane's first row
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        if ((alive >> i) & 1u) pay[i] = __ldcs(pcol + (i >> 2) * 128 + (i & 3));
     }
     // warp scan of the survivor counts of the two 4-row chunks (8 bits each)
     const uint32_t c = (uint32_t)__popc(alive & 0xfu) | ((uint32_t)__popc(alive >> 4) << 8);
