@@ -540,7 +540,7 @@ sj_status sieve_step_timed(sj_ctx* c, const sj_rel_s* in, const std::vector<Test
     }
     dfree(c, gap, gbytes);
   }
-  st = check_launch(c, "k_sieve_local/k_sieve_move");
+  st = check_launch(c, "k_sieve / k_sieve_warp + k_sieve_move");
   if (st != SJ_OK) {
     free_rel(c, r);
     return st;
