@@ -528,7 +528,7 @@ def main():
         default_ms = max_over_ranks(dms, ws) / 20
     if not args.no_tune and not args.filter_params:
         from paper_2308_16370_b300 import autotune
-        tr = autotune.tune(ctx, rels, w["edges"], w["preds"], w["root"], w["sum"], reps=3,
+        tr = autotune.tune(ctx, rels, w["edges"], w["preds"], w["root"], w["sum"], reps=9,
                            use_cache=False, flush=flush)
         TUNED.update(tr["params"])
         tune_info = {"params": tr["params"], "candidates": len(tr["timings"]),

@@ -483,6 +483,12 @@ SJ_API sj_status sj_counters(sj_ctx *ctx, int64_t *launches, int64_t *h2d_bytes,
  * bytes, NUL-terminated) receives the reason of the last failed capture. */
 SJ_API sj_status sj_graph_stats(sj_ctx *ctx, int64_t *replays, int64_t *captures, int64_t *failures,
                                 char *why, int len);
+/* Turn the capture of CUDA graphs by sj_sieve_join on (default) or off for
+ * this context; off also drops the graphs held.  A capture costs the calling
+ * thread about as much host time as the query it captures, which pays off
+ * for query shapes that repeat many times and not for a stream of mostly
+ * distinct shapes (the serving runtime's workers turn it off). */
+SJ_API sj_status sj_graphs_enable(sj_ctx *ctx, int on);
 /* Device idle time (ms) between the end of a profiled launch of each class and
  * the start of the next profiled launch (host work, syncs, memsets), summed
  * per class into gap_ms[SJ_K_COUNT]. */

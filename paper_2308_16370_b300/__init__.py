@@ -35,7 +35,7 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "out of device memory", 3: "hash ta
 EXPORTS = ["sj_create", "sj_destroy", "sj_sync", "sj_last_error", "sj_status_str", "sj_version",
            "sj_load_relation", "sj_rel_info", "sj_free_rel", "sj_build_filter", "sj_filter_info",
            "sj_filter_probe", "sj_free_filter", "sj_sieve", "sj_sieve_path", "sj_join",
-           "sj_prof_enable", "sj_prof_kinds", "sj_prof_reset", "sj_prof_read", "sj_counters", "sj_graph_stats", "sj_sieve_noalloc",
+           "sj_prof_enable", "sj_prof_kinds", "sj_prof_reset", "sj_prof_read", "sj_counters", "sj_graph_stats", "sj_graphs_enable", "sj_sieve_noalloc",
            "sj_server_create", "sj_server_add_relation", "sj_server_submit", "sj_server_poll",
            "sj_server_stats_get", "sj_server_destroy", "sj_triangles", "sj_sieve_join", "sj_prof_gaps",
            "sj_selftest_wait_timeout"]
@@ -162,6 +162,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "sj_prof_read": [P, I, ctypes.POINTER(I64), ctypes.POINTER(ctypes.c_double),
                          ctypes.POINTER(ctypes.c_double)],
         "sj_counters": [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64)],
+        "sj_graphs_enable": [P, I],
         "sj_graph_stats": [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.c_char_p, I],
         "sj_prof_gaps": [P, ctypes.POINTER(ctypes.c_double)],
         "sj_selftest_wait_timeout": [P],
@@ -528,6 +529,10 @@ class Context:
     def selftest_wait_timeout(self) -> int:
         """Make one bounded device wait run out; returns the status (4 = timeout)."""
         return int(self.lib.sj_selftest_wait_timeout(self.ctx))
+
+    def graphs_enable(self, on: bool = True):
+        """Capture (and replay) CUDA graphs of repeated sieve_join shapes."""
+        self._check(self.lib.sj_graphs_enable(self.ctx, 1 if on else 0))
 
     def graph_stats(self):
         """sj_sieve_join CUDA-graph replays, captures, failed captures and the

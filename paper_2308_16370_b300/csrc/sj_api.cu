@@ -85,6 +85,7 @@ struct sj_ctx {
   int64_t graph_replays = 0, graph_captures = 0, graph_failures = 0;
   std::string graph_why;
   bool capturing = false;  // no allocator calls while a graph is captured
+  bool graphs_on = true;   // capture repeated query shapes (sj_graphs_enable)
   cudaStream_t cap_stream = nullptr;  // captures run here (the user's stream may be the legacy one)
   uint64_t arena_gen = 0;
   // per query shape: output tuples of each join level in the last exact run,
@@ -2033,6 +2034,17 @@ sj_status sj_prof_gaps(sj_ctx* c, double* gap_ms) {
   return SJ_OK;
 }
 
+sj_status sj_graphs_enable(sj_ctx* c, int on) {
+  if (!c) return SJ_EINVAL;
+  c->graphs_on = on != 0;
+  if (!c->graphs_on) {
+    cudaStreamSynchronize(c->stream);
+    for (auto& kv : c->graphs) drop_graph(kv.second);
+    c->graphs.clear();
+  }
+  return SJ_OK;
+}
+
 sj_status sj_graph_stats(sj_ctx* c, int64_t* replays, int64_t* captures, int64_t* failures, char* why,
                          int len) {
   if (!c) return SJ_EINVAL;
@@ -2378,7 +2390,7 @@ extern "C" sj_status sj_sieve_join(sj_ctx* c, const sj_path* path, const sj_siev
       // a shape is captured once it has run device-sized before: one-off
       // shapes (common in serving) do not pay for a capture
       const int runs = ++c->plan_runs[sig];
-      const bool capture = st == SJ_OK && runs >= 2 &&
+      const bool capture = st == SJ_OK && runs >= 2 && c->graphs_on &&
                            (g == c->graphs.end() || !g->second.failed || g->second.gen != c->arena_gen);
       if (st == SJ_OK) {
         if (c->plan_caps.size() > 4096) {

@@ -243,6 +243,9 @@ sj_status sj_server_create(sj_server** out, const sj_server_opts* opts) {
       delete s;
       return SJ_ECUDA;
     }
+    // a serving stream is mostly distinct query shapes: a graph capture would
+    // add a query's worth of host time to one request and rarely be replayed
+    sj_graphs_enable(c, 0);
     s->streams.push_back(st);
     s->ctxs.push_back(c);
   }

@@ -432,3 +432,25 @@ def test_profiled_graph_replays_report_kernel_times(ctx):
         assert ag["launches"] > 0 and ag["ms"] > 0
     finally:
         ctx.prof_enable(False)
+
+
+def test_graphs_disabled_still_exact(ctx):
+    """With graph capture turned off, repeated calls stay on the device-sized
+    path, capture nothing and stay exact; turning it back on restores replay."""
+    w = inputs.uniform_chain(nrel=4, nrows=40_000, domain=10_000, seed=61)
+    rels = load(ctx, w)
+    exp = oracle.agg_propagation(w)
+    ctx.graphs_enable(False)
+    try:
+        g0 = ctx.graph_stats()
+        for _ in range(5):
+            got = ctx.sieve_join(rels, w["edges"], w["preds"], w["root"], refs=w["sum"])
+            assert (got["count"], got["sum"]) == (exp["count"], exp["sum"])
+        g1 = ctx.graph_stats()
+        assert (g1["replays"], g1["captures"]) == (g0["replays"], g0["captures"])
+    finally:
+        ctx.graphs_enable(True)
+    for _ in range(3):  # device-sized + capture, then replays
+        got = ctx.sieve_join(rels, w["edges"], w["preds"], w["root"], refs=w["sum"])
+        assert (got["count"], got["sum"]) == (exp["count"], exp["sum"])
+    assert ctx.graph_stats()["replays"] - g1["replays"] == 2
