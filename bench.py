@@ -70,6 +70,7 @@ def parse():
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--no-cyclic", action="store_true", help="skip the triangle-query run")
     ap.add_argument("--no-star", action="store_true", help="skip the star-join run")
+    ap.add_argument("--no-rst", action="store_true", help="skip the Sec. 3.1.1 R,S,T closed-form run")
     ap.add_argument("--filter-params", default=None,
                     help="bits_per_key,k,layout,passes: fixed parameters (no default-parameter "
                          "timing, no tuning), e.g. for profiling the tuned path")
@@ -372,6 +373,50 @@ def serving_run(args, torch, sj):
 
 
 # ----------------------------------------------------------------------------- star join
+def freitag_run(torch, sj, ctx, stream, r=1_000_000, d=4):
+    """The synthetic R, S, T benchmark of Sec. 3.1.1 at r = 1e6, d = 4: unary
+    relations of 40M, 22M and 22M rows whose natural join holds exactly r * d^3
+    tuples (closed form); COUNT only, sieved and plain."""
+    from paper_2308_16370_b300 import inputs
+    w = inputs.freitag_rst(r, d)
+    w["sum"] = []
+    dev = [[torch.from_numpy(c).cuda() for c in rr] for rr in w["rels"]]
+    rels = [ctx.load_relation(cols, where="borrow") for cols in dev]
+    tuples = sum(len(rr[0]) for rr in w["rels"])
+    exp = r * d ** 3
+
+    def timeit(fn, reps):
+        ts, res = [], None
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res = fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts)), res
+
+    for _ in range(3):  # exact, device-sized, device-sized + graph capture
+        ctx.sieve_join(rels, w["edges"], w["preds"], w["root"])
+    ms, res = timeit(lambda: ctx.sieve_join(rels, w["edges"], w["preds"], w["root"]), 5)
+    out = {"workload": f"Sec. 3.1.1 R,S,T: r={r}, d={d}, unary relations of "
+                       f"{len(w['rels'][0][0])}, {len(w['rels'][1][0])}, {len(w['rels'][2][0])} rows; COUNT",
+           "input_tuples": tuples, "closed_form_count": exp,
+           "sieved": {"ms": ms, "tuples_per_s": tuples / (ms / 1000.0), "count": res["count"],
+                      "matches_closed_form": res["count"] == exp}}
+    pms, pres = timeit(lambda: ctx.join(rels, w["edges"], w["preds"], w["root"]), 3)
+    out["plain"] = {"ms": pms, "tuples_per_s": tuples / (pms / 1000.0),
+                    "matches_closed_form": pres["count"] == exp,
+                    "intermediate_tuples": pres["intermediate"]}
+    for x in rels:
+        x.free()
+    del dev
+    torch.cuda.empty_cache()
+    return out
+
+
 def star_run(torch, sj, ctx, stream):
     """Star join: 100M fact rows (4 int32 FKs + int64 measure), 4 dimensions of
     1M rows with a 10% range predicate each; COUNT and SUM(measure), sieved
@@ -407,11 +452,15 @@ def star_run(torch, sj, ctx, stream):
             ts.append(e0.elapsed_time(e1))
         return float(np.median(ts)), r
 
-    ms, r = timeit(lambda: ctx.sieve_join(rels, w["edges"], w["preds"], w["root"], refs=w["sum"],
-                                          stats=True), 5)
+    # per-step statistics once (exact path), then the one-call path as a user
+    # repeating the query runs it (device-sized, then graph replays)
+    st = ctx.sieve_join(rels, w["edges"], w["preds"], w["root"], refs=w["sum"], stats=True)
+    for _ in range(2):
+        ctx.sieve_join(rels, w["edges"], w["preds"], w["root"], refs=w["sum"])
+    ms, r = timeit(lambda: ctx.sieve_join(rels, w["edges"], w["preds"], w["root"], refs=w["sum"]), 5)
     out["sieved"] = {"ms": ms, "tuples_per_s": tuples / (ms / 1000.0), "count": r["count"],
                      "sum": r["sum"], "matches_direct_lookup": (r["count"], r["sum"]) == exp,
-                     "sieve_steps": [list(x) for x in r["steps"]]}
+                     "sieve_steps": [list(x) for x in st["steps"]]}
     ms, r = timeit(lambda: ctx.join(rels, w["edges"], w["preds"], w["root"], refs=w["sum"]), 3)
     out["plain"] = {"ms": ms, "tuples_per_s": tuples / (ms / 1000.0),
                     "matches_direct_lookup": (r["count"], r["sum"]) == exp,
@@ -608,6 +657,10 @@ def main():
     if not args.no_star:
         star = star_run(torch, sj, ctx, stream)
 
+    rst = None
+    if not args.no_rst:
+        rst = freitag_run(torch, sj, ctx, stream)
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_oracle_run(spec)
@@ -639,6 +692,7 @@ def main():
         "e2e": e2e,
         "plain_gpu_hash_join": plain,
         "roofline": {"bound": "hbm", "kernel": "k_sieve", "achieved": achieved, "peak": peak,
+                     "frac_of_nominal_7700": achieved / 7700.0,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "launches": sv["launches"],
                      "avg_launch_ms": sv["ms"] / max(1, sv["launches"]),
@@ -651,6 +705,7 @@ def main():
         "serving": serving,
         "cyclic_triangles": cyclic,
         "star": star,
+        "rst_closed_form": rst,
         "device_idle_ms_per_step_after": {k: v / bsteps for k, v in gaps.items() if v},
         "cpu_baseline": cpu,
     }
