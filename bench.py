@@ -44,7 +44,10 @@ WORKLOADS = {
                         sample=lambda: __import__("paper_2308_16370_b300.inputs", fromlist=["x"]).zipf_chain(
                             nrows=2_000_000, domain=1_000_000),
                         sample_desc="same 4-way Zipf chain at 1/5 scale (2M rows per relation, 1M "
-                                    "domain, same key skew and 1% restriction)"),
+                                    "domain, same key skew and 1% restriction)",
+                        # reference arm with many steps: a smaller sample of the same shape
+                        sample_scaled=lambda n: __import__("paper_2308_16370_b300.inputs", fromlist=["x"]).zipf_chain(
+                            nrows=n, domain=max(1, n // 2))),
     "chain3_uniform": dict(desc="3-way chain R(a,b) S(b,c) T(c,d), 100k rows each, keys uniform "
                                 "in [0,50000); COUNT(*) and SUM(a+d)",
                            gen=lambda: __import__("paper_2308_16370_b300.inputs", fromlist=["x"]).uniform_chain(),
@@ -519,6 +522,9 @@ def cpu_oracle_run(spec, reps_seconds=10.0, max_reps=20):
                       f"({tuples} input tuples each), single thread, {t_tot:.1f} s total"}
 
 
+REF_BUDGET_S = 90.0
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return
@@ -526,6 +532,27 @@ def run_reference(args, ws, rank):
     import oracle
     oracle.build_lib()
     w = spec["sample"]()
+    sample_desc = spec["sample_desc"]
+    # keep the whole run within about REF_BUDGET_S: with many steps, each step
+    # joins a proportionally smaller sample of the same shape
+    t0 = time.perf_counter()
+    oracle.hash_join(w)
+    per = time.perf_counter() - t0
+    runs = max(1, args.steps + args.warmup)
+    if per * runs > REF_BUDGET_S and "sample_scaled" in spec:
+        n0 = len(w["rels"][0][0])
+        n = max(20_000, int(n0 * REF_BUDGET_S / (per * runs)))
+        w = spec["sample_scaled"](n)
+        # small samples run faster per tuple (cache-resident): re-fit once
+        t0 = time.perf_counter()
+        oracle.hash_join(w)
+        per = time.perf_counter() - t0
+        if per * runs < 0.5 * REF_BUDGET_S:
+            n = min(n0, int(n * 0.5 * REF_BUDGET_S / (per * runs)))
+            w = spec["sample_scaled"](n)
+        sample_desc = (f"same 4-way Zipf chain at {n} rows per relation ({n // 2} domain, same key "
+                       f"skew and 1% restriction), sized so that {runs} runs fit about "
+                       f"{REF_BUDGET_S:.0f} s")
     tuples = sum(len(r[0]) for r in w["rels"])
     for _ in range(args.warmup):
         oracle.hash_join(w)
@@ -538,9 +565,9 @@ def run_reference(args, ws, rank):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic",
-            "config": {"workload": args.workload, "desc": spec["desc"], "sample": spec["sample_desc"]},
+            "config": {"workload": args.workload, "desc": spec["desc"], "sample": sample_desc},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": spec["sample_desc"]},
+                             "sample": sample_desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
