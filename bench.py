@@ -115,6 +115,49 @@ def max_over_ranks(x: float, ws: int) -> float:
 
 
 # ----------------------------------------------------------------------------- clocks
+class _CtypesNvml:
+    """The few read-only NVML queries the clock sampler needs, bound with
+    ctypes to the driver's libnvidia-ml when the pynvml module is absent."""
+    NVML_CLOCK_SM = 1
+
+    def __init__(self):
+        import ctypes
+        self.ct = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+
+    def _ok(self, r):
+        if r != 0:
+            raise RuntimeError(f"NVML error {r}")
+
+    def nvmlInit(self):
+        self._ok(self.lib.nvmlInit_v2())
+
+    def nvmlDeviceGetHandleByUUID(self, uuid):
+        h = self.ct.c_void_p()
+        self._ok(self.lib.nvmlDeviceGetHandleByUUID(self.ct.c_char_p(uuid), self.ct.byref(h)))
+        return h
+
+    def nvmlDeviceGetHandleByIndex(self, i):
+        h = self.ct.c_void_p()
+        self._ok(self.lib.nvmlDeviceGetHandleByIndex_v2(self.ct.c_uint(i), self.ct.byref(h)))
+        return h
+
+    def nvmlDeviceGetClockInfo(self, h, kind):
+        v = self.ct.c_uint()
+        self._ok(self.lib.nvmlDeviceGetClockInfo(h, self.ct.c_int(kind), self.ct.byref(v)))
+        return v.value
+
+    def nvmlDeviceGetMaxClockInfo(self, h, kind):
+        v = self.ct.c_uint()
+        self._ok(self.lib.nvmlDeviceGetMaxClockInfo(h, self.ct.c_int(kind), self.ct.byref(v)))
+        return v.value
+
+    def nvmlDeviceGetCurrentClocksThrottleReasons(self, h):
+        v = self.ct.c_ulonglong()
+        self._ok(self.lib.nvmlDeviceGetCurrentClocksThrottleReasons(h, self.ct.byref(v)))
+        return v.value
+
+
 class ClockSampler:
     """SM clock and throttle reasons sampled during the timed region: NVML
     queries every few milliseconds from a thread (read-only), or nvidia-smi's
@@ -136,7 +179,10 @@ class ClockSampler:
         self.source = None
 
     def _nvml_handle(self):
-        import pynvml
+        try:
+            import pynvml
+        except ImportError:
+            pynvml = _CtypesNvml()  # the driver's libnvidia-ml through ctypes
         pynvml.nvmlInit()
         try:
             import torch
@@ -167,8 +213,9 @@ class ClockSampler:
             self.th.start()
             self.source = "nvml"
             return self
-        except Exception:
+        except Exception as e:  # fall back to nvidia-smi's query loop
             self.nvml = None
+            self.nvml_error = repr(e)[:120]
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
@@ -200,6 +247,17 @@ class ClockSampler:
             except Exception:
                 self.proc.kill()
             self.th.join(timeout=2)
+            if len(self.lines) <= self.skip:
+                # a timed region shorter than the query interval: one sample
+                # taken the moment it ends
+                try:
+                    out = subprocess.run(["nvidia-smi", "-i", str(self.device),
+                                          f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits"],
+                                         capture_output=True, text=True, timeout=10).stdout
+                    self.lines += [ln.strip() for ln in out.splitlines() if ln.strip()]
+                    self.source = "nvidia-smi (one sample at the end of the timed region)"
+                except Exception:
+                    pass
 
     def summary(self):
         sm, mx, reasons = [], None, set()
@@ -218,8 +276,11 @@ class ClockSampler:
                     reasons.add(nm)
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm), "source": self.source}
+        out = {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+               "samples": len(sm), "source": self.source}
+        if getattr(self, "nvml_error", None):
+            out["nvml_error"] = self.nvml_error
+        return out
 
 
 # ----------------------------------------------------------------------------- steps
@@ -712,7 +773,8 @@ def main():
                    "autotune": tune_info,
                    "default_params_ms_per_step": default_ms,
                    "sieved_intermediate_tuples": res["intermediate"]},
-        "clocks": {k: clocks.get(k) for k in ("sm_mhz", "sm_max_mhz", "reasons", "samples", "source")},
+        "clocks": {k: clocks.get(k) for k in ("sm_mhz", "sm_max_mhz", "reasons", "samples", "source",
+                                              "nvml_error") if k in clocks},
         "gpu_launches": counters["launches"],
         "cuda_graphs": graphs,
         "gpu_launches_per_step": counters["launches"] / args.steps,
