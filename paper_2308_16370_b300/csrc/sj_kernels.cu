@@ -898,6 +898,19 @@ __device__ __forceinline__ int64_t table_find(const Table& t, int32_t key) {
   return -1;
 }
 
+// Slot of `key` when it sits in one of the first two slots of its home
+// bucket (the common case at load <= 1/2), -1 when that half-bucket shows it
+// absent, else the full probe.
+__device__ __forceinline__ int64_t table_find_first(const Table& t, int32_t key, uint32_t b,
+                                                    ulonglong2 q) {
+  const uint64_t lo = (uint32_t)key;
+  if (q.x == 0) return -1;
+  if ((q.x & 0xffffffffull) == lo) return (int64_t)b * 4;
+  if (q.y == 0) return -1;
+  if ((q.y & 0xffffffffull) == lo) return (int64_t)b * 4 + 1;
+  return table_find(t, key);
+}
+
 // Per-CTA aggregation of skewed keys: a CTA takes kAggRows rows per round and
 // combines the rows of each key (dense id or table slot) in a shared-memory
 // table before touching global memory, so a key repeated r times in a round
@@ -993,37 +1006,45 @@ __global__ void __launch_bounds__(kBlock) k_mm_probe(MMProbeArgs a) {
     break;
   }
   const int64_t base = (int64_t)tile * kProbeTile;
-  int32_t id[8];
-  uint32_t m[8];
+  // the 8 keys of a thread, then their 8 home half-buckets read together,
+  // then the row counts of the hits together: three round trips per tile
+  int32_t kk[8];
+  uint32_t okm = 0;
 #pragma unroll
   for (int v = 0; v < 2; ++v) {
     const int64_t r0 = base + (int64_t)(v * kBlock + tid) * 4;
-    int32_t k4[4];
-    bool ok4[4];
     if (r0 + 4 <= n) {
       const int4 x = __ldcs(reinterpret_cast<const int4*>(a.keys + r0));
-      k4[0] = x.x; k4[1] = x.y; k4[2] = x.z; k4[3] = x.w;
-      ok4[0] = ok4[1] = ok4[2] = ok4[3] = true;
+      kk[4 * v] = x.x; kk[4 * v + 1] = x.y; kk[4 * v + 2] = x.z; kk[4 * v + 3] = x.w;
+      okm |= 0xfu << (4 * v);
     } else {
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        ok4[e] = r0 + e < n;
-        k4[e] = ok4[e] ? __ldcs(a.keys + r0 + e) : 0;
-      }
-    }
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      id[4 * v + e] = -1;
-      m[4 * v + e] = 0;
-      if (ok4[e]) {
-        const int64_t s = table_find(a.t, k4[e]);
-        if (s >= 0) {
-          id[4 * v + e] = (int32_t)s;
-          m[4 * v + e] = __ldg(a.cnt + s);
+        kk[4 * v + e] = 0;
+        if (r0 + e < n) {
+          kk[4 * v + e] = __ldcs(a.keys + r0 + e);
+          okm |= 1u << (4 * v + e);
         }
       }
     }
   }
+  uint32_t bk[8];
+  ulonglong2 q[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    bk[j] = table_bucket(kk[j], a.t.bucket_mask);
+    q[j] = ((okm >> j) & 1u) ? __ldg(reinterpret_cast<const ulonglong2*>(a.t.slots + (uint64_t)bk[j] * 4))
+                             : make_ulonglong2(0ull, 0ull);
+  }
+  int32_t id[8];
+  uint32_t m[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int64_t s = ((okm >> j) & 1u) ? table_find_first(a.t, kk[j], bk[j], q[j]) : -1;
+    id[j] = (int32_t)s;
+  }
+#pragma unroll
+  for (int j = 0; j < 8; ++j) m[j] = id[j] >= 0 ? __ldg(a.cnt + id[j]) : 0u;
   // scan channels: [0] hit counts of chunks 0 and 1 packed (32 bits each),
   // [1] output tuples of chunk 0, [2] output tuples of chunk 1
   Vec<3> c;
@@ -1225,18 +1246,6 @@ __device__ __forceinline__ void add128(U128& x, uint64_t lo, uint64_t hi) {
 // One probe row per thread and iteration: the table is small and cache
 // resident here, so occupancy (32 registers, 8 CTAs per SM) hides latency
 // better than batching rows per thread.
-// Slot of `key` when it sits in one of the first two slots of its home
-// bucket (the common case at load <= 1/2), -1 when that half-bucket shows it
-// absent, else the full probe.
-__device__ __forceinline__ int64_t table_find_first(const Table& t, int32_t key, uint32_t b,
-                                                    ulonglong2 q) {
-  const uint64_t lo = (uint32_t)key;
-  if (q.x == 0) return -1;
-  if ((q.x & 0xffffffffull) == lo) return (int64_t)b * 4;
-  if (q.y == 0) return -1;
-  if ((q.y & 0xffffffffull) == lo) return (int64_t)b * 4 + 1;
-  return table_find(t, key);
-}
 
 // Probe of the final level's (count, sum) table.  The common shape -- a long
 // probe relation whose SUM term is at most one int32 column -- takes 4 rows per
