@@ -428,6 +428,17 @@ SJ_API sj_status sj_server_destroy(sj_server *srv);
  * relations, which are freed before returning (Sec. 2.2: pruning phase, then
  * enumeration phase).  `opts` and `stats` as for sj_sieve_path, the rest as
  * for sj_join.  Errors: those of the two calls.
+ *
+ * Repeated COUNT_SUM queries of one shape (same relation handles and device
+ * buffers, edges, predicates, options and SUM columns; `stats` NULL) run
+ * faster: the first call is exact and synchronises per join level; later
+ * calls keep every size on the device, with intermediate buffers of twice the
+ * previous run's size, and synchronise once (an intermediate that outgrows its
+ * buffer is detected and the call reruns exactly, so the result never
+ * depends on this); from the third call the query is captured once as a CUDA
+ * graph and replayed (see sj_graph_stats, sj_graphs_enable).  The contents of
+ * the relations may change between calls.  Temporaries come from a
+ * per-context arena that grows to the largest call.
  */
 SJ_API sj_status sj_sieve_join(sj_ctx *ctx, const sj_path *path, const sj_sieve_opts *opts,
                                int mode, int nrefs, const sj_colref *refs, sj_result *result,
