@@ -192,11 +192,13 @@ SJ_API sj_status sj_sieve(sj_ctx *ctx, sj_rel rel, int nprobe, const int *key_co
  * and its params (k, layout and seed; bits_per_key is not used).  All
  * pointers are device pointers, 16-byte aligned.  `status` is NULL or a
  * device uint32 that receives SJ_ETIMEOUT-style bits (1 = a bounded wait gave
- * up) and is not cleared by the call.  The work is enqueued on cuda_stream
- * (NULL = legacy default stream) of the current device; nothing is
- * synchronised.
+ * up) and is not cleared by the call.  With status NULL the bits go to a word
+ * inside the library that no caller can read, so a wait that gave up cannot
+ * be reported: pass a status word to learn that out_cols and *out_count are
+ * not valid.  The work is enqueued on cuda_stream (NULL = legacy default
+ * stream) of the current device; nothing is synchronised.
  *
- * Its scratch is one fixed device array of about 256 KiB inside this library
+ * Its scratch is one fixed device array of about 64 KiB inside this library
  * (held by every GPU that loads the library until the process exits), sized
  * for SJ_NOALLOC_MAX_ROWS rows; larger relations are rejected with SJ_EINVAL.
  * Every call shares that array and clears what must start at zero, so calls

@@ -29,8 +29,6 @@ constexpr int kMiscTotals = 4;   // [4..5] matching probe rows, output tuples
 constexpr int kMiscSteps = 8;    // [8 .. 8 + kMaxSlots) per-step row counts
 constexpr int kMaxSlots = 120;
 constexpr int kMiscWords = kMiscSteps + kMaxSlots;
-// sieve steps over at most this many tiles use the one-pass look-back kernel
-constexpr int64_t kLookBackMaxTiles = 64;
 // internal status: a device-sized join outgrew a buffer and must be rerun
 constexpr sj_status kRetry = 100;
 // d_misc words of the device-sized join: per-level totals and output counts
@@ -458,8 +456,11 @@ FilterView view(const sj_filter_s* f) {
 // One sieve step without synchronising: kept rows of `in` into a new relation.
 // `slot` >= 0 also stores the kept-row count in the per-step statistics;
 // `slot_in` is the statistics slot of `in`'s own count (deferred profiling bytes).
+// `zero` lists filters (allocated, words not cleared) that the builds following
+// this step write from its output: the step clears exactly the words they use.
 sj_status sieve_step_timed(sj_ctx* c, const sj_rel_s* in, const std::vector<TestSpec>& tests,
-                           int slot, int slot_in, sj_rel* out) {
+                           int slot, int slot_in, sj_rel* out,
+                           const std::vector<sj_filter>* zero = nullptr) {
   const int64_t cap = rel_cap(in);
   sj_rel r = new_rel(c, in->ncols, cap);
   if (!r) return fail(c, SJ_ENOMEM, "sieve output allocation failed");
@@ -481,67 +482,37 @@ sj_status sieve_step_timed(sj_ctx* c, const sj_rel_s* in, const std::vector<Test
   }
   a.n_host = in->d_n ? 0 : in->nrows;
   a.n_dev = in->d_n;
-  const int64_t ntiles = (cap + kSieveTile - 1) / kSieveTile;
+  a.out_n = r->d_n;
+  a.out_n2 = slot >= 0 ? c->d_misc + kMiscSteps + slot : nullptr;
+  a.fast_words_ok = 1;
+  if (!tests.empty() && !tests[0].is_pred && tests[0].f->nblocks_cap * 8 >= (1ull << 32)) a.fast_words_ok = 0;
+  if (zero) {
+    for (sj_filter f : *zero) {
+      if (a.nzero == kMaxZero) break;
+      a.zero_words[a.nzero] = f->words;
+      a.zero_bpk[a.nzero] = f->p.bits_per_key;
+      a.zero_cap_words[a.nzero] = f->nblocks_cap * 8;
+      a.nzero++;
+    }
+  }
+  a.chunk_rows = sieve_chunk_rows(cap, c->num_sms);
+  const int64_t nchunks = (cap + a.chunk_rows - 1) / a.chunk_rows;
+  sj_status st = scratch_for<1>(c, nchunks, &a.tile_counter, &a.lb);
+  if (st != SJ_OK) {
+    free_rel(c, r);
+    return st;
+  }
   // algorithmic bytes: the first tested column of every input row; each kept
   // row's other columns read and all of its columns written
   const int nvec = tests.empty() ? 0 : 1;
   const double per_in = 4.0 * nvec;
   const double per_out = 4.0 * (in->ncols - nvec) + 4.0 * in->ncols;
-  sj_status st = SJ_OK;
-  if (ntiles <= kLookBackMaxTiles) {
-    // few tiles: one pass with a decoupled look-back (short chains, one launch)
-    for (int j = 0; j < in->ncols; ++j) a.out[j] = r->cols[j];
-    a.out_n = r->d_n;
-    a.out_n2 = slot >= 0 ? c->d_misc + kMiscSteps + slot : nullptr;
-    st = scratch_for<1>(c, ntiles, &a.tile_counter, &a.lb);
-    if (st != SJ_OK) {
-      free_rel(c, r);
-      return st;
-    }
+  {
     Launch L = in->d_n ? Launch(c, SJ_K_SIEVE, 0, slot_in, per_in, slot, per_out)
                        : Launch(c, SJ_K_SIEVE, per_in * (double)in->nrows, slot, per_out);
-    launch_sieve(a, cap, c->stream);
-  } else {
-    // many tiles: two passes -- each tile compacts into its slot of a gapped
-    // buffer, then the move kernel packs the slots in order; no tile waits
-    // for another, which matters when hundreds of tiles are in flight
-    const int64_t nwt = (cap + kWarpRows - 1) / kWarpRows;
-    const int64_t nbt = (cap + kSieveBlockRows - 1) / kSieveBlockRows;
-    const size_t gcol = round_up((size_t)std::max<int64_t>(cap, 1) * 4);
-    const size_t tbytes = round_up((size_t)std::max<int64_t>(nwt, 1) * 4);
-    const size_t gbytes = gcol * (size_t)in->ncols + tbytes + round_up((size_t)std::max<int64_t>(nbt, 1) * 4);
-    uint8_t* gap = static_cast<uint8_t*>(dalloc(c, gbytes));
-    if (!gap) {
-      free_rel(c, r);
-      return fail(c, SJ_ENOMEM, "sieve staging allocation failed");
-    }
-    SieveMoveArgs m;
-    memset(&m, 0, sizeof(m));
-    for (int j = 0; j < in->ncols; ++j) {
-      a.out[j] = reinterpret_cast<int32_t*>(gap + gcol * j);
-      m.gap[j] = a.out[j];
-      m.out[j] = r->cols[j];
-    }
-    a.tile_cnt = reinterpret_cast<uint32_t*>(gap + gcol * in->ncols);
-    a.block_cnt = reinterpret_cast<uint32_t*>(gap + gcol * in->ncols + tbytes);
-    a.fast_words_ok = 1;
-    if (!tests.empty() && !tests[0].is_pred && tests[0].f->nblocks_cap * 8 >= (1ull << 32)) a.fast_words_ok = 0;
-    m.nout = in->ncols;
-    m.tile_cnt = a.tile_cnt;
-    m.block_cnt = a.block_cnt;
-    m.n_host = a.n_host;
-    m.n_dev = a.n_dev;
-    m.out_n = r->d_n;
-    m.out_n2 = slot >= 0 ? c->d_misc + kMiscSteps + slot : nullptr;
-    {
-      Launch L = in->d_n ? Launch(c, SJ_K_SIEVE, 0, slot_in, per_in, slot, per_out)
-                         : Launch(c, SJ_K_SIEVE, per_in * (double)in->nrows, slot, per_out);
-      c->launches++;  // two kernels
-      launch_sieve_two_pass(a, m, cap, c->num_sms, c->stream);
-    }
-    dfree(c, gap, gbytes);
+    launch_sieve_chunk(a, cap, c->num_sms, c->stream);
   }
-  st = check_launch(c, "k_sieve / k_sieve_warp + k_sieve_move");
+  st = check_launch(c, "k_sieve_chunk");
   if (st != SJ_OK) {
     free_rel(c, r);
     return st;
@@ -568,9 +539,9 @@ sj_status check_params(sj_ctx* c, const sj_filter_params& p) {
   return SJ_OK;
 }
 
-// Build a filter over column `col` of `rel` without synchronising.
-sj_status build_filter_nosync(sj_ctx* c, const sj_rel_s* rel, int col, const sj_filter_params& p,
-                              int slot_in, sj_filter* out) {
+// Allocate a filter for a build over `rel` (capacity from its row bound); its
+// words are not cleared.
+sj_status alloc_filter(sj_ctx* c, const sj_rel_s* rel, const sj_filter_params& p, sj_filter* out) {
   const int64_t cap = rel_cap(rel);
   sj_filter f = new sj_filter_s();
   f->p = p;
@@ -585,11 +556,19 @@ sj_status build_filter_nosync(sj_ctx* c, const sj_rel_s* rel, int col, const sj_
   }
   f->hdr = static_cast<uint64_t*>(f->mem);
   f->words = reinterpret_cast<uint32_t*>(static_cast<uint8_t*>(f->mem) + kAlign);
-  cudaError_t e = cudaMemsetAsync(f->words, 0, nbc * 32, c->stream);
-  if (e != cudaSuccess) {
-    dfree(c, f->mem, f->mem_bytes);
-    delete f;
-    return fail(c, SJ_ECUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
+  *out = f;
+  return SJ_OK;
+}
+
+// Build filter `f` over column `col` of `rel` without synchronising.  Unless
+// `cleared` (the sieve step that produced `rel` cleared the words), the words
+// the filter can use are cleared first.
+sj_status launch_build(sj_ctx* c, sj_filter f, const sj_rel_s* rel, int col, int slot_in,
+                       bool cleared) {
+  const sj_filter_params& p = f->p;
+  if (!cleared) {
+    cudaError_t e = cudaMemsetAsync(f->words, 0, f->nblocks_cap * 32, c->stream);
+    if (e != cudaSuccess) return fail(c, SJ_ECUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
   }
   BloomBuildArgs a;
   a.keys = rel->cols[col];
@@ -597,7 +576,7 @@ sj_status build_filter_nosync(sj_ctx* c, const sj_rel_s* rel, int col, const sj_
   a.n_dev = rel->d_n;
   a.hdr = f->hdr;
   a.words = f->words;
-  a.nblocks_cap = nbc;
+  a.nblocks_cap = f->nblocks_cap;
   a.bits_per_key = p.bits_per_key;
   a.k = p.k;
   a.layout = p.layout;
@@ -607,9 +586,17 @@ sj_status build_filter_nosync(sj_ctx* c, const sj_rel_s* rel, int col, const sj_
   {
     Launch L = rel->d_n ? Launch(c, SJ_K_BLOOM_BUILD, 0, slot_in, per_key)
                         : Launch(c, SJ_K_BLOOM_BUILD, per_key * (double)rel->nrows);
-    launch_bloom_build(a, cap, c->num_sms, c->stream);
+    launch_bloom_build(a, rel_cap(rel), c->num_sms, c->stream);
   }
-  sj_status st = check_launch(c, "k_bloom_build");
+  return check_launch(c, "k_bloom_build");
+}
+
+// Build a filter over column `col` of `rel` without synchronising.
+sj_status build_filter_nosync(sj_ctx* c, const sj_rel_s* rel, int col, const sj_filter_params& p,
+                              int slot_in, sj_filter* out) {
+  sj_filter f = nullptr;
+  SJ_TRY(alloc_filter(c, rel, p, &f));
+  const sj_status st = launch_build(c, f, rel, col, slot_in, false);
   if (st != SJ_OK) {
     dfree(c, f->mem, f->mem_bytes);
     delete f;
@@ -981,11 +968,62 @@ sj_status sieve_path_impl(sj_ctx* c, const sj_path* path, const sj_sieve_opts* o
   const size_t p0 = c->prof.size();
   std::vector<sj_rel> cur(n, nullptr);   // owned temporaries (null = the input itself)
   std::vector<int> last_slot(n, -1);     // step slot holding the relation's current count
-  std::vector<sj_filter> filters;
+  std::vector<sj_filter> filters;        // filters this call built (freed at the end)
   struct StepRec { int kind, rel, slot_in, slot_out; int64_t rows_in_host; };
   std::vector<StepRec> steps;
   int slot = 0;
   uint64_t filter_bytes = 0;
+
+  // The schedule is planned first, then run: a sieve step knows which filters
+  // are built from its output next (before that relation is sieved again) and
+  // clears their words itself.  Filter ids index `fl`.
+  enum { kOpStep, kOpBuild, kOpFinal };
+  struct Op {
+    int type, rel, kind;                    // kind: step kind for statistics
+    std::vector<std::pair<int, int>> probes;  // (column, filter id)
+    bool pred;
+    int col, fid;                           // build: column and filter id
+  };
+  std::vector<Op> ops;
+  std::vector<sj_filter> fl;
+  std::vector<char> fl_given;               // handed-in leaf filter (not built here)
+  auto new_fid = [&]() { fl.push_back(nullptr); fl_given.push_back(0); return (int)fl.size() - 1; };
+  for (int i = 0; i < n; ++i)
+    if (has_pred(path, i)) ops.push_back({kOpStep, i, 0, {}, true, -1, -1});
+  if (o.passes == SJ_NO_SIEVE || n == 1)
+    for (int i = 0; i < n; ++i) ops.push_back({kOpFinal, i, 0, {}, false, -1, -1});
+  if (o.passes != SJ_NO_SIEVE && n > 1) {
+    std::vector<int> up(n, -1), down(n, -1);
+    if (o.passes == SJ_FWD_BWD) {
+      for (int v : tr.post) {
+        if (!tr.children[v].empty()) {
+          if ((int)tr.children[v].size() > SJ_MAX_PROBES)
+            return fail(c, SJ_EINVAL, "a relation has more than 4 children");
+          Op op{kOpStep, v, 1, {}, false, -1, -1};
+          for (int ch : tr.children[v]) op.probes.push_back({edge_col(path->edges[tr.pedge[ch]], v), up[ch]});
+          ops.push_back(op);
+        }
+        if (tr.parent[v] >= 0) {
+          up[v] = new_fid();
+          if (tr.children[v].empty() && o.leaf_filters && o.leaf_filters[v]) {
+            fl[up[v]] = o.leaf_filters[v];  // reused (Sec. 2.3); owned by the caller
+            fl_given[up[v]] = 1;
+          } else {
+            ops.push_back({kOpBuild, v, 0, {}, false, edge_col(path->edges[tr.pedge[v]], v), up[v]});
+          }
+        }
+      }
+    }
+    for (int v : tr.pre) {
+      if (tr.parent[v] >= 0)
+        ops.push_back({kOpStep, v, 2, {{edge_col(path->edges[tr.pedge[v]], v), down[v]}}, false, -1, -1});
+      ops.push_back({kOpFinal, v, 0, {}, false, -1, -1});  // v is not sieved again
+      for (int ch : tr.children[v]) {
+        down[ch] = new_fid();
+        ops.push_back({kOpBuild, v, 0, {}, false, edge_col(path->edges[tr.pedge[ch]], v), down[ch]});
+      }
+    }
+  }
 
   auto cleanup = [&]() {
     for (auto f : filters) free_filter(c, f);
@@ -996,65 +1034,55 @@ sj_status sieve_path_impl(sj_ctx* c, const sj_path* path, const sj_sieve_opts* o
     }
   };
   auto rel_of = [&](int i) -> const sj_rel_s* { return cur[i] ? cur[i] : path->rels[i]; };
-  auto do_step = [&](int i, int kind, const std::vector<TestSpec>& t) -> sj_status {
-    if (slot >= kMaxSlots || (int)steps.size() >= SJ_MAX_STEPS)
-      return fail(c, SJ_EINVAL, "too many sieve steps");
-    sj_rel r = nullptr;
-    const sj_rel_s* in = rel_of(i);
-    SJ_TRY(sieve_step_timed(c, in, t, slot, last_slot[i], &r));
-    steps.push_back({kind, i, last_slot[i], slot, in->d_n ? -1 : in->nrows});
-    free_rel(c, cur[i]);
-    cur[i] = r;
-    last_slot[i] = slot++;
-    return SJ_OK;
-  };
-  auto do_build = [&](int i, int col, sj_filter* f) -> sj_status {
-    SJ_TRY(build_filter_nosync(c, rel_of(i), col, fp, last_slot[i], f));
-    filters.push_back(*f);
-    filter_bytes += (*f)->nblocks_cap * 32;
-    return SJ_OK;
-  };
-
-  auto final_of = [&](int i) -> sj_status { return on_final ? (*on_final)(i, rel_of(i)) : SJ_OK; };
+  std::vector<char> cleared(fl.size(), 0);
   sj_status st = SJ_OK;
-  for (int i = 0; i < n && st == SJ_OK; ++i)
-    if (has_pred(path, i))
-      st = do_step(i, 0, {{path->preds[i].col, true, path->preds[i].lo, path->preds[i].hi, nullptr}});
-  if (o.passes == SJ_NO_SIEVE || n == 1)
-    for (int i = 0; i < n && st == SJ_OK; ++i) st = final_of(i);
-  if (st == SJ_OK && o.passes != SJ_NO_SIEVE && n > 1) {
-    std::vector<sj_filter> up(n, nullptr), down(n, nullptr);
-    if (o.passes == SJ_FWD_BWD) {
-      for (int v : tr.post) {
+  for (size_t q = 0; q < ops.size() && st == SJ_OK; ++q) {
+    const Op& op = ops[q];
+    const int i = op.rel;
+    if (op.type == kOpFinal) {
+      if (on_final) st = (*on_final)(i, rel_of(i));
+    } else if (op.type == kOpBuild) {
+      sj_filter f = fl[op.fid];
+      if (!f) {
+        st = alloc_filter(c, rel_of(i), fp, &f);
         if (st != SJ_OK) break;
-        if (!tr.children[v].empty()) {
-          std::vector<TestSpec> t;
-          for (int ch : tr.children[v])
-            t.push_back({edge_col(path->edges[tr.pedge[ch]], v), false, 0, 0, up[ch]});
-          if ((int)t.size() > SJ_MAX_PROBES) {
-            st = fail(c, SJ_EINVAL, "a relation has more than 4 children");
-            break;
-          }
-          st = do_step(v, 1, t);
-        }
-        if (st == SJ_OK && tr.parent[v] >= 0) {
-          if (tr.children[v].empty() && o.leaf_filters && o.leaf_filters[v]) {
-            up[v] = o.leaf_filters[v];  // reused (Sec. 2.3); owned by the caller
-          } else {
-            st = do_build(v, edge_col(path->edges[tr.pedge[v]], v), &up[v]);
-          }
-        }
+        fl[op.fid] = f;
+        filters.push_back(f);
+        filter_bytes += f->nblocks_cap * 32;
       }
-    }
-    for (int v : tr.pre) {
+      st = launch_build(c, f, rel_of(i), op.col, last_slot[i], cleared[op.fid] != 0);
+    } else {
+      if (slot >= kMaxSlots || (int)steps.size() >= SJ_MAX_STEPS) {
+        st = fail(c, SJ_EINVAL, "too many sieve steps");
+        break;
+      }
+      std::vector<TestSpec> t;
+      if (op.pred) t.push_back({path->preds[i].col, true, path->preds[i].lo, path->preds[i].hi, nullptr});
+      for (auto& pr : op.probes) t.push_back({pr.first, false, 0, 0, fl[pr.second]});
+      // the filters built from this step's output before relation i is sieved again
+      std::vector<sj_filter> zero;
+      for (size_t u = q + 1; u < ops.size() && st == SJ_OK; ++u) {
+        if (ops[u].rel != i) continue;
+        if (ops[u].type == kOpStep) break;
+        if (ops[u].type != kOpBuild || (int)zero.size() == kMaxZero) continue;
+        sj_filter f = nullptr;
+        st = alloc_filter(c, cur[i] ? cur[i] : path->rels[i], fp, &f);
+        if (st != SJ_OK) break;
+        fl[ops[u].fid] = f;
+        cleared[ops[u].fid] = 1;
+        filters.push_back(f);
+        filter_bytes += f->nblocks_cap * 32;
+        zero.push_back(f);
+      }
       if (st != SJ_OK) break;
-      if (tr.parent[v] >= 0)
-        st = do_step(v, 2, {{edge_col(path->edges[tr.pedge[v]], v), false, 0, 0, down[v]}});
-      if (st == SJ_OK) st = final_of(v);  // v is not sieved again
-      for (int ch : tr.children[v]) {
-        if (st != SJ_OK) break;
-        st = do_build(v, edge_col(path->edges[tr.pedge[ch]], v), &down[ch]);
-      }
+      sj_rel r = nullptr;
+      const sj_rel_s* in = rel_of(i);
+      st = sieve_step_timed(c, in, t, slot, last_slot[i], &r, &zero);
+      if (st != SJ_OK) break;
+      steps.push_back({op.kind, i, last_slot[i], slot, in->d_n ? -1 : in->nrows});
+      free_rel(c, cur[i]);
+      cur[i] = r;
+      last_slot[i] = slot++;
     }
   }
   if (st == SJ_OK && sync_end) st = sync_read(c);

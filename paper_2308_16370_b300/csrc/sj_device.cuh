@@ -35,6 +35,63 @@ __device__ __forceinline__ uint64_t key_hash(int32_t key, uint64_t seed) {
   return fmix64((uint64_t)(uint32_t)key ^ seed);
 }
 
+// fmix64 of (uint64(uint32 key) xor seed) in 32-bit operations, for the hot
+// probe loops.  With x = seed_hi : (key xor seed_lo), the first xor-shift
+// only folds seed_hi >> 1 into the low word and the first multiply's
+// seed_hi * C1 term is a constant, so both are computed once per launch
+// (Key32Hash) and a key costs one xor, five multiplies and two xor-shifts.
+// The result equals fmix64 bit for bit.
+struct Key32Hash {
+  uint32_t a;  // seed_lo ^ (seed_hi >> 1)
+  uint32_t b;  // low 32 bits of seed_hi * C1_lo
+  uint64_t seed64;
+};
+__device__ __forceinline__ Key32Hash key32_hash_fold(uint64_t seed) {
+  const uint32_t slo = (uint32_t)seed, shi = (uint32_t)(seed >> 32);
+  Key32Hash f;
+  f.a = slo ^ (shi >> 1);
+  f.b = shi * 0xed558ccdu;
+  f.seed64 = seed;
+  return f;
+}
+__device__ __forceinline__ void key32_hash(const Key32Hash& f, uint32_t key, uint32_t& hi,
+                                           uint32_t& lo) {
+  const uint32_t l = key ^ f.a;
+  // (seed_hi : l) * 0xff51afd7ed558ccd mod 2^64
+  const uint64_t p = (uint64_t)l * 0xed558ccdu + ((uint64_t)f.b << 32);
+  const uint32_t xh = (uint32_t)(p >> 32) + l * 0xff51afd7u;
+  const uint32_t xl = (uint32_t)p ^ (xh >> 1);
+  // (xh : xl) * 0xc4ceb9fe1a85ec53 mod 2^64
+  const uint64_t q = (uint64_t)xl * 0x1a85ec53u;
+  hi = (uint32_t)(q >> 32) + xl * 0xc4ceb9feu + xh * 0x1a85ec53u;
+  lo = (uint32_t)q ^ (hi >> 1);
+}
+
+// 1 << (s mod 32) in one funnel shift.
+__device__ __forceinline__ uint32_t bit_of(uint32_t s) { return __funnelshift_l(0u, 1u, s); }
+
+// Register-blocked mask of k = K bits from the low word of the hash.
+template <int K>
+__device__ __forceinline__ uint32_t reg32_mask_fs(uint32_t lo) {
+  uint32_t m = bit_of(lo);
+#pragma unroll
+  for (int i = 1; i < K; ++i) m |= bit_of(lo >> (5 * i));
+  return m;
+}
+
+// L2 policy that keeps a filter resident while key columns stream past it.
+__device__ __forceinline__ uint64_t l2_evict_last_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+// Read-only filter word load (L1-cacheable) with an L2 eviction hint.
+__device__ __forceinline__ uint32_t ld_filter_word(const uint32_t* p, uint64_t pol) {
+  uint32_t v;
+  asm("ld.global.nc.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+  return v;
+}
+
 // Filter view passed by value to kernels.  nblocks is read from device memory
 // because a filter built from a compacted relation is sized on the device.
 struct FilterView {

@@ -335,13 +335,6 @@ __device__ __forceinline__ uint32_t test_reg32_k(const SieveTest& t, uint32_t nw
   return pass & live;
 }
 
-template <int K>
-__device__ __forceinline__ uint32_t test16_reg32_k(const SieveTest& t, uint32_t nwords,
-                                                   const int32_t* key, uint32_t live) {
-  return test_reg32_k<8, K>(t, nwords, key, live & 0xffu) |
-         (test_reg32_k<8, K>(t, nwords, key + 8, live >> 8) << 8);
-}
-
 template <int NK>
 __device__ __forceinline__ uint32_t test_blocked(const SieveTest& t, uint64_t nb, const int32_t* key,
                                                  uint32_t live) {
@@ -367,184 +360,7 @@ __device__ __forceinline__ uint32_t test_blocked(const SieveTest& t, uint64_t nb
   return pass & live;
 }
 
-__device__ __forceinline__ uint32_t test_classic(const SieveTest& t, uint64_t nb, const int32_t* key,
-                                                 uint32_t live) {
-  uint32_t pass = 0;
-#pragma unroll
-  for (int j = 0; j < 16; ++j)
-    if ((live >> j) & 1u) pass |= filter_contains(t.f, nb, key[j]) ? (1u << j) : 0u;
-  return pass;
-}
-
-// All 16 keys of a thread against one test.
-__device__ __forceinline__ uint32_t test16(const SieveTest& t, const int32_t* key, uint32_t live) {
-  if (t.is_pred) return test_pred<16>(t, key, live);
-  const uint64_t nb = __ldg(t.f.hdr);
-  if (t.f.layout == 0) {
-    if (nb * 8 < (1ull << 32)) {
-      const uint32_t nw = (uint32_t)(nb * 8);
-      switch (t.f.k) {
-        case 1: return test16_reg32_k<1>(t, nw, key, live);
-        case 2: return test16_reg32_k<2>(t, nw, key, live);
-        case 3: return test16_reg32_k<3>(t, nw, key, live);
-        case 4: return test16_reg32_k<4>(t, nw, key, live);
-        default: break;
-      }
-    }
-    return test_reg32<8>(t, nb, key, live & 0xffu) | (test_reg32<8>(t, nb, key + 8, live >> 8) << 8);
-  }
-  if (t.f.layout == 1) {
-    uint32_t pass = 0;
-#pragma unroll
-    for (int q = 0; q < 8; ++q)
-      pass |= test_blocked<2>(t, nb, key + 2 * q, (live >> (2 * q)) & 0x3u) << (2 * q);
-    return pass;
-  }
-  return test_classic(t, nb, key, live);
-}
-
-// NT threads per CTA, 16 rows per thread: tiles of NT * 16 rows.
-template <int NT>
-__global__ void __launch_bounds__(NT, 1024 / NT) k_sieve(SieveArgs a) {
-  constexpr int kTile = NT * 16;
-  __shared__ uint32_t s_tile;
-  __shared__ Vec<1> s_warp[NT / 32];
-  __shared__ uint64_t s_prefix;
-  const int tid = threadIdx.x;
-  if (tid == 0) s_tile = draw_ticket(a.tile_counter);
-  __syncthreads();
-  const uint32_t tile = s_tile;
-  const int64_t n = a.n_dev ? (int64_t)(*a.n_dev) : a.n_host;
-  const int64_t ntiles = (n + kTile - 1) / kTile;
-  if ((int64_t)tile >= ntiles) {
-    if (tile == 0 && tid == 0) {
-      *a.out_n = 0;
-      if (a.out_n2) *a.out_n2 = 0;
-    }
-    return;
-  }
-  const int64_t base = (int64_t)tile * kTile;
-  const int32_t* vcol = a.ntest > 0 ? a.test[0].col : nullptr;
-
-  // 1. first test column: 4 coalesced 16-byte loads per thread
-  int32_t key[16];
-  uint32_t alive = 0;
-#pragma unroll
-  for (int v = 0; v < 4; ++v) {
-    const int64_t r0 = base + (int64_t)(v * NT + tid) * 4;
-    if (r0 + 4 <= n) {
-      if (vcol) {
-        const int4 x = __ldcs(reinterpret_cast<const int4*>(vcol + r0));
-        key[4 * v + 0] = x.x;
-        key[4 * v + 1] = x.y;
-        key[4 * v + 2] = x.z;
-        key[4 * v + 3] = x.w;
-      }
-      alive |= 0xfu << (4 * v);
-    } else {
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        key[4 * v + e] = 0;
-        if (r0 + e < n) {
-          if (vcol) key[4 * v + e] = __ldcs(vcol + r0 + e);
-          alive |= 1u << (4 * v + e);
-        }
-      }
-    }
-  }
-
-  // 2. tests; later tests only load the rows still alive
-  if (a.ntest > 0) alive = test16(a.test[0], key, alive);
-#pragma unroll
-  for (int t = 1; t < kMaxTests; ++t) {
-    if (t < a.ntest && alive) {
-#pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const int64_t row = base + (int64_t)((i >> 2) * NT + tid) * 4 + (i & 3);
-        key[i] = ((alive >> i) & 1u) ? __ldcs(a.test[t].col + row) : 0;
-      }
-      alive = test16(a.test[t], key, alive);
-    }
-  }
-  // the first test column's values are reloaded for output if tests overwrote them
-  const bool keys_valid = a.ntest <= 1;
-
-  // 3. block scan of the survivor counts of the 4 chunks (16 bits each)
-  Vec<1> cnt;
-  cnt.v[0] = 0;
-#pragma unroll
-  for (int v = 0; v < 4; ++v) cnt.v[0] |= (uint64_t)__popc((alive >> (4 * v)) & 0xfu) << (16 * v);
-  Vec<1> tot;
-  const Vec<1> ex = block_exclusive_scan<1, NT>(cnt, &tot, s_warp);
-  uint64_t chunk_off[4];
-  uint64_t tile_total = 0;
-#pragma unroll
-  for (int v = 0; v < 4; ++v) {
-    chunk_off[v] = tile_total;
-    tile_total += (tot.v[0] >> (16 * v)) & 0xffffull;
-  }
-
-  // 4. decoupled look-back for the tile's global offset
-  if (tid < 32) {
-    Vec<1> aggv;
-    aggv.v[0] = tile_total;
-    if (tile == 0) {
-      if (tid == 0) {
-        lb_publish<1>(a.lb, 0, 2, aggv);
-        s_prefix = 0;
-      }
-    } else {
-      if (tid == 0) lb_publish<1>(a.lb, tile, 1, aggv);
-      const Vec<1> e = lb_exclusive<1>(a.lb, tile);
-      if (tid == 0) {
-        Vec<1> incv;
-        incv.v[0] = e.v[0] + tile_total;
-        lb_publish<1>(a.lb, tile, 2, incv);
-        s_prefix = e.v[0];
-      }
-    }
-  }
-  __syncthreads();
-  const uint64_t prefix = s_prefix;
-  if ((int64_t)tile == ntiles - 1 && tid == 0) {
-    *a.out_n = prefix + tile_total;
-    if (a.out_n2) *a.out_n2 = prefix + tile_total;
-  }
-
-  // 5. write the survivors of every output column, in input order
-#pragma unroll
-  for (int v = 0; v < 4; ++v) {
-    const uint32_t bits = (alive >> (4 * v)) & 0xfu;
-    if (!bits) continue;
-    const uint64_t pos0 = prefix + chunk_off[v] + ((ex.v[0] >> (16 * v)) & 0xffffull);
-    const int64_t r0 = base + (int64_t)(v * NT + tid) * 4;
-#pragma unroll
-    for (int j = 0; j < kMaxCols; ++j) {
-      if (j >= a.nout) break;
-      int32_t val[4];
-      if (a.out_is_vec[j] && keys_valid) {
-#pragma unroll
-        for (int e = 0; e < 4; ++e) val[e] = key[4 * v + e];
-      } else if (r0 + 4 <= n) {
-        const int4 x = __ldcs(reinterpret_cast<const int4*>(a.in[j] + r0));
-        val[0] = x.x;
-        val[1] = x.y;
-        val[2] = x.z;
-        val[3] = x.w;
-      } else {
-#pragma unroll
-        for (int e = 0; e < 4; ++e) val[e] = ((bits >> e) & 1u) ? __ldcs(a.in[j] + r0 + e) : 0;
-      }
-      int32_t* dst = a.out[j] + pos0;
-      int k = 0;
-#pragma unroll
-      for (int e = 0; e < 4; ++e)
-        if ((bits >> e) & 1u) dst[k++] = val[e];
-    }
-  }
-}
-
-// All 8 keys of a lane against one test (the 8-row counterpart of test16).
+// All 8 keys of a lane against one test.
 template <int K>
 __device__ __forceinline__ uint32_t test8(const SieveTest& t, const int32_t* key, uint32_t live) {
   if (K > 0) {
@@ -580,201 +396,343 @@ __device__ __forceinline__ uint32_t test8(const SieveTest& t, const int32_t* key
   return pass;
 }
 
-// Pass 1 of the two-pass sieve.  Every warp owns a tile of kWarpRows rows
-// (8 per lane, two coalesced 16-byte loads per lane) and compacts its
-// survivors, in input order, into its own slot of a gapped buffer with a
-// warp-level scan only: no warp of the block waits for another.  The first
-// non-key output column of the survivors is loaded before the scan so that its
-// latency overlaps it.  The block's total goes to block_cnt (the move kernel's
-// prefix sums), written by whichever warp finishes last.
-// K > 0: exactly one test, a register-blocked filter with k = K (the hot path).
-template <int K>
-__global__ void __launch_bounds__(kSieveWarpBlock, K > 0 ? 6 : 4) k_sieve_warp(SieveArgs a) {
-  __shared__ uint32_t s_sum, s_done;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int64_t n = a.n_dev ? (int64_t)(*a.n_dev) : a.n_host;
-  const int64_t bbase = (int64_t)blockIdx.x * kSieveBlockRows;
-  if (bbase >= n) return;
-  if (tid == 0) {
-    s_sum = 0;
-    s_done = 0;
-  }
-  __syncthreads();
-  const int64_t wt = (int64_t)blockIdx.x * (kSieveWarpBlock / 32) + warp;
-  const int64_t base = wt * kWarpRows;
-  uint32_t total = 0;
-  if (base < n) {
-    const int32_t* vcol = a.ntest > 0 ? a.test[0].col : nullptr;
-    int32_t key[8];
-    uint32_t alive = 0;
+// ---------------------------------------------------------------- chunked sieve
+// One launch per sieve step (Sec. 2.2 pruning phase).  A CTA draws a ticket t
+// and owns rows [t C, t C + C), C = a.chunk_rows (a multiple of 2048, at most
+// kCkMaxRows):
+//  1. probe: each warp takes 256-row tiles of the chunk; lane l loads rows
+//     32 j + l (j < 8: coalesced 128-byte loads, the next tile's keys loading
+//     while this one is tested) and one ballot per j gives the survivor bits
+//     of rows 32 j .. 32 j + 31 in row order; lane 0 stores the tile's eight
+//     words in shared memory;
+//  2. count: a block scan of the tiles' popcounts gives each tile's offset in
+//     the chunk and the chunk total, which is published for the look-back;
+//  3. list: every survivor's row offset (16 bits) goes to its rank in a
+//     shared-memory list;
+//  4. look-back: the whole CTA reads the states of the 1024 chunks before it at
+//     once and sums back to the nearest inclusive prefix (bounded waits);
+//  5. write: thread i moves survivors i, i + 256, ... of every column, so a
+//     chunk's gathers are in flight together and its output stores contiguous;
+//  6. filters that the following builds write (a.zero_*) are cleared here,
+//     sized by the step's own output: the chunk with output rows [p, p + c)
+//     clears words [W(p), W(p + c)) with W(x) = 8 ceil(bpk x / 256), so the
+//     launch clears exactly the words of a filter over its total rows; chunk 0
+//     also clears the first block (the filter of an empty relation).
+// Survivors are written in input order, as by the other sieve kernels.
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// Keys of one warp tile: row base + 32 j + lane; rows at or beyond n read 0.
+__device__ __forceinline__ void ck_load8(const int32_t* col, int64_t base, int64_t n, int lane,
+                                         int32_t (&k)[8]) {
+  const int32_t* p = col + base + lane;
+  if (base + kCkTileRows <= n) {
 #pragma unroll
-    for (int v = 0; v < 2; ++v) {
-      const int64_t r0 = base + (int64_t)(v * 32 + lane) * 4;
-      if (r0 + 4 <= n) {
-        if (vcol) {
-          const int4 x = __ldcs(reinterpret_cast<const int4*>(vcol + r0));
-          key[4 * v + 0] = x.x;
-          key[4 * v + 1] = x.y;
-          key[4 * v + 2] = x.z;
-          key[4 * v + 3] = x.w;
-        }
-        alive |= 0xfu << (4 * v);
-      } else {
+    for (int j = 0; j < 8; ++j) k[j] = __ldcs(p + 32 * j);
+  } else {
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          key[4 * v + e] = 0;
-          if (r0 + e < n) {
-            if (vcol) key[4 * v + e] = __ldcs(vcol + r0 + e);
-            alive |= 1u << (4 * v + e);
-          }
-        }
-      }
-    }
-    if (K > 0) {
-      alive = test8<K>(a.test[0], key, alive);
-    } else {
-      if (a.ntest > 0) alive = test8<0>(a.test[0], key, alive);
-#pragma unroll 1
-      for (int t = 1; t < a.ntest; ++t) {
-        if (!alive) break;
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const int64_t row = base + (int64_t)((i >> 2) * 32 + lane) * 4 + (i & 3);
-          key[i] = ((alive >> i) & 1u) ? __ldcs(a.test[t].col + row) : 0;
-        }
-        alive = test8<0>(a.test[t], key, alive);
-      }
-    }
-    // the first test column's values are reloaded for output if tests overwrote them
-    const bool keys_valid = a.ntest <= 1;
-    // the first column not served from the key registers: loaded now
-    int pf = -1;
-    for (int j = 0; j < a.nout; ++j)
-      if (!(a.out_is_vec[j] && keys_valid)) {
-        pf = j;
-        break;
-      }
-    int32_t pay[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) pay[i] = 0;
-    if (pf >= 0 && alive) {
-      const int32_t* pcol = a.in[pf] + base + lane * 4;  // this lane's first row
-#pragma unroll
-      for (int i = 0; i < 8; ++i)
-        if ((alive >> i) & 1u) pay[i] = __ldcs(pcol + (i >> 2) * 128 + (i & 3));
-    }
-    // warp scan of the survivor counts of the two 4-row chunks (8 bits each)
-    const uint32_t c = (uint32_t)__popc(alive & 0xfu) | ((uint32_t)__popc(alive >> 4) << 8);
-    uint32_t inc = c;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, inc, d);
-      if (lane >= d) inc += y;
-    }
-    const uint32_t tot = __shfl_sync(0xffffffffu, inc, 31);
-    const uint32_t ex = inc - c;
-    const uint32_t tot0 = tot & 0xffu;
-    total = tot0 + (tot >> 8);
-    if (lane == 0) a.tile_cnt[wt] = total;
-    const uint64_t prefix = (uint64_t)wt * kWarpRows;
-#pragma unroll
-    for (int v = 0; v < 2; ++v) {
-      const uint32_t bits = (alive >> (4 * v)) & 0xfu;
-      if (!bits) continue;
-      const uint64_t pos0 = prefix + (v ? tot0 : 0u) + ((ex >> (8 * v)) & 0xffu);
-      const int64_t r0 = base + (int64_t)(v * 32 + lane) * 4;
-      for (int j = 0; j < a.nout; ++j) {
-        int32_t val[4];
-        if (a.out_is_vec[j] && keys_valid) {
-#pragma unroll
-          for (int e = 0; e < 4; ++e) val[e] = key[4 * v + e];
-        } else if (j == pf) {
-#pragma unroll
-          for (int e = 0; e < 4; ++e) val[e] = pay[4 * v + e];
-        } else {
-#pragma unroll
-          for (int e = 0; e < 4; ++e) val[e] = ((bits >> e) & 1u) ? __ldcs(a.in[j] + r0 + e) : 0;
-        }
-        int32_t* dst = a.out[j] + pos0;
-        int k = 0;
-#pragma unroll
-        for (int e = 0; e < 4; ++e)
-          if ((bits >> e) & 1u) dst[k++] = val[e];
-      }
-    }
-  }
-  if (lane == 0) {
-    atomicAdd(&s_sum, total);
-    __threadfence_block();
-    if (atomicAdd(&s_done, 1u) == kSieveWarpBlock / 32 - 1) a.block_cnt[blockIdx.x] = atomicAdd(&s_sum, 0u);
+    for (int j = 0; j < 8; ++j) k[j] = (base + 32 * j + lane < n) ? __ldcs(p + 32 * j) : 0;
   }
 }
 
-// Pass 2: move every warp tile's survivors from its gapped slot to the dense
-// output.  Block b owns a contiguous range of pass-1 blocks: it sums the
-// block totals before its range (a few KB from L2), scans its warp tiles'
-// counts 256 at a time, and then each thread moves output rows tid,
-// tid + 256, ... of the chunk, finding the source tile by binary search over
-// the chunk's offsets, so a chunk's loads are all in flight together.  The
-// owner of the last tile writes the total.
-__global__ void __launch_bounds__(kBlock) k_sieve_move(SieveMoveArgs a) {
-  constexpr int kGroup = kSieveWarpBlock / 32;  // warp tiles per pass-1 block
-  __shared__ uint64_t s_red[kBlock / 32];
-  __shared__ Vec<1> s_warp[kBlock / 32];
-  __shared__ uint32_t s_off[kBlock];
+// Hot path: one register-blocked filter with k = K and fewer than 2^32 words.
+template <int K>
+__device__ __forceinline__ void ck_test_reg32(const uint32_t* words, uint32_t nwords,
+                                              const Key32Hash& hf, uint64_t pol,
+                                              const int32_t (&key)[8], int64_t base, int64_t n,
+                                              int lane, uint32_t (&b)[8]) {
+  uint32_t w[8], m[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    uint32_t hi, lo;
+    key32_hash(hf, (uint32_t)key[j], hi, lo);
+    m[j] = reg32_mask_fs<K>(lo);
+    w[j] = ld_filter_word(words + __umulhi(hi, nwords), pol);
+  }
+  if (base + kCkTileRows <= n) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) b[j] = __ballot_sync(0xffffffffu, (~w[j] & m[j]) == 0u);
+  } else {
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      b[j] = __ballot_sync(0xffffffffu, (~w[j] & m[j]) == 0u && base + 32 * j + lane < n);
+  }
+}
+
+// Any tests: predicates and filters of every layout, later tests loading only
+// the rows still alive.
+__device__ __forceinline__ void ck_test_generic(const SieveArgs& a, int32_t (&key)[8], int64_t base,
+                                                int64_t n, int lane, uint32_t (&b)[8]) {
+  uint32_t alive = 0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) alive |= (base + 32 * j + lane < n) ? (1u << j) : 0u;
+  if (a.ntest > 0) alive = test8<0>(a.test[0], key, alive);
+#pragma unroll 1
+  for (int t = 1; t < a.ntest; ++t) {
+    if (!__any_sync(0xffffffffu, alive != 0u)) break;
+    const int32_t* p = a.test[t].col + base + lane;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) key[j] = ((alive >> j) & 1u) ? __ldcs(p + 32 * j) : 0;
+    alive = test8<0>(a.test[t], key, alive);
+  }
+#pragma unroll
+  for (int j = 0; j < 8; ++j) b[j] = __ballot_sync(0xffffffffu, (alive >> j) & 1u);
+}
+
+// Exclusive prefix of chunk t > 0 (all threads get it).  The CTA reads the
+// states of chunks t - 1 .. t - 1024 at once, four per thread, waits (bounded)
+// until each holds at least its aggregate, and sums back to the nearest chunk
+// holding an inclusive prefix; a window without one is added whole and the
+// next window read.  A wait that gives up records kErrTimeout and counts the
+// chunk as an inclusive 0, so the kernel always finishes.
+__device__ uint64_t ck_lookback(const LookBack<1>& lb, uint32_t t, int* s_stop, uint64_t* s_red) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int R = kCkWindow / kCkThreads;
+  uint64_t excl = 0;
+  int64_t hi = (int64_t)t - 1;
+  for (;;) {
+    uint64_t w[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int64_t idx = hi - (tid + kCkThreads * r);
+      w[r] = idx >= 0 ? ld_volatile_u64(lb.st + idx) : 0ull;
+    }
+    int best = 0x7fffffff;
+    uint64_t v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int d = tid + kCkThreads * r;
+      const int64_t idx = hi - d;
+      uint32_t s = 2;
+      v[r] = 0;
+      if (idx >= 0) {
+        s = lb_state<1>(lb, w[r]);
+        uint32_t spins = 0, ns = 8;
+        while (s == 0) {
+          if (++spins > kSpinLimit) break;
+          __nanosleep(ns);
+          if (ns < 256) ns <<= 1;
+          w[r] = ld_volatile_u64(lb.st + idx);
+          s = lb_state<1>(lb, w[r]);
+        }
+        if (s == 0) {
+          atomicOr(lb.status, kErrTimeout);
+          s = 2;
+        } else {
+          v[r] = w[r] & kValueMask;
+        }
+      }
+      if (s == 2 && d < best) best = d;
+    }
+    if (tid == 0) *s_stop = 0x7fffffff;
+    __syncthreads();
+    if (best != 0x7fffffff) atomicMin(s_stop, best);
+    __syncthreads();
+    const int stop = *s_stop;
+    uint64_t part = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+      if (tid + kCkThreads * r <= stop) part += v[r];
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) part += __shfl_xor_sync(0xffffffffu, part, d);
+    if (lane == 0) s_red[warp] = part;
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kCkThreads / 32; ++i) excl += s_red[i];
+    __syncthreads();  // s_stop and s_red are reused
+    if (stop != 0x7fffffff) return excl;
+    hi -= kCkWindow;
+  }
+}
+
+// Step 5: survivors i = tid, tid + 256, ... of NC columns, U per thread in flight.
+template <int NC, int U>
+__device__ __forceinline__ void ck_write(const SieveArgs& a, int64_t cbase, uint64_t prefix,
+                                         uint32_t total, const uint16_t* s_list) {
+  for (uint32_t i0 = threadIdx.x; i0 < total; i0 += U * kCkThreads) {
+    int32_t v[NC][U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const uint32_t i = i0 + u * kCkThreads;
+      const int64_t row = cbase + (i < total ? s_list[i] : 0);
+#pragma unroll
+      for (int c = 0; c < NC; ++c)
+        if (c < a.nout && i < total) v[c][u] = __ldcs(a.in[c] + row);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const uint32_t i = i0 + u * kCkThreads;
+#pragma unroll
+      for (int c = 0; c < NC; ++c)
+        if (c < a.nout && i < total) a.out[c][prefix + i] = v[c][u];
+    }
+  }
+}
+
+// Step 6: clear words [W(p0), W(p1)) of every filter the next builds write.
+__device__ __forceinline__ void ck_zero(const SieveArgs& a, uint64_t p0, uint64_t p1, bool first) {
+  for (int z = 0; z < a.nzero; ++z) {
+    const uint64_t bpk = a.zero_bpk[z];
+    uint64_t lo = 8 * ((bpk * p0 + 255) / 256);
+    uint64_t hi = 8 * ((bpk * p1 + 255) / 256);
+    if (first) {
+      lo = 0;
+      if (hi < 8) hi = 8;
+    }
+    if (hi > a.zero_cap_words[z]) hi = a.zero_cap_words[z];
+    uint4* q = reinterpret_cast<uint4*>(a.zero_words[z]);
+    for (uint64_t i = lo / 4 + threadIdx.x; i < hi / 4; i += kCkThreads) q[i] = make_uint4(0, 0, 0, 0);
+  }
+}
+
+template <int K>
+__global__ void __launch_bounds__(kCkThreads, K > 0 ? kCkMinBlocks : 4) k_sieve_chunk(SieveArgs a) {
+  constexpr int kMaxTiles = kCkMaxRows / kCkTileRows;
+  __shared__ __align__(16) uint32_t s_bits[kMaxTiles * 8];
+  __shared__ uint32_t s_toff[kMaxTiles + 1];
+  __shared__ uint16_t s_list[kCkList];
+  __shared__ Vec<1> s_warp[kCkThreads / 32];
+  __shared__ uint64_t s_red[kCkThreads / 32];
+  __shared__ uint32_t s_ticket;
+  __shared__ int s_stop;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) s_ticket = draw_ticket(a.tile_counter);
+  __syncthreads();
+  const uint32_t t = s_ticket;
   const int64_t n = a.n_dev ? (int64_t)(*a.n_dev) : a.n_host;
-  const int64_t ntiles = (n + kWarpRows - 1) / kWarpRows;
-  const int64_t nblk = (n + kSieveBlockRows - 1) / kSieveBlockRows;
-  if (ntiles == 0) {
-    if (blockIdx.x == 0 && tid == 0) {
-      *a.out_n = 0;
-      if (a.out_n2) *a.out_n2 = 0;
+  const int64_t C = a.chunk_rows;
+  const int64_t nchunks = (n + C - 1) / C;
+  if ((int64_t)t >= nchunks) {
+    if (t == 0) {  // empty input
+      if (tid == 0) {
+        *a.out_n = 0;
+        if (a.out_n2) *a.out_n2 = 0;
+      }
+      ck_zero(a, 0, 0, true);
     }
     return;
   }
-  const int64_t per = (nblk + gridDim.x - 1) / gridDim.x;
-  const int64_t b0 = (int64_t)blockIdx.x * per;
-  const int64_t b1 = b0 + per < nblk ? b0 + per : nblk;
-  if (b0 >= b1) return;
-  uint64_t part = 0;
-  for (int64_t u = tid; u < b0; u += kBlock) part += __ldg(a.block_cnt + u);
-#pragma unroll
-  for (int d = 16; d > 0; d >>= 1) part += __shfl_xor_sync(0xffffffffu, part, d);
-  if (lane == 0) s_red[warp] = part;
-  __syncthreads();
-  uint64_t prefix = 0;
-#pragma unroll
-  for (int w = 0; w < kBlock / 32; ++w) prefix += s_red[w];
-  const int64_t t0 = b0 * kGroup;
-  const int64_t t1 = b1 * kGroup < ntiles ? b1 * kGroup : ntiles;
-  for (int64_t c0 = t0; c0 < t1; c0 += kBlock) {
-    const int64_t j = c0 + tid;
-    const uint32_t cnt = j < t1 ? __ldg(a.tile_cnt + j) : 0u;
-    Vec<1> x, tot;
-    x.v[0] = cnt;
-    const Vec<1> ex = block_exclusive_scan<1, kBlock>(x, &tot, s_warp);
-    s_off[tid] = (uint32_t)ex.v[0];  // chunk-relative: at most 256 * kWarpRows
-    __syncthreads();
-    const int m = (int)(t1 - c0 < kBlock ? t1 - c0 : kBlock);
-    const uint32_t rows = (uint32_t)tot.v[0];
-    for (uint32_t r = tid; r < rows; r += kBlock) {
-      int lo = 0, hi = m - 1;  // last tile whose offset is <= r
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (s_off[mid] <= r) lo = mid;
-        else hi = mid - 1;
-      }
-      const uint64_t src = (uint64_t)(c0 + lo) * kWarpRows + (r - s_off[lo]);
-      for (int col = 0; col < a.nout; ++col) a.out[col][prefix + r] = __ldcs(a.gap[col] + src);
+  const int64_t cbase = (int64_t)t * C;
+  const int64_t crows = n - cbase < C ? n - cbase : C;
+  const int ntile = (int)((crows + kCkTileRows - 1) / kCkTileRows);
+
+  // 1. probe
+  {
+    const int32_t* col0 = a.ntest > 0 ? a.test[0].col : nullptr;
+    uint32_t nwords = 0;
+    Key32Hash hf = {0, 0, 0};
+    uint64_t pol = 0;
+    if (K > 0) {
+      nwords = (uint32_t)(__ldg(a.test[0].f.hdr) * 8);
+      hf = key32_hash_fold(a.test[0].f.seed);
+      pol = l2_evict_last_policy();
     }
-    prefix += rows;
-    __syncthreads();  // s_off reused by the next chunk
+    int32_t cur[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) cur[j] = 0;
+    if (warp < ntile && col0) ck_load8(col0, cbase + (int64_t)warp * kCkTileRows, n, lane, cur);
+    for (int T = warp; T < ntile; T += kCkThreads / 32) {
+      const int64_t base = cbase + (int64_t)T * kCkTileRows;
+      // the warp's next tile loads while this one is tested
+      int32_t nxt[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) nxt[j] = 0;
+      const int Tn = T + kCkThreads / 32;
+      if (Tn < ntile && col0) ck_load8(col0, cbase + (int64_t)Tn * kCkTileRows, n, lane, nxt);
+      uint32_t b[8];
+      if (K > 0) ck_test_reg32<(K > 0 ? K : 1)>(a.test[0].f.words, nwords, hf, pol, cur, base, n, lane, b);
+      else ck_test_generic(a, cur, base, n, lane, b);
+      if (lane == 0) {
+        uint4* d = reinterpret_cast<uint4*>(s_bits + T * 8);
+        d[0] = make_uint4(b[0], b[1], b[2], b[3]);
+        d[1] = make_uint4(b[4], b[5], b[6], b[7]);
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) cur[j] = nxt[j];
+    }
   }
-  if (t1 == ntiles && tid == 0) {
-    *a.out_n = prefix;
-    if (a.out_n2) *a.out_n2 = prefix;
+  __syncthreads();
+
+  // 2. count: tile offsets and the chunk total
+  uint32_t total;
+  {
+    uint32_t c = 0;
+    if (tid < ntile) {
+      const uint4 x = reinterpret_cast<const uint4*>(s_bits)[2 * tid];
+      const uint4 y = reinterpret_cast<const uint4*>(s_bits)[2 * tid + 1];
+      c = __popc(x.x) + __popc(x.y) + __popc(x.z) + __popc(x.w) + __popc(y.x) + __popc(y.y) +
+          __popc(y.z) + __popc(y.w);
+    }
+    Vec<1> cv, tot;
+    cv.v[0] = c;
+    const Vec<1> ex = block_exclusive_scan<1, kCkThreads>(cv, &tot, s_warp);
+    if (tid < ntile) s_toff[tid] = (uint32_t)ex.v[0];
+    total = (uint32_t)tot.v[0];
+    if (tid == 0) s_toff[ntile] = total;
   }
+  if (tid == 0) {
+    Vec<1> agg;
+    agg.v[0] = total;
+    lb_publish<1>(a.lb, t, t == 0 ? 2u : 1u, agg);
+  }
+  __syncthreads();
+
+  // 3. survivors of ranks [0, kCkList) listed, then 4. look-back, 5. write;
+  // denser chunks take more rounds of kCkList ranks
+  uint64_t prefix = 0;
+  for (uint32_t r0 = 0; r0 == 0 || r0 < total; r0 += kCkList) {
+    const uint32_t r1 = r0 + kCkList;
+    if (r0 > 0) __syncthreads();  // the previous round's list is consumed
+    for (int T = warp; T < ntile; T += kCkThreads / 32) {
+      const uint32_t tb = s_toff[T];
+      if (tb >= r1 || s_toff[T + 1] <= r0) continue;  // no rank of this round (warp-uniform)
+      const uint32_t wj = lane < 8 ? s_bits[T * 8 + lane] : 0u;
+      const uint32_t cj = __popc(wj);
+      uint32_t inc = cj;
+#pragma unroll
+      for (int d = 1; d < 8; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= d) inc += y;
+      }
+      const uint32_t exj = inc - cj;
+      uint32_t nz = __ballot_sync(0xffffffffu, wj != 0u);
+      while (nz) {
+        const int j = __ffs(nz) - 1;
+        nz &= nz - 1;
+        const uint32_t bj = __shfl_sync(0xffffffffu, wj, j);
+        const uint32_t ej = __shfl_sync(0xffffffffu, exj, j);
+        const uint32_t rank = tb + ej + __popc(bj & lanemask_lt());
+        if (((bj >> lane) & 1u) && rank >= r0 && rank < r1)
+          s_list[rank - r0] = (uint16_t)(T * kCkTileRows + 32 * j + lane);
+      }
+    }
+    if (r0 == 0) {
+      if (t > 0) {
+        prefix = ck_lookback(a.lb, t, &s_stop, s_red);
+        if (tid == 0) {
+          Vec<1> inc;
+          inc.v[0] = prefix + total;
+          lb_publish<1>(a.lb, t, 2u, inc);
+        }
+      }
+      if ((int64_t)t == nchunks - 1 && tid == 0) {
+        *a.out_n = prefix + total;
+        if (a.out_n2) *a.out_n2 = prefix + total;
+      }
+    }
+    __syncthreads();  // this round's list is complete
+    const uint32_t m = total - r0 < (uint32_t)kCkList ? total - r0 : (uint32_t)kCkList;
+    if (a.nout <= 2) ck_write<2, 4>(a, cbase, prefix + r0, m, s_list);
+    else if (a.nout <= 4) ck_write<4, 2>(a, cbase, prefix + r0, m, s_list);
+    else ck_write<kMaxCols, 1>(a, cbase, prefix + r0, m, s_list);
+  }
+
+  // 6. clear the next filters' words
+  ck_zero(a, prefix, prefix + total, t == 0);
 }
 
 // ---------------------------------------------------------------- scan
@@ -1548,28 +1506,33 @@ void launch_bloom_probe(const BloomProbeArgs& a, int num_sms, cudaStream_t s) {
   k_bloom_probe<<<host_grid(a.n, kBlock * 4, num_sms * 8), kBlock, 0, s>>>(a);
 }
 
-void launch_sieve(const SieveArgs& a, int64_t n_upper, cudaStream_t s) {
-  k_sieve<kSieveThreads><<<host_grid(n_upper, kSieveTile, 1 << 30), kSieveThreads, 0, s>>>(a);
+int sieve_chunk_rows(int64_t n_upper, int num_sms) {
+  // one chunk per CTA slot of the GPU (kCkMinBlocks per SM), so that one wave
+  // splits the rows evenly; whole warp tiles, at least one tile per warp
+  const int64_t slots = (int64_t)(num_sms > 0 ? num_sms : 1) * kCkMinBlocks;
+  int64_t c = (n_upper + slots - 1) / slots;
+  c = (c + kCkTileRows - 1) / kCkTileRows * kCkTileRows;
+  if (c < kCkChunkQuantum) c = kCkChunkQuantum;
+  if (c > kCkMaxRows) c = kCkMaxRows;
+  return (int)c;
 }
 
-void launch_sieve_two_pass(const SieveArgs& a, const SieveMoveArgs& m, int64_t n_upper, int num_sms,
-                           cudaStream_t s) {
-  const int g = host_grid(n_upper, kSieveBlockRows, 1 << 30);
-  // the hot instance: one register-blocked filter test with k <= 4 (k is
-  // known on the host; the 32-bit word count is checked on the device)
+void launch_sieve_chunk(const SieveArgs& a, int64_t n_upper, int num_sms, cudaStream_t s) {
+  (void)num_sms;
+  int64_t g = (n_upper + a.chunk_rows - 1) / a.chunk_rows;
+  if (g < 1) g = 1;
   const bool fast = a.ntest == 1 && !a.test[0].is_pred && a.test[0].f.layout == 0 &&
                     a.test[0].f.k >= 1 && a.test[0].f.k <= 4 && a.fast_words_ok;
   if (!fast) {
-    k_sieve_warp<0><<<g, kSieveWarpBlock, 0, s>>>(a);
-  } else {
-    switch (a.test[0].f.k) {
-      case 1: k_sieve_warp<1><<<g, kSieveWarpBlock, 0, s>>>(a); break;
-      case 2: k_sieve_warp<2><<<g, kSieveWarpBlock, 0, s>>>(a); break;
-      case 3: k_sieve_warp<3><<<g, kSieveWarpBlock, 0, s>>>(a); break;
-      default: k_sieve_warp<4><<<g, kSieveWarpBlock, 0, s>>>(a); break;
-    }
+    k_sieve_chunk<0><<<(unsigned)g, kCkThreads, 0, s>>>(a);
+    return;
   }
-  k_sieve_move<<<g < 4 * num_sms ? g : 4 * num_sms, kBlock, 0, s>>>(m);
+  switch (a.test[0].f.k) {
+    case 1: k_sieve_chunk<1><<<(unsigned)g, kCkThreads, 0, s>>>(a); break;
+    case 2: k_sieve_chunk<2><<<(unsigned)g, kCkThreads, 0, s>>>(a); break;
+    case 3: k_sieve_chunk<3><<<(unsigned)g, kCkThreads, 0, s>>>(a); break;
+    default: k_sieve_chunk<4><<<(unsigned)g, kCkThreads, 0, s>>>(a); break;
+  }
 }
 
 void launch_scan_u32(const ScanArgs& a, int64_t n_upper, int num_sms, cudaStream_t s) {

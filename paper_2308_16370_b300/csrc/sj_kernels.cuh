@@ -34,6 +34,8 @@ struct BloomProbeArgs {
 void launch_bloom_probe(const BloomProbeArgs& a, int num_sms, cudaStream_t s);
 
 // ------------------------------------------------------------------ sieve
+constexpr int kMaxZero = 4;    // filters one chunked sieve step zeroes for the builds after it
+
 // One test of a sieve step: a range predicate (lo <= v < hi) or a filter probe.
 struct SieveTest {
   const int32_t* col;
@@ -51,42 +53,35 @@ struct SieveArgs {
   SieveTest test[kMaxTests];
   int64_t n_host;
   const uint64_t* n_dev;
-  uint64_t* out_n;        // kept rows (written by the last tile)
+  uint64_t* out_n;        // kept rows (written by the last chunk)
   uint64_t* out_n2;       // optional second copy (per-step statistics), or null
-  uint32_t* tile_counter; // 0 at launch (reset by the kernel for the next one)
-  LookBack<1> lb;
-  uint32_t* tile_cnt;     // two-pass sieve: survivors per warp tile
-  uint32_t* block_cnt;    // two-pass sieve: survivors per pass-1 block
+  uint32_t* tile_counter; // chunk ticket: 0 at launch (reset by the kernel for the next one)
+  LookBack<1> lb;         // one state word per chunk
   int32_t fast_words_ok;  // filter word count of test 0 is below 2^32
+  // chunked sieve (k_sieve_chunk)
+  int32_t chunk_rows;     // rows per chunk, a multiple of kCkTileRows, at most kCkMaxRows
+  int32_t nzero;          // filters the following builds write: zeroed here, see k_sieve_chunk
+  uint32_t* zero_words[kMaxZero];
+  uint32_t zero_bpk[kMaxZero];
+  uint64_t zero_cap_words[kMaxZero];
 };
 
-// Pass 2 of the two-pass sieve (see k_sieve_move).
-struct SieveMoveArgs {
-  const int32_t* gap[kMaxCols];   // gapped pass-1 output, kWarpRows rows per tile slot
-  int32_t* out[kMaxCols];
-  int nout;
-  const uint32_t* tile_cnt;
-  const uint32_t* block_cnt;
-  int64_t n_host;
-  const uint64_t* n_dev;
-  uint64_t* out_n;
-  uint64_t* out_n2;
-};
-// Tiles of kSieveThreads x 16 rows: each thread 4 vectors x 4 int32.
-#ifndef SJ_SIEVE_THREADS
-#define SJ_SIEVE_THREADS 256
-#endif
-constexpr int kSieveThreads = SJ_SIEVE_THREADS;
-constexpr int kSieveTile = kSieveThreads * 16;
-// Two-pass sieve: warp tiles of 32 lanes x 8 rows, 8 warps per block.
-constexpr int kWarpRows = 256;
-constexpr int kSieveWarpBlock = 256;
-constexpr int kSieveBlockRows = kWarpRows * (kSieveWarpBlock / 32);
-void launch_sieve(const SieveArgs& a, int64_t n_upper, cudaStream_t s);
-// Two-pass variant: pass 1 writes each tile's survivors to a gapped buffer
-// (a.out) and its count to a.tile_cnt; pass 2 compacts them into m.out.
-void launch_sieve_two_pass(const SieveArgs& a, const SieveMoveArgs& m, int64_t n_upper, int num_sms,
-                           cudaStream_t s);
+// Chunked single-launch sieve (k_sieve_chunk).  A CTA takes one chunk of
+// chunk_rows rows by ticket: it probes the chunk (survivor bits per row in
+// shared memory), lists its survivors in shared memory, gets its output offset
+// from a decoupled look-back over the chunks before it (read 1024 at a time by
+// the whole CTA) and writes its survivors.  Scratch: one ticket counter and
+// one look-back word per chunk (a.tile_counter, a.lb).
+constexpr int kCkThreads = 256;
+constexpr int kCkTileRows = 256;                 // warp tile: 8 rows per lane, row = 32 j + lane
+constexpr int kCkChunkQuantum = kCkTileRows * (kCkThreads / 32);
+constexpr int kCkMaxRows = 16384;                // rows per chunk (row offsets fit 16 bits)
+constexpr int kCkMinBlocks = 5;                  // resident CTAs per SM (48 registers, no spills)
+constexpr int kCkList = 2048;                    // survivors listed per round (2 bytes each)
+constexpr int kCkWindow = 4 * kCkThreads;        // chunk states read per look-back round
+// Rows per chunk for a launch over at most n_upper rows.
+int sieve_chunk_rows(int64_t n_upper, int num_sms);
+void launch_sieve_chunk(const SieveArgs& a, int64_t n_upper, int num_sms, cudaStream_t s);
 
 // ------------------------------------------------------------------ scans
 struct ScanArgs {

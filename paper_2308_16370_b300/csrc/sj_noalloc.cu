@@ -4,8 +4,8 @@
 // where they want to sieve: code running inside a custom allocator or memory
 // manager, or a runtime that hands out only pre-reserved buffers and forbids
 // allocations on its hot path.  sj_sieve_noalloc serves them: the caller
-// passes inputs and outputs, and the only scratch the step needs (the tile
-// ticket, the look-back tile states and a filter header) lives in the
+// passes inputs and outputs, and the only scratch the step needs (the chunk
+// ticket, the look-back chunk states and a filter header) lives in the
 // fixed-size file-scope device array below, which every GPU that loads this
 // library holds until the process exits.
 #include <cuda_runtime.h>
@@ -18,20 +18,23 @@
 
 namespace {
 
-// Largest relation one call accepts, and the scratch it implies.
+// Largest relation one call accepts, and the scratch it implies: the chunked
+// sieve takes at most kCkMaxRows rows per chunk, or one chunk per CTA slot of
+// the GPU when that is more rows (at most 8192 chunks up to 2^27 rows on any
+// GPU with fewer than 1638 SMs; checked per call).
 constexpr int64_t kMaxRows = SJ_NOALLOC_MAX_ROWS;
-constexpr int64_t kMaxTiles = (kMaxRows + sj::kSieveTile - 1) / sj::kSieveTile;
-constexpr size_t kOffCounter = 0;    // uint32 tile ticket
+constexpr int64_t kMaxChunks = (kMaxRows + sj::kCkMaxRows - 1) / sj::kCkMaxRows;
+constexpr size_t kOffCounter = 0;    // uint32 chunk ticket
 constexpr size_t kOffStatus = 64;    // uint32 status word (when the caller passes none)
 constexpr size_t kOffHdr = 128;      // uint64 nblocks, uint64 rows inserted
-constexpr size_t kOffStates = 256;   // one packed look-back word per tile
-constexpr size_t kScratchBytes = kOffStates + 8 * kMaxTiles;  // 256 KiB + 256 B
+constexpr size_t kOffStates = 256;   // one packed look-back word per chunk
+constexpr size_t kScratchBytes = kOffStates + 8 * kMaxChunks;  // 64 KiB + 256 B
 
 static __device__ __align__(256) unsigned char g_sieve_scratch[kScratchBytes];
 
 // Device-side set-up of one call: clear what must start at zero and write the
 // filter header the sieve kernel reads.  Device code names the array directly.
-__global__ void k_noalloc_prepare(uint64_t nblocks, uint32_t ntiles, int clear_status) {
+__global__ void k_noalloc_prepare(uint64_t nblocks, uint32_t nchunks, int clear_status) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0) {
     *reinterpret_cast<uint32_t*>(g_sieve_scratch + kOffCounter) = 0u;
@@ -41,16 +44,17 @@ __global__ void k_noalloc_prepare(uint64_t nblocks, uint32_t ntiles, int clear_s
     hdr[1] = 0;
   }
   uint64_t* states = reinterpret_cast<uint64_t*>(g_sieve_scratch + kOffStates);
-  for (uint32_t t = i; t < ntiles; t += gridDim.x * blockDim.x) states[t] = 0ull;
+  for (uint32_t t = i; t < nchunks; t += gridDim.x * blockDim.x) states[t] = 0ull;
 }
 
 // Host code must not use g_sieve_scratch as an address: in host code the name
 // is a host-side stand-in.  The device address is looked up once per device.
 constexpr int kMaxDevices = 64;
 unsigned char* g_dev_addr[kMaxDevices] = {};
+int g_dev_sms[kMaxDevices] = {};
 std::mutex g_mu;
 
-sj_status scratch_address(int device, unsigned char** out, const char** err) {
+sj_status scratch_address(int device, unsigned char** out, int* num_sms, const char** err) {
   std::lock_guard<std::mutex> lock(g_mu);
   if (!g_dev_addr[device]) {
     void* p = nullptr;
@@ -59,9 +63,17 @@ sj_status scratch_address(int device, unsigned char** out, const char** err) {
       if (err) *err = "cudaGetSymbolAddress of the sieve scratch array failed";
       return SJ_ECUDA;
     }
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || sms < 1) {
+      cudaGetLastError();
+      if (err) *err = "cudaDeviceGetAttribute(multiprocessor count) failed";
+      return SJ_ECUDA;
+    }
     g_dev_addr[device] = static_cast<unsigned char*>(p);
+    g_dev_sms[device] = sms;
   }
   *out = g_dev_addr[device];
+  *num_sms = g_dev_sms[device];
   return SJ_OK;
 }
 
@@ -101,13 +113,19 @@ extern "C" sj_status sj_sieve_noalloc(void* cuda_stream, int ncols, const int32_
     return SJ_ECUDA;
   }
   unsigned char* base = nullptr;
-  sj_status st = scratch_address(device, &base, err);
+  int num_sms = 0;
+  sj_status st = scratch_address(device, &base, &num_sms, err);
   if (st != SJ_OK) return st;
 
   cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
-  const int64_t ntiles = (nrows + sj::kSieveTile - 1) / sj::kSieveTile;
-  const uint32_t prep_grid = (uint32_t)((ntiles + 255) / 256 > 0 ? (ntiles + 255) / 256 : 1);
-  k_noalloc_prepare<<<prep_grid, 256, 0, stream>>>(nblocks, (uint32_t)ntiles, status ? 0 : 1);
+  const int chunk_rows = sj::sieve_chunk_rows(nrows, num_sms);
+  const int64_t nchunks = (nrows + chunk_rows - 1) / chunk_rows;
+  if (nchunks > kMaxChunks) {
+    if (err) *err = "too many chunks for the fixed scratch on this GPU";
+    return SJ_EINVAL;
+  }
+  const uint32_t prep_grid = (uint32_t)((nchunks + 255) / 256 > 0 ? (nchunks + 255) / 256 : 1);
+  k_noalloc_prepare<<<prep_grid, 256, 0, stream>>>(nblocks, (uint32_t)nchunks, status ? 0 : 1);
 
   sj::SieveArgs a = {};
   a.ntest = 1;
@@ -132,7 +150,10 @@ extern "C" sj_status sj_sieve_noalloc(void* cuda_stream, int ncols, const int32_
   a.lb.st = reinterpret_cast<uint64_t*>(base + kOffStates);
   a.lb.status = status ? status : reinterpret_cast<uint32_t*>(base + kOffStatus);
   a.lb.epoch = 0;  // the states are zeroed by k_noalloc_prepare
-  sj::launch_sieve(a, nrows, stream);
+  a.chunk_rows = chunk_rows;
+  a.fast_words_ok = 1;  // nblocks < 2^32 is checked above, but the word count must be too
+  if (nblocks * 8 >= (uint64_t(1) << 32)) a.fast_words_ok = 0;
+  sj::launch_sieve_chunk(a, nrows, num_sms, stream);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     if (err) *err = cudaGetErrorString(e);
