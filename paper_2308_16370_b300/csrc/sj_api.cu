@@ -496,8 +496,7 @@ sj_status sieve_step_timed(sj_ctx* c, const sj_rel_s* in, const std::vector<Test
     }
   }
   a.chunk_rows = sieve_chunk_rows(cap, c->num_sms);
-  const int64_t nchunks = (cap + a.chunk_rows - 1) / a.chunk_rows;
-  sj_status st = scratch_for<1>(c, nchunks, &a.tile_counter, &a.lb);
+  sj_status st = scratch_for<1>(c, (cap + a.chunk_rows - 1) / a.chunk_rows, &a.tile_counter, &a.lb);
   if (st != SJ_OK) {
     free_rel(c, r);
     return st;
@@ -1221,18 +1220,15 @@ sj_status build_adjacency(sj_ctx* c, Temps& tmp, const int32_t* keys, int64_t n,
     launch_mm_insert(mi, c->num_sms, c->stream);
   }
   SJ_TRY(check_launch(c, "k_mm_insert"));
-  ScanArgs sa;
-  sa.in = cnt;
-  sa.out = off;
-  sa.n_host = ns;
-  sa.n_dev = nullptr;
-  sa.total = nullptr;
-  SJ_TRY(scratch_for<1>(c, (ns + kScanTile - 1) / kScanTile, &sa.tile_counter, &sa.lb));
+  unsigned long long* cursor = tmp.get<unsigned long long>(1, &st);
+  if (st != SJ_OK) return fail(c, st, "adjacency allocation failed");
+  SJ_CUDA(c, cudaMemsetAsync(cursor, 0, sizeof(unsigned long long), c->stream));
+  GroupOffArgs ga{cnt, off, ns, nullptr, cursor};
   {
     Launch L(c, SJ_K_HT_BUILD, 12.0 * (double)ns);
-    launch_scan_u32(sa, ns, c->num_sms, c->stream);
+    launch_group_offsets(ga, ns, c->num_sms, c->stream);
   }
-  SJ_TRY(check_launch(c, "k_scan_u32"));
+  SJ_TRY(check_launch(c, "k_group_offsets"));
   MMScatterArgs ms{rid, rank, off, n, rows};
   {
     Launch L(c, SJ_K_HT_BUILD, 20.0 * (double)n);
@@ -1655,6 +1651,7 @@ sj_status build_adjacency_dev(sj_ctx* c, Temps& tmp, const int32_t* keys, const 
                               int64_t n_host, int64_t cap, uint32_t* mask, uint32_t* nslots_dev,
                               Adjacency* g) {
   sj_status st = SJ_OK;
+  const int sms = c->num_sms;
   const int64_t capn = std::max<int64_t>(cap, 1);
   const uint64_t cap_slots = pow2_at_least(std::max<uint64_t>(64, 2 * (uint64_t)capn));
   unsigned long long* slots = tmp.get<unsigned long long>(cap_slots, &st);
@@ -1663,11 +1660,12 @@ sj_status build_adjacency_dev(sj_ctx* c, Temps& tmp, const int32_t* keys, const 
   uint32_t* rank = tmp.get<uint32_t>(capn, &st);
   uint64_t* off = tmp.get<uint64_t>(cap_slots, &st);
   int32_t* rows = tmp.get<int32_t>(capn, &st);
+  unsigned long long* cursor = tmp.get<unsigned long long>(1, &st);
   if (st != SJ_OK) return fail(c, st, "adjacency allocation failed");
-  TableInitArgs ti{slots, mask, n_dev, n_host, nullptr, cnt, nslots_dev};
+  TableInitArgs ti{slots, mask, n_dev, n_host, nullptr, cnt, nslots_dev, cursor};
   {
     Launch L(c, SJ_K_HT_BUILD, 0.0);
-    launch_table_init(ti, (int64_t)cap_slots, c->num_sms, c->stream);
+    launch_table_init(ti, (int64_t)cap_slots, sms, c->stream);
   }
   SJ_TRY(check_launch(c, "k_table_init"));
   Table t;
@@ -1679,26 +1677,20 @@ sj_status build_adjacency_dev(sj_ctx* c, Temps& tmp, const int32_t* keys, const 
   if (!n_dev) mi.n = n_host;
   {
     Launch L(c, SJ_K_HT_BUILD, 12.0 * (double)cap);
-    launch_mm_insert(mi, c->num_sms, c->stream);
+    launch_mm_insert(mi, sms, c->stream);
   }
   SJ_TRY(check_launch(c, "k_mm_insert"));
-  ScanArgs sa;
-  sa.in = cnt;
-  sa.out = off;
-  sa.n_host = 0;
-  sa.n_dev = nslots_dev;
-  sa.total = nullptr;
-  SJ_TRY(scratch_for<1>(c, ((int64_t)cap_slots + kScanTile - 1) / kScanTile, &sa.tile_counter, &sa.lb));
+  GroupOffArgs ga{cnt, off, 0, nslots_dev, cursor};
   {
     Launch L(c, SJ_K_HT_BUILD, 12.0 * (double)cap);
-    launch_scan_u32(sa, (int64_t)cap_slots, c->num_sms, c->stream);
+    launch_group_offsets(ga, (int64_t)cap_slots, sms, c->stream);
   }
-  SJ_TRY(check_launch(c, "k_scan_u32"));
+  SJ_TRY(check_launch(c, "k_group_offsets"));
   MMScatterArgs ms{rid, rank, off, n_dev ? cap : n_host, rows};
   ms.n_dev = n_dev;
   {
     Launch L(c, SJ_K_HT_BUILD, 20.0 * (double)cap);
-    launch_mm_scatter(ms, c->num_sms, c->stream);
+    launch_mm_scatter(ms, sms, c->stream);
   }
   SJ_TRY(check_launch(c, "k_mm_scatter"));
   g->t = t;
@@ -1731,7 +1723,12 @@ struct SideDrain {
 };
 
 sj_status ensure_side(sj_ctx* c, int nlev) {
-  if (!c->side && cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess)
+  int prio_least = 0, prio_greatest = 0;
+  if (cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest) != cudaSuccess) {
+    cudaGetLastError();
+    prio_least = 0;
+  }
+  if (!c->side && cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_least) != cudaSuccess)
     return fail(c, SJ_ECUDA, "side stream creation failed");
   if (!c->ev_ready && cudaEventCreateWithFlags(&c->ev_ready, cudaEventDisableTiming) != cudaSuccess)
     return fail(c, SJ_ECUDA, "event creation failed");
@@ -2246,14 +2243,17 @@ sj_status run_device_sized(sj_ctx* c, const sj_path* path, const sj_sieve_opts* 
                            sj_result* result, std::vector<uint64_t>* T, bool finish) {
   const std::vector<LevelPlan> plan = join_order(path);
   const int nlev = (int)plan.size() - 1;
-  std::vector<int> level_of(path->nrel, -1);
-  for (int L = 0; L < nlev; ++L) level_of[plan[L].rel] = L;
   std::vector<Adjacency> built(std::max(nlev, 0));
   Temps bt(c);  // arena memory: lives until the arena scope ends
   sj_status st = SJ_OK;
   uint32_t* smallb = bt.get<uint32_t>(2 * SJ_MAX_REL, &st);
   if (st != SJ_OK) return fail(c, st, "allocation failed");
+  std::vector<int> level_of(path->nrel, -1);
+  for (int L = 0; L < nlev; ++L) level_of[plan[L].rel] = L;
   SJ_TRY(ensure_side(c, nlev));
+  // each level's multimap is built on the side stream as soon as the pruning
+  // phase is done with its relation, overlapping the remaining sieve steps
+  // (those launch at a higher priority, see launch_sieve_chunk)
   const FinalHook hook = [&](int i, const sj_rel_s* r) -> sj_status {
     const int L = level_of[i];
     if (L < 0) return SJ_OK;
@@ -2284,7 +2284,16 @@ void capture_graph(sj_ctx* c, uint64_t key, const sj_path* path, const sj_sieve_
   const uint64_t gen = c->arena_gen;
   sj_rel sieved[SJ_MAX_REL] = {};
   cudaGraph_t graph = nullptr;
-  if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+  // the capture stream has the device's highest priority and the side stream
+  // its lowest, and the graph keeps those per node: the critical path's
+  // kernels (pruning, probes) get SMs before the side stream's table builds
+  int prio_least = 0, prio_greatest = 0;
+  if (cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest) != cudaSuccess) {
+    cudaGetLastError();
+    prio_least = prio_greatest = 0;
+  }
+  if (!c->cap_stream &&
+      cudaStreamCreateWithPriority(&c->cap_stream, cudaStreamNonBlocking, prio_greatest) != cudaSuccess) {
     cudaGetLastError();
     c->cap_stream = nullptr;
   }
@@ -2309,7 +2318,7 @@ void capture_graph(sj_ctx* c, uint64_t key, const sj_path* path, const sj_sieve_
     if (e != cudaSuccess) note_graph_failure(c, std::string("end capture: ") + cudaGetErrorString(e));
     cudaError_t ei = cudaSuccess;
     if (st == SJ_OK && e == cudaSuccess && graph &&
-        (ei = cudaGraphInstantiate(&G.exec, graph, 0)) == cudaSuccess) {
+        (ei = cudaGraphInstantiate(&G.exec, graph, cudaGraphInstantiateFlagUseNodePriority)) == cudaSuccess) {
       G.failed = false;
       G.caps = caps;
       G.nkernels = c->launches - launches0;

@@ -1,14 +1,15 @@
 // sm_103a kernels of the sieved multi-way join.
 //
-//   k_bloom_build  -- Bloom filter build (Sec. 2.1 step 1): read-before-OR
-//                     atomics into an L2-resident filter
-//   k_bloom_probe  -- membership test (Sec. 2.1 step 3)
-//   k_sieve        -- one pruning step (Sec. 2.2): vectorised key loads, filter
-//                     probes, order-preserving stream compaction with a
-//                     decoupled look-back
-//   k_scan_u32     -- exclusive prefix sum (hash-table offsets)
-//   k_mm_*         -- multimap hash join level (Sec. 2.2 enumeration phase)
-//   k_agg_*        -- last join level folded into COUNT(*) / SUM
+//   k_bloom_build    -- Bloom filter build (Sec. 2.1 step 1): atomicOr into an
+//                       L2-resident filter, repeated (word, mask) pairs skipped
+//   k_bloom_probe    -- membership test (Sec. 2.1 step 3)
+//   k_sieve_chunk    -- one pruning step (Sec. 2.2): key loads, filter probes,
+//                       survivor bits by warp ballots, order-preserving
+//                       compaction with a CTA-wide decoupled look-back
+//   k_group_offsets  -- row-group offsets of a multimap (one atomic per tile)
+//   k_mm_*           -- multimap hash join level (Sec. 2.2 enumeration phase)
+//   k_agg_*          -- last join level folded into COUNT(*) / SUM
+//   k_pair_*, k_triangles -- the cyclic query with its closing filter (Sec. 2.3)
 //
 // Nothing here is a dense contraction, so there are no tensor-core paths: all
 // kernels are bound by HBM bandwidth or by L2 latency of random accesses.
@@ -19,9 +20,16 @@ namespace sj {
 namespace {
 
 constexpr uint64_t kTableSeed = 0x9e3779b97f4a7c15ull;
+// fmix64(uint32(key) xor kTableSeed) with the seed's terms folded at compile time
+constexpr uint32_t kTableHashA = (uint32_t)kTableSeed ^ ((uint32_t)(kTableSeed >> 32) >> 1);
+constexpr uint32_t kTableHashB = (uint32_t)(kTableSeed >> 32) * 0xed558ccdu;
 
+// Home bucket of a key: the low word of fmix64(uint32(key) xor kTableSeed).
 __device__ __forceinline__ uint32_t table_bucket(int32_t key, uint32_t mask) {
-  return (uint32_t)fmix64((uint64_t)(uint32_t)key ^ kTableSeed) & mask;
+  const Key32Hash h = {kTableHashA, kTableHashB, kTableSeed};
+  uint32_t hi, lo;
+  key32_hash(h, (uint32_t)key, hi, lo);
+  return lo & mask;
 }
 
 // A table whose mask was written on the device (k_table_init) reads it once.
@@ -589,6 +597,54 @@ __device__ __forceinline__ void ck_zero(const SieveArgs& a, uint64_t p0, uint64_
   }
 }
 
+// Steps 3 and 5 of a chunk whose survivor bits (s_bits) and tile offsets
+// (s_toff, ntile + 1 entries) are known: survivors are listed kCkList ranks
+// per round in shared memory (row offsets in the chunk) and written, round by
+// round.  `resolve` runs once, between the first round's listing and its
+// writes (all threads call it), and returns the chunk's output offset.
+template <class Resolve>
+__device__ __forceinline__ uint64_t ck_list_and_write(const SieveArgs& a, int64_t cbase, int ntile,
+                                                      uint32_t total, const uint32_t* s_bits,
+                                                      const uint32_t* s_toff, uint16_t* s_list,
+                                                      Resolve resolve) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint64_t prefix = 0;
+  for (uint32_t r0 = 0; r0 == 0 || r0 < total; r0 += kCkList) {
+    const uint32_t r1 = r0 + kCkList;
+    if (r0 > 0) __syncthreads();  // the previous round's list is consumed
+    for (int T = warp; T < ntile; T += kCkThreads / 32) {
+      const uint32_t tb = s_toff[T];
+      if (tb >= r1 || s_toff[T + 1] <= r0) continue;  // no rank of this round (warp-uniform)
+      const uint32_t wj = lane < 8 ? s_bits[T * 8 + lane] : 0u;
+      const uint32_t cj = __popc(wj);
+      uint32_t inc = cj;
+#pragma unroll
+      for (int d = 1; d < 8; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= d) inc += y;
+      }
+      const uint32_t exj = inc - cj;
+      uint32_t nz = __ballot_sync(0xffffffffu, wj != 0u);
+      while (nz) {
+        const int j = __ffs(nz) - 1;
+        nz &= nz - 1;
+        const uint32_t bj = __shfl_sync(0xffffffffu, wj, j);
+        const uint32_t ej = __shfl_sync(0xffffffffu, exj, j);
+        const uint32_t rank = tb + ej + __popc(bj & lanemask_lt());
+        if (((bj >> lane) & 1u) && rank >= r0 && rank < r1)
+          s_list[rank - r0] = (uint16_t)(T * kCkTileRows + 32 * j + lane);
+      }
+    }
+    if (r0 == 0) prefix = resolve();
+    __syncthreads();  // this round's list is complete
+    const uint32_t m = total - r0 < (uint32_t)kCkList ? total - r0 : (uint32_t)kCkList;
+    if (a.nout <= 2) ck_write<2, 4>(a, cbase, prefix + r0, m, s_list);
+    else if (a.nout <= 4) ck_write<4, 2>(a, cbase, prefix + r0, m, s_list);
+    else ck_write<kMaxCols, 1>(a, cbase, prefix + r0, m, s_list);
+  }
+  return prefix;
+}
+
 template <int K>
 __global__ void __launch_bounds__(kCkThreads, K > 0 ? kCkMinBlocks : 4) k_sieve_chunk(SieveArgs a) {
   constexpr int kMaxTiles = kCkMaxRows / kCkTileRows;
@@ -651,6 +707,7 @@ __global__ void __launch_bounds__(kCkThreads, K > 0 ? kCkMinBlocks : 4) k_sieve_
         d[0] = make_uint4(b[0], b[1], b[2], b[3]);
         d[1] = make_uint4(b[4], b[5], b[6], b[7]);
       }
+
 #pragma unroll
       for (int j = 0; j < 8; ++j) cur[j] = nxt[j];
     }
@@ -681,133 +738,71 @@ __global__ void __launch_bounds__(kCkThreads, K > 0 ? kCkMinBlocks : 4) k_sieve_
   }
   __syncthreads();
 
-  // 3. survivors of ranks [0, kCkList) listed, then 4. look-back, 5. write;
-  // denser chunks take more rounds of kCkList ranks
-  uint64_t prefix = 0;
-  for (uint32_t r0 = 0; r0 == 0 || r0 < total; r0 += kCkList) {
-    const uint32_t r1 = r0 + kCkList;
-    if (r0 > 0) __syncthreads();  // the previous round's list is consumed
-    for (int T = warp; T < ntile; T += kCkThreads / 32) {
-      const uint32_t tb = s_toff[T];
-      if (tb >= r1 || s_toff[T + 1] <= r0) continue;  // no rank of this round (warp-uniform)
-      const uint32_t wj = lane < 8 ? s_bits[T * 8 + lane] : 0u;
-      const uint32_t cj = __popc(wj);
-      uint32_t inc = cj;
-#pragma unroll
-      for (int d = 1; d < 8; d <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, d);
-        if (lane >= d) inc += y;
-      }
-      const uint32_t exj = inc - cj;
-      uint32_t nz = __ballot_sync(0xffffffffu, wj != 0u);
-      while (nz) {
-        const int j = __ffs(nz) - 1;
-        nz &= nz - 1;
-        const uint32_t bj = __shfl_sync(0xffffffffu, wj, j);
-        const uint32_t ej = __shfl_sync(0xffffffffu, exj, j);
-        const uint32_t rank = tb + ej + __popc(bj & lanemask_lt());
-        if (((bj >> lane) & 1u) && rank >= r0 && rank < r1)
-          s_list[rank - r0] = (uint16_t)(T * kCkTileRows + 32 * j + lane);
+  // 3.-5. survivors listed, look-back, writes
+  const uint64_t prefix = ck_list_and_write(a, cbase, ntile, total, s_bits, s_toff, s_list, [&]() {
+    uint64_t p = 0;
+    if (t > 0) {
+      p = ck_lookback(a.lb, t, &s_stop, s_red);
+      if (tid == 0) {
+        Vec<1> inc;
+        inc.v[0] = p + total;
+        lb_publish<1>(a.lb, t, 2u, inc);
       }
     }
-    if (r0 == 0) {
-      if (t > 0) {
-        prefix = ck_lookback(a.lb, t, &s_stop, s_red);
-        if (tid == 0) {
-          Vec<1> inc;
-          inc.v[0] = prefix + total;
-          lb_publish<1>(a.lb, t, 2u, inc);
-        }
-      }
-      if ((int64_t)t == nchunks - 1 && tid == 0) {
-        *a.out_n = prefix + total;
-        if (a.out_n2) *a.out_n2 = prefix + total;
-      }
+    if ((int64_t)t == nchunks - 1 && tid == 0) {
+      *a.out_n = p + total;
+      if (a.out_n2) *a.out_n2 = p + total;
     }
-    __syncthreads();  // this round's list is complete
-    const uint32_t m = total - r0 < (uint32_t)kCkList ? total - r0 : (uint32_t)kCkList;
-    if (a.nout <= 2) ck_write<2, 4>(a, cbase, prefix + r0, m, s_list);
-    else if (a.nout <= 4) ck_write<4, 2>(a, cbase, prefix + r0, m, s_list);
-    else ck_write<kMaxCols, 1>(a, cbase, prefix + r0, m, s_list);
-  }
+    return p;
+  });
 
   // 6. clear the next filters' words
   ck_zero(a, prefix, prefix + total, t == 0);
 }
 
-// ---------------------------------------------------------------- scan
-// CTAs loop over tiles in ticket order (a grid of a few CTAs per SM serves any
-// n, including a count known on the device only).
-__global__ void __launch_bounds__(kBlock) k_scan_u32(ScanArgs a) {
-  __shared__ uint32_t s_tile;
+// ---------------------------------------------------------------- group offsets
+__global__ void __launch_bounds__(kBlock) k_group_offsets(GroupOffArgs a) {
   __shared__ Vec<2> s_warp[kBlock / 32];
-  __shared__ uint64_t s_prefix;
+  __shared__ unsigned long long s_base;
   const int tid = threadIdx.x;
-  const int64_t n = a.n_dev ? (int64_t)(*a.n_dev) : a.n_host;
-  const int64_t ntiles = (n + kScanTile - 1) / kScanTile;
-  for (;;) {
-  if (tid == 0) s_tile = draw_ticket_loop(a.tile_counter, (uint64_t)ntiles);
-  __syncthreads();
-  const uint32_t tile = s_tile;
-  if ((int64_t)tile >= ntiles) {
-    if (tile == 0 && tid == 0 && a.total) *a.total = 0;
-    break;
-  }
-  const int64_t base = (int64_t)tile * kScanTile;
-  uint32_t x[8];
+  const int64_t n = a.n_dev ? (int64_t)__ldg(a.n_dev) : a.n_host;
+  const int64_t ntiles = (n + kGroupTile - 1) / kGroupTile;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t base = tile * kGroupTile;
+    uint32_t x[8];
 #pragma unroll
-  for (int v = 0; v < 2; ++v) {
-    const int64_t r0 = base + (int64_t)(v * kBlock + tid) * 4;
-    if (r0 + 4 <= n) {
-      const uint4 q = __ldg(reinterpret_cast<const uint4*>(a.in + r0));
-      x[4 * v] = q.x;
-      x[4 * v + 1] = q.y;
-      x[4 * v + 2] = q.z;
-      x[4 * v + 3] = q.w;
-    } else {
+    for (int v = 0; v < 2; ++v) {
+      const int64_t r0 = base + (int64_t)(v * kBlock + tid) * 4;
+      if (r0 + 4 <= n) {
+        const uint4 q = __ldg(reinterpret_cast<const uint4*>(a.cnt + r0));
+        x[4 * v] = q.x;
+        x[4 * v + 1] = q.y;
+        x[4 * v + 2] = q.z;
+        x[4 * v + 3] = q.w;
+      } else {
 #pragma unroll
-      for (int e = 0; e < 4; ++e) x[4 * v + e] = (r0 + e < n) ? __ldg(a.in + r0 + e) : 0u;
-    }
-  }
-  Vec<2> s;
-  s.v[0] = (uint64_t)x[0] + x[1] + x[2] + x[3];
-  s.v[1] = (uint64_t)x[4] + x[5] + x[6] + x[7];
-  Vec<2> tot;
-  const Vec<2> ex = block_exclusive_scan<2>(s, &tot, s_warp);
-  const uint64_t tile_total = tot.v[0] + tot.v[1];
-  if (tid < 32) {
-    Vec<1> aggv;
-    aggv.v[0] = tile_total;
-    if (tile == 0) {
-      if (tid == 0) {
-        lb_publish<1>(a.lb, 0, 2, aggv);
-        s_prefix = 0;
-      }
-    } else {
-      if (tid == 0) lb_publish<1>(a.lb, tile, 1, aggv);
-      const Vec<1> e = lb_exclusive<1>(a.lb, tile);
-      if (tid == 0) {
-        Vec<1> incv;
-        incv.v[0] = e.v[0] + tile_total;
-        lb_publish<1>(a.lb, tile, 2, incv);
-        s_prefix = e.v[0];
+        for (int e = 0; e < 4; ++e) x[4 * v + e] = (r0 + e < n) ? __ldg(a.cnt + r0 + e) : 0u;
       }
     }
-  }
-  __syncthreads();
-  const uint64_t prefix = s_prefix;
-  if ((int64_t)tile == ntiles - 1 && tid == 0 && a.total) *a.total = prefix + tile_total;
+    Vec<2> sv, tot;
+    sv.v[0] = (uint64_t)x[0] + x[1] + x[2] + x[3];
+    sv.v[1] = (uint64_t)x[4] + x[5] + x[6] + x[7];
+    const Vec<2> ex = block_exclusive_scan<2>(sv, &tot, s_warp);
+    if (tid == 0) s_base = atomicAdd(a.cursor, (unsigned long long)(tot.v[0] + tot.v[1]));
+    __syncthreads();
+    const uint64_t gb = s_base;
 #pragma unroll
-  for (int v = 0; v < 2; ++v) {
-    uint64_t run = prefix + (v ? tot.v[0] : 0) + ex.v[v];
-    const int64_t r0 = base + (int64_t)(v * kBlock + tid) * 4;
+    for (int v = 0; v < 2; ++v) {
+      uint64_t run = gb + (v ? tot.v[0] : 0) + ex.v[v];
+      const int64_t r0 = base + (int64_t)(v * kBlock + tid) * 4;
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      if (r0 + e < n) a.out[r0 + e] = run;
-      run += x[4 * v + e];
+      for (int e = 0; e < 4; ++e) {
+        if (r0 + e < n) a.off[r0 + e] = run;
+        run += x[4 * v + e];
+      }
     }
+    __syncthreads();  // s_base is rewritten by the next tile
   }
-  }  // tile loop (the scan's barriers order s_tile / s_prefix reuse)
 }
 
 // ---------------------------------------------------------------- hash tables
@@ -837,9 +832,9 @@ __device__ __forceinline__ int64_t table_find_or_insert(const Table& t, int32_t 
   return -1;
 }
 
-// Read-only lookup after the build finished: slot index of `key`, or -1.
-__device__ __forceinline__ int64_t table_find(const Table& t, int32_t key) {
-  uint32_t b = table_bucket(key, t.bucket_mask);
+// Read-only lookup after the build finished, starting at bucket b: slot index
+// of `key`, or -1.
+__device__ __forceinline__ int64_t table_find_at(const Table& t, int32_t key, uint32_t b) {
   const uint64_t lo = (uint32_t)key;
   for (uint32_t step = 0; step <= t.bucket_mask; ++step) {
     const ulonglong2* p = reinterpret_cast<const ulonglong2*>(t.slots + (uint64_t)b * 4);
@@ -855,6 +850,9 @@ __device__ __forceinline__ int64_t table_find(const Table& t, int32_t key) {
   }
   return -1;
 }
+__device__ __forceinline__ int64_t table_find(const Table& t, int32_t key) {
+  return table_find_at(t, key, table_bucket(key, t.bucket_mask));
+}
 
 // Slot of `key` when it sits in one of the first two slots of its home
 // bucket (the common case at load <= 1/2), -1 when that half-bucket shows it
@@ -866,7 +864,7 @@ __device__ __forceinline__ int64_t table_find_first(const Table& t, int32_t key,
   if ((q.x & 0xffffffffull) == lo) return (int64_t)b * 4;
   if (q.y == 0) return -1;
   if ((q.y & 0xffffffffull) == lo) return (int64_t)b * 4 + 1;
-  return table_find(t, key);
+  return table_find_at(t, key, b);
 }
 
 // Per-CTA aggregation of skewed keys: a CTA takes kAggRows rows per round and
@@ -1136,6 +1134,7 @@ __global__ void __launch_bounds__(kBlock) k_table_init(TableInitArgs a) {
   if (gid == 0) {
     *a.mask_out = (uint32_t)(nslots / 4 - 1);
     if (a.nslots_out) *a.nslots_out = (uint32_t)nslots;
+    if (a.zero64) *a.zero64 = 0ull;
   }
   for (int64_t i = gid; i < (int64_t)nslots; i += stride) {
     a.slots[i] = 0ull;
@@ -1495,11 +1494,42 @@ int host_grid(int64_t work, int per_block, int cap) {
   return (int)g;
 }
 
+// Launch at the device's highest stream priority (cudaLaunchAttributePriority;
+// inside a stream capture it becomes the kernel node's priority).  The
+// pruning phase's kernels use it so that the CTA scheduler gives them SMs
+// ahead of table builds running on another stream.
+int critical_priority() {
+  static int prio = [] {
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    return greatest;
+  }();
+  return prio;
+}
+
+template <typename... KArgs, typename... Args>
+void launch_hi(void (*kernel)(KArgs...), unsigned grid, unsigned block, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributePriority;
+  attr[0].val.priority = critical_priority();
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- launchers
 void launch_bloom_build(const BloomBuildArgs& a, int64_t n_upper, int num_sms, cudaStream_t s) {
-  k_bloom_build<<<host_grid(n_upper, kBlock * kBuildKeys, num_sms * 3), kBlock, 0, s>>>(a);
+  launch_hi(k_bloom_build, (unsigned)host_grid(n_upper, kBlock * kBuildKeys, num_sms * 3), kBlock, s, a);
 }
 
 void launch_bloom_probe(const BloomProbeArgs& a, int num_sms, cudaStream_t s) {
@@ -1507,9 +1537,9 @@ void launch_bloom_probe(const BloomProbeArgs& a, int num_sms, cudaStream_t s) {
 }
 
 int sieve_chunk_rows(int64_t n_upper, int num_sms) {
-  // one chunk per CTA slot of the GPU (kCkMinBlocks per SM), so that one wave
-  // splits the rows evenly; whole warp tiles, at least one tile per warp
-  const int64_t slots = (int64_t)(num_sms > 0 ? num_sms : 1) * kCkMinBlocks;
+  // one chunk per CTA slot of the GPU (kCkWaveBlocks per SM), so that one
+  // wave splits the rows evenly; whole warp tiles, at least one tile per warp
+  const int64_t slots = (int64_t)(num_sms > 0 ? num_sms : 1) * kCkWaveBlocks;
   int64_t c = (n_upper + slots - 1) / slots;
   c = (c + kCkTileRows - 1) / kCkTileRows * kCkTileRows;
   if (c < kCkChunkQuantum) c = kCkChunkQuantum;
@@ -1524,19 +1554,19 @@ void launch_sieve_chunk(const SieveArgs& a, int64_t n_upper, int num_sms, cudaSt
   const bool fast = a.ntest == 1 && !a.test[0].is_pred && a.test[0].f.layout == 0 &&
                     a.test[0].f.k >= 1 && a.test[0].f.k <= 4 && a.fast_words_ok;
   if (!fast) {
-    k_sieve_chunk<0><<<(unsigned)g, kCkThreads, 0, s>>>(a);
+    launch_hi(k_sieve_chunk<0>, (unsigned)g, kCkThreads, s, a);
     return;
   }
   switch (a.test[0].f.k) {
-    case 1: k_sieve_chunk<1><<<(unsigned)g, kCkThreads, 0, s>>>(a); break;
-    case 2: k_sieve_chunk<2><<<(unsigned)g, kCkThreads, 0, s>>>(a); break;
-    case 3: k_sieve_chunk<3><<<(unsigned)g, kCkThreads, 0, s>>>(a); break;
-    default: k_sieve_chunk<4><<<(unsigned)g, kCkThreads, 0, s>>>(a); break;
+    case 1: launch_hi(k_sieve_chunk<1>, (unsigned)g, kCkThreads, s, a); break;
+    case 2: launch_hi(k_sieve_chunk<2>, (unsigned)g, kCkThreads, s, a); break;
+    case 3: launch_hi(k_sieve_chunk<3>, (unsigned)g, kCkThreads, s, a); break;
+    default: launch_hi(k_sieve_chunk<4>, (unsigned)g, kCkThreads, s, a); break;
   }
 }
 
-void launch_scan_u32(const ScanArgs& a, int64_t n_upper, int num_sms, cudaStream_t s) {
-  k_scan_u32<<<host_grid(n_upper, kScanTile, 4 * num_sms), kBlock, 0, s>>>(a);
+void launch_group_offsets(const GroupOffArgs& a, int64_t n_upper, int num_sms, cudaStream_t s) {
+  k_group_offsets<<<host_grid(n_upper, kGroupTile, 4 * num_sms), kBlock, 0, s>>>(a);
 }
 
 void launch_mm_insert(const MMInsertArgs& a, int num_sms, cudaStream_t s) {

@@ -71,30 +71,37 @@ struct SieveArgs {
 // shared memory), lists its survivors in shared memory, gets its output offset
 // from a decoupled look-back over the chunks before it (read 1024 at a time by
 // the whole CTA) and writes its survivors.  Scratch: one ticket counter and
-// one look-back word per chunk (a.tile_counter, a.lb).
+// one look-back word per chunk (a.tile_counter, a.lb).  One wave of CTAs
+// covers the input (chunks of up to kCkMaxRows rows; larger inputs take
+// several waves), so a launch runs fastest when it has the GPU to itself.
 constexpr int kCkThreads = 256;
 constexpr int kCkTileRows = 256;                 // warp tile: 8 rows per lane, row = 32 j + lane
 constexpr int kCkChunkQuantum = kCkTileRows * (kCkThreads / 32);
 constexpr int kCkMaxRows = 16384;                // rows per chunk (row offsets fit 16 bits)
 constexpr int kCkMinBlocks = 5;                  // resident CTAs per SM (48 registers, no spills)
+constexpr int kCkWaveBlocks = kCkMinBlocks;      // CTAs per SM one launch's chunks are sized for
 constexpr int kCkList = 2048;                    // survivors listed per round (2 bytes each)
 constexpr int kCkWindow = 4 * kCkThreads;        // chunk states read per look-back round
 // Rows per chunk for a launch over at most n_upper rows.
 int sieve_chunk_rows(int64_t n_upper, int num_sms);
 void launch_sieve_chunk(const SieveArgs& a, int64_t n_upper, int num_sms, cudaStream_t s);
 
-// ------------------------------------------------------------------ scans
-struct ScanArgs {
-  const uint32_t* in;
-  uint64_t* out;          // exclusive prefix, uint64
-  int64_t n_host;
-  const uint32_t* n_dev;  // device count (uint32), or null
-  uint64_t* total;        // optional
-  uint32_t* tile_counter;
-  LookBack<1> lb;
+
+
+// ------------------------------------------------------------------ group offsets
+// Start of every table slot's row group in a multimap (CSR by slot).  Groups
+// only need disjoint ranges, not slot order, so each tile of slots takes its
+// range from one atomicAdd on a cursor (zeroed before the launch) and scans
+// its own counts: one pass, no tile waits for another.
+struct GroupOffArgs {
+  const uint32_t* cnt;    // rows per slot
+  uint64_t* off;          // group start per slot (written)
+  int64_t n_host;         // slots, when n_dev is null
+  const uint32_t* n_dev;  // device slot count, or null
+  unsigned long long* cursor;
 };
-constexpr int kScanTile = kBlock * 8;
-void launch_scan_u32(const ScanArgs& a, int64_t n_upper, int num_sms, cudaStream_t s);
+constexpr int kGroupTile = kBlock * 8;
+void launch_group_offsets(const GroupOffArgs& a, int64_t n_upper, int num_sms, cudaStream_t s);
 
 // ------------------------------------------------------------------ hash tables
 // Open addressing, linear probing over buckets of four 8-byte slots (one
@@ -107,7 +114,7 @@ struct Table {
 
 // Device-side sizing of a table (k_table_init): nslots = power of two >= max(64, 2n)
 // for the n read from n_dev, mask written to *mask_out, slots (and the
-// optional per-slot arrays) zeroed up to nslots, cnt zeroed up to n, *zero32 = 0.
+// optional per-slot arrays) zeroed up to nslots, *zero64 = 0.
 struct TableInitArgs {
   unsigned long long* slots;
   uint32_t* mask_out;
@@ -116,6 +123,7 @@ struct TableInitArgs {
   ulonglong2* pairs;              // optional, nslots entries
   uint32_t* cnt;                  // optional, nslots entries to clear
   uint32_t* nslots_out;           // optional: receives nslots
+  unsigned long long* zero64 = nullptr;  // optional word cleared (a group-offset cursor)
 };
 void launch_table_init(const TableInitArgs& a, int64_t cap_slots, int num_sms, cudaStream_t s);
 
