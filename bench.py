@@ -566,21 +566,41 @@ def cyclic_run(torch, sj, ctx, stream):
 
 
 # ----------------------------------------------------------------------------- CPU oracle
-def cpu_oracle_run(spec, reps_seconds=10.0, max_reps=20):
-    """Time the CPU oracle (plain hash join) on the bounded sample."""
+def cpu_oracle_run(spec, w_full, gpu_res, reps_seconds=10.0, max_reps=20):
+    """The CPU oracle (plain binary hash join; serial build, probe split over
+    threads) timed on the bounded sample at 1 thread and at os.cpu_count()
+    threads; and the GPU's timed result checked against the oracle's aggregate
+    propagation over the full workload."""
     import oracle
     oracle.build_lib()
     w = spec["sample"]()
     tuples = sum(len(r[0]) for r in w["rels"])
-    t_tot, reps = 0.0, 0
-    while reps < max_reps and (reps == 0 or t_tot < reps_seconds):
-        t0 = time.perf_counter()
-        oracle.hash_join(w)
-        t_tot += time.perf_counter() - t0
-        reps += 1
-    return {"value": tuples * reps / t_tot, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{spec['sample_desc']}; {reps} run(s) of the oracle's plain binary hash join "
-                      f"({tuples} input tuples each), single thread, {t_tot:.1f} s total"}
+    nproc = os.cpu_count() or 1
+
+    def timed_at(threads):
+        oracle.set_threads(threads)
+        t_tot, reps = 0.0, 0
+        while reps < max_reps and (reps == 0 or t_tot < reps_seconds):
+            t0 = time.perf_counter()
+            oracle.hash_join(w)
+            t_tot += time.perf_counter() - t0
+            reps += 1
+        return tuples * reps / t_tot, reps, t_tot
+
+    v1, r1, s1 = timed_at(1)
+    vn, rn, sn = timed_at(nproc)
+    oracle.set_threads(nproc)
+    exp = oracle.agg_propagation(w_full)
+    oracle.set_threads(1)
+    check = {"oracle_count": exp["count"], "oracle_sum": exp["sum"],
+             "equal": (exp["count"], exp["sum"]) == (gpu_res["count"], gpu_res["sum"])}
+    assert check["equal"], ("GPU result differs from the oracle", check, gpu_res)
+    return {"value": vn, "unit": UNIT, "cores": nproc, "kind": "oracle",
+            "sample": f"{spec['sample_desc']}; the oracle's plain binary hash join ({tuples} input "
+                      f"tuples per run), probe split over {nproc} threads: {rn} run(s) in {sn:.1f} s",
+            "single_thread": {"value": v1, "unit": UNIT, "cores": 1,
+                              "sample": f"same sample, 1 thread: {r1} run(s) in {s1:.1f} s"},
+            "full_workload_check": check}
 
 
 REF_BUDGET_S = 90.0
@@ -592,6 +612,8 @@ def run_reference(args, ws, rank):
     spec = WORKLOADS[args.workload]
     import oracle
     oracle.build_lib()
+    nproc = os.cpu_count() or 1
+    oracle.set_threads(nproc)  # the probe of each join level split over the host's cores
     w = spec["sample"]()
     sample_desc = spec["sample_desc"]
     # keep the whole run within about REF_BUDGET_S: with many steps, each step
@@ -627,8 +649,8 @@ def run_reference(args, ws, rank):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic",
             "config": {"workload": args.workload, "desc": spec["desc"], "sample": sample_desc},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": sample_desc},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": nproc, "kind": "oracle",
+                             "sample": sample_desc + f"; probe split over {nproc} threads"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -708,16 +730,39 @@ def main():
     ms_per_step = total_ms / args.steps
     value = tuples * ws / (ms_per_step / 1000.0)
 
-    # ---- plain GPU hash join (no sieve), same workload
+    # ---- plain GPU hash join (no sieve), same workload: through sj_join
+    # (synchronises per level) and through the same one-call path as the
+    # sieved step (sj_sieve_join with the sieve off: device-sized, CUDA graph)
     plain = None
     if not args.no_plain:
         psteps = max(2, min(args.steps, 5))
         pms, (pres, _) = timed(torch, stream, lambda: plain_step(ctx, rels, w), psteps, 1, flush, ws)
         pms = max_over_ranks(pms, ws) / psteps
         assert (pres["count"], pres["sum"]) == (res["count"], res["sum"])
-        plain = {"value": tuples * ws / (pms / 1000.0), "unit": UNIT, "ms_per_step": pms,
+        nos = dict(TUNED, passes=sj.NO_SIEVE)
+        one = lambda: ctx.sieve_join(rels, w["edges"], w["preds"], w["root"], refs=w["sum"], **nos)
+        qsteps = max(3, min(args.steps, 10))
+        qms, qres = timed(torch, stream, one, qsteps, 4, flush, ws)
+        qms = max_over_ranks(qms, ws) / qsteps
+        assert (qres["count"], qres["sum"]) == (res["count"], res["sum"])
+        plain = {"value": tuples * ws / (qms / 1000.0), "unit": UNIT, "ms_per_step": qms,
+                 "path": "sj_sieve_join(passes=NO_SIEVE): the sieved step's own path (device-sized "
+                         "sizes, CUDA-graph replay), sieve off",
                  "intermediate_tuples": pres["intermediate"],
-                 "sieved_speedup": pms / ms_per_step}
+                 "sieved_speedup": qms / ms_per_step,
+                 "sj_join": {"ms_per_step": pms, "value": tuples * ws / (pms / 1000.0),
+                             "path": "sj_join over the unsieved relations (one sync per level)",
+                             "sieved_speedup": pms / ms_per_step}}
+    # ---- the forward-then-backward schedule with the same filter parameters
+    fwd_bwd = None
+    if TUNED.get("passes", sj.FWD_BWD) != sj.FWD_BWD:
+        fb = dict(TUNED, passes=sj.FWD_BWD)
+        fone = lambda: ctx.sieve_join(rels, w["edges"], w["preds"], w["root"], refs=w["sum"], **fb)
+        fsteps = max(3, min(args.steps, 20))
+        fms, fres = timed(torch, stream, fone, fsteps, 4, flush, ws)
+        assert (fres["count"], fres["sum"]) == (res["count"], res["sum"])
+        fms = max_over_ranks(fms, ws) / fsteps
+        fwd_bwd = {"filter_params": fb, "ms_per_step": fms, "value": tuples * ws / (fms / 1000.0)}
 
     # ---- end to end through the C ABI with host buffers
     e2e = None
@@ -751,7 +796,7 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu:
-        cpu = cpu_oracle_run(spec)
+        cpu = cpu_oracle_run(spec, w, res)
 
     if rank != 0:
         return
@@ -780,6 +825,7 @@ def main():
         "gpu_launches_per_step": counters["launches"] / args.steps,
         "e2e": e2e,
         "plain_gpu_hash_join": plain,
+        "fwd_bwd_same_params": fwd_bwd,
         "roofline": {"bound": "hbm", "kernel": "k_sieve", "achieved": achieved, "peak": peak,
                      "frac_of_nominal_7700": achieved / 7700.0,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,

@@ -55,7 +55,7 @@ def build_lib(force: bool = False) -> str:
     if force or not os.path.exists(_LIB_PATH) or \
             os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC_PATH):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC",
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread",
                                "-o", tmp, _SRC_PATH])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -74,11 +74,24 @@ def _load():
         lib.orc_join_pairs_fill.argtypes = [P, i64, P, i64, P, P]
         lib.orc_join_agg.restype = ctypes.c_int
         lib.orc_join_agg.argtypes = [P, i64, P, P, i64, P, P]
+        lib.orc_set_threads.restype = None
+        lib.orc_set_threads.argtypes = [ctypes.c_int]
+        lib.orc_get_threads.restype = ctypes.c_int
         lib.orc_nested_loop.restype = ctypes.c_int
         lib.orc_nested_loop.argtypes = [ctypes.c_int, P, P, P, ctypes.c_int, P, P,
                                         ctypes.c_int, P, P]
         _lib = lib
     return _lib
+
+
+def set_threads(n: int) -> None:
+    """Probe threads of the C join levels (1 = serial; the build stays
+    serial).  Results do not depend on it."""
+    _load().orc_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return int(_load().orc_get_threads())
 
 
 def _ptr(a: np.ndarray):
@@ -519,12 +532,26 @@ def triangle_counts(src, dst, cuts):
         raise MemoryError("oracle join")
     a = src[pi].astype(np.int64)
     c = dst[pj].astype(np.int64)
-    edges = np.sort((src.astype(np.int64) << 32) | dst.astype(np.int64))
-    probe = (c << 32) | a
+    edges = np.sort(_pair_key(src, dst))
+    probe = _pair_key(c, a)
     pos = np.minimum(np.searchsorted(edges, probe), max(len(edges) - 1, 0))
     closes = edges[pos] == probe if len(edges) else np.zeros(len(probe), dtype=bool)
-    sub = np.searchsorted(np.asarray(cuts, dtype=np.int64), a[closes], side="right") - 1
-    return np.bincount(sub, minlength=len(cuts) - 1).astype(np.int64)
+    return np.bincount(_subquery(cuts, a[closes]), minlength=len(cuts) - 1).astype(np.int64)
+
+
+def _pair_key(s, d):
+    """One int64 per vertex pair (s, d), distinct for distinct pairs of int32
+    ids: s in the high word, d's 32-bit pattern in the low word."""
+    s = np.asarray(s, dtype=np.int64)
+    d = np.asarray(d, dtype=np.int64)
+    return (s << 32) | (d & 0xFFFFFFFF)
+
+
+def _subquery(cuts, a):
+    """Subquery of each vertex a: the i with cuts[i] <= a < cuts[i+1]; a below
+    cuts[0] belongs to subquery 0 and a at or above cuts[-1] to the last."""
+    sub = np.searchsorted(np.asarray(cuts, dtype=np.int64), a, side="right") - 1
+    return np.clip(sub, 0, len(cuts) - 2)
 
 
 def triangle_counts_for(src, dst, verts):
@@ -534,7 +561,7 @@ def triangle_counts_for(src, dst, verts):
     search in the sorted edge keys)."""
     src = np.asarray(src, dtype=np.int64)
     dst = np.asarray(dst, dtype=np.int64)
-    edges = np.sort((src << 32) | dst)
+    edges = np.sort(_pair_key(src, dst))
     order = np.argsort(src, kind="stable")
     s_sorted = src[order]
 
@@ -550,6 +577,6 @@ def triangle_counts_for(src, dst, verts):
         for b in bs:
             l2, h2 = np.searchsorted(s_sorted, [b, b + 1])
             cs = dst[order[l2:h2]]
-            total += int(is_edge((cs << 32) | a).sum())
+            total += int(is_edge(_pair_key(cs, a)).sum())
         out.append(total)
     return np.array(out, dtype=np.int64)

@@ -12,18 +12,51 @@
  * those of the unpruned natural join.  This file holds
  *
  *   - a chained-bucket binary hash join level (pairs of matching rows, and the
- *     aggregate form used at the last level), and
+ *     aggregate form used at the last level), whose probe can be split over
+ *     threads (orc_set_threads) with the same results, and
  *   - a nested-loop enumeration of a whole tree-shaped join (the brute force
  *     used on tiny inputs).
  *
  * COUNT is kept in 128 bits so overflow of 2^63 can be reported; SUM is the
  * int64 sum taken modulo 2^64 (two's complement wrap), which is order-free.
  */
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 
 typedef unsigned __int128 u128;
+
+/* Probe threads of the join levels (the build stays serial).  The probe rows
+ * are split into equal contiguous slices, one per thread, and the slices'
+ * results are put together in slice order, so every result is the same for
+ * any thread count. */
+static int g_threads = 1;
+void orc_set_threads(int t) { g_threads = t < 1 ? 1 : (t > 256 ? 256 : t); }
+int orc_get_threads(void) { return g_threads; }
+
+typedef void (*slice_fn)(void *arg, int64_t lo, int64_t hi, int slice);
+typedef struct { slice_fn fn; void *arg; int64_t lo, hi; int slice; } slice_job;
+static void *slice_run(void *p) {
+    slice_job *j = (slice_job *)p;
+    j->fn(j->arg, j->lo, j->hi, j->slice);
+    return NULL;
+}
+/* Run fn over [0, n) in `nt` slices; slice s covers [n s / nt, n (s+1) / nt). */
+static void run_slices(slice_fn fn, void *arg, int64_t n, int nt) {
+    if (nt <= 1) { fn(arg, 0, n, 0); return; }
+    pthread_t th[256];
+    slice_job jobs[256];
+    int started[256];
+    for (int s = 0; s < nt; ++s) {
+        jobs[s].fn = fn; jobs[s].arg = arg; jobs[s].slice = s;
+        jobs[s].lo = n * s / nt; jobs[s].hi = n * (s + 1) / nt;
+        started[s] = pthread_create(&th[s], NULL, slice_run, &jobs[s]) == 0;
+        if (!started[s]) slice_run(&jobs[s]);
+    }
+    for (int s = 0; s < nt; ++s)
+        if (started[s]) pthread_join(th[s], NULL);
+}
 
 /* ---------------- chained hash table over an int32 key column ------------- */
 
@@ -57,14 +90,62 @@ static int chain_build(chain_table *t, const int32_t *keys, int64_t n) {
 
 static void chain_free(chain_table *t) { free(t->head); free(t->next); }
 
+/* Number of (probe row, build row) pairs with equal keys in probe rows
+ * [lo, hi). */
+static int64_t count_range(const chain_table *t, const int32_t *pk, const int32_t *bk,
+                           int64_t lo, int64_t hi) {
+    int64_t total = 0;
+    for (int64_t i = lo; i < hi; ++i)
+        for (int64_t r = t->head[bucket_of(pk[i], t->mask)]; r >= 0; r = t->next[r])
+            if (bk[r] == pk[i]) ++total;
+    return total;
+}
+
+typedef struct {
+    const chain_table *t;
+    const int32_t *pk, *bk;
+    const uint64_t *psum, *bval;
+    int64_t *cnt;                 /* per slice */
+    int64_t *out_probe, *out_build;
+    const int64_t *off;           /* per slice: first output position */
+    u128 *acnt;                   /* per slice */
+    uint64_t *asum;               /* per slice */
+} probe_job;
+
+static void count_slice(void *p, int64_t lo, int64_t hi, int s) {
+    probe_job *j = (probe_job *)p;
+    j->cnt[s] = count_range(j->t, j->pk, j->bk, lo, hi);
+}
+static void fill_slice(void *p, int64_t lo, int64_t hi, int s) {
+    probe_job *j = (probe_job *)p;
+    int64_t o = j->off[s];
+    for (int64_t i = lo; i < hi; ++i)
+        for (int64_t r = j->t->head[bucket_of(j->pk[i], j->t->mask)]; r >= 0; r = j->t->next[r])
+            if (j->bk[r] == j->pk[i]) { j->out_probe[o] = i; j->out_build[o] = r; ++o; }
+}
+static void agg_slice(void *p, int64_t lo, int64_t hi, int s) {
+    probe_job *j = (probe_job *)p;
+    u128 count = 0;
+    uint64_t sum = 0;
+    for (int64_t i = lo; i < hi; ++i)
+        for (int64_t r = j->t->head[bucket_of(j->pk[i], j->t->mask)]; r >= 0; r = j->t->next[r])
+            if (j->bk[r] == j->pk[i]) {
+                count += 1;
+                sum += (j->psum ? j->psum[i] : 0) + (j->bval ? j->bval[r] : 0);
+            }
+    j->acnt[s] = count;
+    j->asum[s] = sum;
+}
+
 /* Number of (probe row, build row) pairs with equal keys; -1 if out of memory. */
 int64_t orc_join_pairs_count(const int32_t *pk, int64_t np, const int32_t *bk, int64_t nb) {
     chain_table t;
     if (chain_build(&t, bk, nb)) return -1;
+    int64_t cnt[256];
+    probe_job j = {&t, pk, bk, NULL, NULL, cnt, NULL, NULL, NULL, NULL, NULL};
+    run_slices(count_slice, &j, np, g_threads);
     int64_t total = 0;
-    for (int64_t i = 0; i < np; ++i)
-        for (int64_t r = t.head[bucket_of(pk[i], t.mask)]; r >= 0; r = t.next[r])
-            if (bk[r] == pk[i]) ++total;
+    for (int s = 0; s < g_threads; ++s) total += cnt[s];
     chain_free(&t);
     return total;
 }
@@ -74,10 +155,12 @@ int orc_join_pairs_fill(const int32_t *pk, int64_t np, const int32_t *bk, int64_
                         int64_t *out_probe, int64_t *out_build) {
     chain_table t;
     if (chain_build(&t, bk, nb)) return -1;
+    int64_t cnt[256], off[256];
+    probe_job j = {&t, pk, bk, NULL, NULL, cnt, out_probe, out_build, off, NULL, NULL};
+    run_slices(count_slice, &j, np, g_threads);
     int64_t o = 0;
-    for (int64_t i = 0; i < np; ++i)
-        for (int64_t r = t.head[bucket_of(pk[i], t.mask)]; r >= 0; r = t.next[r])
-            if (bk[r] == pk[i]) { out_probe[o] = i; out_build[o] = r; ++o; }
+    for (int s = 0; s < g_threads; ++s) { off[s] = o; o += cnt[s]; }
+    run_slices(fill_slice, &j, np, g_threads);
     chain_free(&t);
     return 0;
 }
@@ -91,14 +174,13 @@ int orc_join_agg(const int32_t *pk, int64_t np, const uint64_t *psum,
                  const int32_t *bk, int64_t nb, const uint64_t *bval, uint64_t *out) {
     chain_table t;
     if (chain_build(&t, bk, nb)) return -1;
+    u128 acnt[256];
+    uint64_t asum[256];
+    probe_job j = {&t, pk, bk, psum, bval, NULL, NULL, NULL, NULL, acnt, asum};
+    run_slices(agg_slice, &j, np, g_threads);
     u128 count = 0;
     uint64_t sum = 0;
-    for (int64_t i = 0; i < np; ++i)
-        for (int64_t r = t.head[bucket_of(pk[i], t.mask)]; r >= 0; r = t.next[r])
-            if (bk[r] == pk[i]) {
-                count += 1;
-                sum += (psum ? psum[i] : 0) + (bval ? bval[r] : 0);
-            }
+    for (int s = 0; s < g_threads; ++s) { count += acnt[s]; sum += asum[s]; }
     chain_free(&t);
     out[0] = (uint64_t)count;
     out[1] = (uint64_t)(count >> 64);

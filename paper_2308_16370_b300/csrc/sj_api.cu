@@ -34,6 +34,9 @@ constexpr sj_status kRetry = 100;
 // d_misc words of the device-sized join: per-level totals and output counts
 constexpr int kMiscLevelTotals = kMiscSteps + 96;  // 2 words per level, 8 levels
 constexpr int kMiscLevelCount = kMiscSteps + 112;  // 1 word per level
+// the same words as statistics slots (profiling resolves bytes from them)
+constexpr int kSlotLevelTotals = kMiscLevelTotals - kMiscSteps;
+constexpr int kSlotLevelCount = kMiscLevelCount - kMiscSteps;
 
 struct ProfRec {
   int kind;
@@ -336,6 +339,13 @@ struct Launch {
     else cudaEventRecord(e, c->stream);
   }
 };
+
+// A launch whose algorithmic bytes are `per` bytes per row, the rows being the
+// device count in statistics slot `slot` (resolved once it is read back), or
+// the host-known n when slot < 0.
+inline Launch rows_launch(sj_ctx* c, int kind, double per, int slot, int64_t n_host) {
+  return slot >= 0 ? Launch(c, kind, 0.0, slot, per) : Launch(c, kind, per * (double)std::max<int64_t>(n_host, 0));
+}
 
 sj_status check_launch(sj_ctx* c, const char* what) {
   cudaError_t e = cudaGetLastError();
@@ -936,7 +946,9 @@ sj_status sj_sieve(sj_ctx* c, sj_rel rel, int nprobe, const int* key_cols, const
 
 namespace {
 // Called once per relation as soon as its last sieve step is enqueued.
-using FinalHook = std::function<sj_status(int rel, const sj_rel_s* r)>;
+// `slot` is the statistics slot of its device row count (-1: not sieved, the
+// host knows the count).
+using FinalHook = std::function<sj_status(int rel, const sj_rel_s* r, int slot)>;
 sj_status sieve_path_impl(sj_ctx* c, const sj_path* path, const sj_sieve_opts* opts, sj_rel* out_sieved,
                           sj_sieve_stats* stats, bool sync_end, const FinalHook* on_final = nullptr);
 }
@@ -1039,7 +1051,7 @@ sj_status sieve_path_impl(sj_ctx* c, const sj_path* path, const sj_sieve_opts* o
     const Op& op = ops[q];
     const int i = op.rel;
     if (op.type == kOpFinal) {
-      if (on_final) st = (*on_final)(i, rel_of(i));
+      if (on_final) st = (*on_final)(i, rel_of(i), last_slot[i]);
     } else if (op.type == kOpBuild) {
       sj_filter f = fl[op.fid];
       if (!f) {
@@ -1639,6 +1651,7 @@ namespace {
 struct AsyncInter {
   std::map<ColKey, const int32_t*> cols;
   const uint64_t* n_dev = nullptr;  // null: n_host is the row count
+  int slot = -1;                    // statistics slot of *n_dev (profiling), -1 if unknown
   int64_t n_host = 0;
   int64_t cap = 0;                  // rows allocated
   const uint64_t* psum = nullptr;
@@ -1647,9 +1660,13 @@ struct AsyncInter {
 
 // Multimap build whose row count may be known on the device only: the table
 // is allocated for `cap` rows and sized and cleared by k_table_init.
+// n_slot: statistics slot of the device row count (-1: n_host is exact).
+// Algorithmic bytes per row: at least 2 table slots of 8 + 4 bytes cleared
+// and, for the offsets, read and written (12 bytes each); 12 (key read, slot
+// and rank written); 20 (slot, rank, offset read, row written).
 sj_status build_adjacency_dev(sj_ctx* c, Temps& tmp, const int32_t* keys, const uint64_t* n_dev,
                               int64_t n_host, int64_t cap, uint32_t* mask, uint32_t* nslots_dev,
-                              Adjacency* g) {
+                              Adjacency* g, int n_slot) {
   sj_status st = SJ_OK;
   const int sms = c->num_sms;
   const int64_t capn = std::max<int64_t>(cap, 1);
@@ -1664,7 +1681,7 @@ sj_status build_adjacency_dev(sj_ctx* c, Temps& tmp, const int32_t* keys, const 
   if (st != SJ_OK) return fail(c, st, "adjacency allocation failed");
   TableInitArgs ti{slots, mask, n_dev, n_host, nullptr, cnt, nslots_dev, cursor};
   {
-    Launch L(c, SJ_K_HT_BUILD, 0.0);
+    Launch L = rows_launch(c, SJ_K_HT_BUILD, 24.0, n_slot, n_host);
     launch_table_init(ti, (int64_t)cap_slots, sms, c->stream);
   }
   SJ_TRY(check_launch(c, "k_table_init"));
@@ -1676,20 +1693,20 @@ sj_status build_adjacency_dev(sj_ctx* c, Temps& tmp, const int32_t* keys, const 
   mi.n_dev = n_dev;
   if (!n_dev) mi.n = n_host;
   {
-    Launch L(c, SJ_K_HT_BUILD, 12.0 * (double)cap);
+    Launch L = rows_launch(c, SJ_K_HT_BUILD, 12.0, n_slot, n_host);
     launch_mm_insert(mi, sms, c->stream);
   }
   SJ_TRY(check_launch(c, "k_mm_insert"));
   GroupOffArgs ga{cnt, off, 0, nslots_dev, cursor};
   {
-    Launch L(c, SJ_K_HT_BUILD, 12.0 * (double)cap);
+    Launch L = rows_launch(c, SJ_K_HT_BUILD, 24.0, n_slot, n_host);
     launch_group_offsets(ga, (int64_t)cap_slots, sms, c->stream);
   }
   SJ_TRY(check_launch(c, "k_group_offsets"));
   MMScatterArgs ms{rid, rank, off, n_dev ? cap : n_host, rows};
   ms.n_dev = n_dev;
   {
-    Launch L(c, SJ_K_HT_BUILD, 20.0 * (double)cap);
+    Launch L = rows_launch(c, SJ_K_HT_BUILD, 20.0, n_slot, n_host);
     launch_mm_scatter(ms, sms, c->stream);
   }
   SJ_TRY(check_launch(c, "k_mm_scatter"));
@@ -1747,7 +1764,7 @@ sj_status device_sized_result(sj_ctx* c, int nlev, sj_result* result, std::vecto
 sj_status join_async(sj_ctx* c, const sj_path* path, const sj_rel* in_rels, int nrefs,
                      const sj_colref* refs, const std::vector<uint64_t>& caps, sj_result* result,
                      std::vector<uint64_t>* levelT, const std::vector<Adjacency>* prebuilt,
-                     bool finish = true) {
+                     bool finish = true, const std::vector<int>* rel_slot = nullptr) {
   const int n = path->nrel;
   std::vector<const sj_rel_s*> rels(in_rels, in_rels + n);
   const std::vector<LevelPlan> plan = join_order(path);
@@ -1763,6 +1780,8 @@ sj_status join_async(sj_ctx* c, const sj_path* path, const sj_rel* in_rels, int 
   in.n_dev = rels[0]->d_n;
   in.n_host = rels[0]->nrows;
   in.cap = rel_cap(rels[0]);
+  auto slot_of = [&](int i) { return (rel_slot && rels[i]->d_n) ? (*rel_slot)[i] : -1; };
+  in.slot = slot_of(0);
   std::vector<int> joined(n, 0);
   joined[0] = 1;
   Terms none;
@@ -1783,7 +1802,7 @@ sj_status join_async(sj_ctx* c, const sj_path* path, const sj_rel* in_rels, int 
     for (int L = 0; L < nlev; ++L) {
       const sj_rel_s* B = rels[plan[L].rel];
       SJ_TRY(build_adjacency_dev(c, keep, B->cols[plan[L].rel_col], B->d_n, B->nrows, rel_cap(B),
-                                 small + 2 * L, small + 2 * L + 1, &built[L]));
+                                 small + 2 * L, small + 2 * L + 1, &built[L], slot_of(plan[L].rel)));
       SJ_CUDA(c, cudaEventRecord(c->ev_built[L], c->stream));
     }
   }
@@ -1806,8 +1825,13 @@ sj_status join_async(sj_ctx* c, const sj_path* path, const sj_rel* in_rels, int 
       if (st != SJ_OK) return fail(c, st, "aggregate table allocation failed");
       TableInitArgs ti{slots, small + 2 * L, swap ? in.n_dev : B->d_n, swap ? in.n_host : B->nrows,
                        cs, nullptr, nullptr};
+      const int bslot = swap ? in.slot : slot_of(lp.rel);
+      const int64_t bhost = swap ? in.n_host : B->nrows;
+      const int pslot = swap ? slot_of(lp.rel) : in.slot;
+      const int64_t phost = swap ? B->nrows : in.n_host;
       {
-        Launch Lk(c, SJ_K_AGG, 0.0);
+        // at least 2 slots of 8 + 16 bytes cleared per build row
+        Launch Lk = rows_launch(c, SJ_K_AGG, 48.0, bslot, bhost);
         launch_table_init(ti, (int64_t)cap_slots, c->num_sms, c->stream);
       }
       SJ_TRY(check_launch(c, "k_table_init"));
@@ -1825,7 +1849,8 @@ sj_status join_async(sj_ctx* c, const sj_path* path, const sj_rel* in_rels, int 
       ai.cs = cs;
       ai.status = status_ptr(c);
       {
-        Launch Lk(c, SJ_K_AGG, 4.0 * (double)ai.n);
+        // key and SUM terms (or the intermediate's partial sum) per build row
+        Launch Lk = rows_launch(c, SJ_K_AGG, 4.0 + 4.0 * ai.terms.n + (ai.vals ? 8.0 : 0.0), bslot, bhost);
         launch_agg_insert(ai, c->num_sms, c->stream);
       }
       SJ_TRY(check_launch(c, "k_agg_insert"));
@@ -1840,7 +1865,9 @@ sj_status join_async(sj_ctx* c, const sj_path* path, const sj_rel* in_rels, int 
       ap.result = reinterpret_cast<unsigned long long*>(c->d_misc + kMiscResult);
       ap.status = status_ptr(c);
       {
-        Launch Lk(c, SJ_K_AGG, 4.0 * (double)ap.n);
+        // key and SUM terms (or the partial sum) per probe row
+        Launch Lk = rows_launch(c, SJ_K_AGG, 4.0 + 4.0 * ap.probe_terms.n + (ap.psum_in ? 8.0 : 0.0),
+                                pslot, phost);
         launch_agg_probe(ap, c->num_sms, c->stream);
       }
       SJ_TRY(check_launch(c, "k_agg_probe"));
@@ -1867,7 +1894,10 @@ sj_status join_async(sj_ctx* c, const sj_path* path, const sj_rel* in_rels, int 
     mp.totals = totals;
     SJ_TRY(scratch_for<2>(c, (capP + kProbeTile - 1) / kProbeTile, &mp.tile_counter, &mp.lb));
     {
-      Launch Lk(c, SJ_K_HT_PROBE, 4.0 * (double)mp.n);
+      // 4 bytes per probe row (key), 16 per matching row (row, id and offset written)
+      Launch Lk = in.slot >= 0 ? Launch(c, SJ_K_HT_PROBE, 0.0, in.slot, 4.0, kSlotLevelTotals + 2 * (int)L, 16.0)
+                               : Launch(c, SJ_K_HT_PROBE, 4.0 * (double)std::max<int64_t>(in.n_host, 0),
+                                        kSlotLevelTotals + 2 * (int)L, 16.0);
       launch_mm_probe(mp, c->num_sms, c->stream);
     }
     SJ_TRY(check_launch(c, "k_mm_probe"));
@@ -1881,6 +1911,7 @@ sj_status join_async(sj_ctx* c, const sj_path* path, const sj_rel* in_rels, int 
     nx.base = false;
     nx.cap = (int64_t)C;
     nx.n_dev = c->d_misc + kMiscLevelCount + L;
+    nx.slot = kSlotLevelCount + (int)L;
     for (auto& ck : carried) nx.cols[ck] = keep.get<int32_t>(C, &st);
     uint64_t* psum_out = want_sum ? keep.get<uint64_t>(C, &st) : nullptr;
     if (st != SJ_OK) return fail(c, st, "intermediate allocation failed");
@@ -1914,7 +1945,10 @@ sj_status join_async(sj_ctx* c, const sj_path* path, const sj_rel* in_rels, int 
       ex.n_out = c->d_misc + kMiscLevelCount + L;
       ex.status = status_ptr(c);
       {
-        Launch Lk(c, SJ_K_HT_EXPAND, 0.0);
+        // per output tuple: each carried column read and written, the partial
+        // sum read and written, and the tuple's probe row, key id and offset
+        const double per = 8.0 * ex.nout + (ex.psum_out ? 16.0 : 0.0) + 12.0;
+        Launch Lk(c, SJ_K_HT_EXPAND, 0.0, kSlotLevelCount + (int)L, per);
         launch_mm_expand_dev(ex, c->num_sms, c->stream);
       }
       SJ_TRY(check_launch(c, "k_mm_expand_dev"));
@@ -1923,6 +1957,7 @@ sj_status join_async(sj_ctx* c, const sj_path* path, const sj_rel* in_rels, int 
   }
   if (!finish) return enqueue_readback(c);  // graph capture: results read at replay
   SJ_TRY(sync_read(c));
+  prof_resolve(c, 0);
   return device_sized_result(c, (int)plan.size() - 1, result, levelT);
 }
 
@@ -2254,19 +2289,21 @@ sj_status run_device_sized(sj_ctx* c, const sj_path* path, const sj_sieve_opts* 
   // each level's multimap is built on the side stream as soon as the pruning
   // phase is done with its relation, overlapping the remaining sieve steps
   // (those launch at a higher priority, see launch_sieve_chunk)
-  const FinalHook hook = [&](int i, const sj_rel_s* r) -> sj_status {
+  std::vector<int> rel_slot(path->nrel, -1);
+  const FinalHook hook = [&](int i, const sj_rel_s* r, int slot) -> sj_status {
+    rel_slot[i] = slot;
     const int L = level_of[i];
     if (L < 0) return SJ_OK;
     SJ_CUDA(c, cudaEventRecord(c->ev_ready, c->stream));
     OnSide side(c);
     SJ_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_ready, 0));
     SJ_TRY(build_adjacency_dev(c, bt, r->cols[plan[L].rel_col], r->d_n, r->nrows, rel_cap(r),
-                               smallb + 2 * L, smallb + 2 * L + 1, &built[L]));
+                               smallb + 2 * L, smallb + 2 * L + 1, &built[L], r->d_n ? slot : -1));
     SJ_CUDA(c, cudaEventRecord(c->ev_built[L], c->stream));
     return SJ_OK;
   };
   st = sieve_path_impl(c, path, opts, sieved, nullptr, false, &hook);
-  if (st == SJ_OK) st = join_async(c, path, sieved, nrefs, refs, caps, result, T, &built, finish);
+  if (st == SJ_OK) st = join_async(c, path, sieved, nrefs, refs, caps, result, T, &built, finish, &rel_slot);
   if (c->side && !c->capturing) cudaStreamSynchronize(c->side);  // before the arena is released
   return st;
 }

@@ -1349,7 +1349,9 @@ __device__ __forceinline__ uint32_t pair_bucket(uint64_t v, uint32_t mask) {
 __global__ void __launch_bounds__(kBlock) k_pairset_insert(PairSetArgs a) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
-    const unsigned long long v = pack_pair(__ldcs(a.src + i), __ldcs(a.dst + i)) + 1ull;
+    const int32_t s = __ldcs(a.src + i), d = __ldcs(a.dst + i);
+    if (s == d) continue;  // not an edge of the query (no self-loops); (-1, -1) would be the empty code
+    const unsigned long long v = pack_pair(s, d) + 1ull;
     uint32_t b = pair_bucket(v, a.t.bucket_mask);
     bool done = false;
     for (uint32_t step = 0; step <= a.t.bucket_mask && !done; ++step) {
@@ -1366,7 +1368,11 @@ __global__ void __launch_bounds__(kBlock) k_pairset_insert(PairSetArgs a) {
   }
 }
 
+// Slots hold pair + 1 and 0 marks an empty slot; the one pair whose code is 0,
+// (-1, -1), is a self-loop, which the set never holds, so self-loop pairs are
+// answered without a lookup.
 __device__ __forceinline__ bool pairset_contains(const Table& t, uint64_t pair) {
+  if ((uint32_t)(pair >> 32) == (uint32_t)pair) return false;
   const unsigned long long v = pair + 1ull;
   uint32_t b = pair_bucket(v, t.bucket_mask);
   for (uint32_t step = 0; step <= t.bucket_mask; ++step) {

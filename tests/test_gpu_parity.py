@@ -296,6 +296,34 @@ def test_chain4_zipf_full_size(ctx):
     assert plain["intermediate"] > 10 * max(1, res["intermediate"])
 
 
+@pytest.mark.parametrize("params", [
+    dict(bits_per_key=12, k=3, layout=sj.REGBLOCKED32, passes=sj.BWD_ONLY),
+    dict(bits_per_key=12, k=4, layout=sj.REGBLOCKED32, passes=sj.BWD_ONLY),
+    dict(bits_per_key=12, k=3, layout=sj.REGBLOCKED32, passes=sj.FWD_BWD),
+])
+def test_headline_path_full_size(ctx, params):
+    """The benchmark's exact call at its full size: sj_sieve_join on the 4-way
+    Zipf chain (10M rows per relation) with the tuned filter parameters, on
+    calls 1 to 6 (exact, device-sized, captured as a CUDA graph, then graph
+    replays), against the oracle's aggregate propagation; the per-step row
+    counts of the first call against the oracle's pruning phase with the same
+    parameters."""
+    w = inputs.zipf_chain()
+    rels = load(ctx, w)
+    exp = oracle.agg_propagation(w)
+    _, osteps = oracle.sieve_path(w, passes=params["passes"], bits_per_key=params["bits_per_key"],
+                                  k=params["k"], layout=params["layout"])
+    got = ctx.sieve_join(rels, w["edges"], w["preds"], w["root"], refs=w["sum"], stats=True, **params)
+    assert (got["count"], got["sum"]) == (exp["count"], exp["sum"])
+    assert got["steps"] == [tuple(s) for s in osteps]
+    g0 = ctx.graph_stats()
+    for call in range(6):
+        got = ctx.sieve_join(rels, w["edges"], w["preds"], w["root"], refs=w["sum"], **params)
+        assert (got["count"], got["sum"]) == (exp["count"], exp["sum"]), call
+    g1 = ctx.graph_stats()
+    assert g1["replays"] - g0["replays"] >= 3 and g1["failures"] == g0["failures"], g1
+
+
 def test_repeat_is_bit_identical(ctx):
     w = inputs.zipf_chain(nrows=500_000, domain=250_000, seed=8)
     rels = load(ctx, w)

@@ -89,3 +89,28 @@ def test_full_size_rmat_sampled(ctx):
     exp = oracle.triangle_counts_for(src, dst, verts)
     for v, e in zip(verts, exp):
         assert int(got2[np.searchsorted(vc, v, side="right") - 1]) == int(e)
+
+
+def test_negative_ids_and_two_cycles_through_minus_one(ctx):
+    """Vertex ids anywhere in int32, 2-cycles through -1 (whose closing pair
+    (-1, -1) packs to the pair set's empty code) and ids beyond both ends of
+    the cuts: exact against the oracle."""
+    g = np.random.default_rng(5)
+    ids = np.concatenate([np.array([-2**31, -1, 0, 2**31 - 1]), g.integers(-60, 60, 40)]).astype(np.int64)
+    ids = np.unique(ids)
+    s = g.choice(ids, 3000)
+    d = g.choice(ids, 3000)
+    extra_s = np.array([-1, 0, -1, 7, -2, -1, -1, 2**31 - 1])
+    extra_d = np.array([0, -1, 7, -1, -1, -2, 2**31 - 1, -1])
+    s = np.concatenate([s, extra_s])
+    d = np.concatenate([d, extra_d])
+    keep = s != d
+    pairs = np.unique(np.stack([s[keep], d[keep]], 1), axis=0)
+    src = pairs[:, 0].astype(np.int32)
+    dst = pairs[:, 1].astype(np.int32)
+    cuts = np.array([-30, -1, 0, 25], dtype=np.int32)
+    for rounds in (0, 2):
+        got, st = gpu_counts(ctx, src, dst, cuts, rounds)
+        exp = oracle.triangle_counts(src, dst, cuts)
+        assert np.array_equal(got.astype(np.int64), exp)
+        assert st["triangles"] == int(exp.sum())

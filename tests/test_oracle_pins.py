@@ -385,3 +385,66 @@ def test_triangle_counts_for_matches_full():
     got = oracle.triangle_counts_for(src, dst, verts)
     for v, c in zip(verts, got):
         assert full[np.searchsorted(cuts, v, side="right") - 1] == c
+
+
+def _brute_triangles(src, dst, cuts):
+    """Ordered (a, b, c) with a->b, b->c, c->a by three nested loops over the
+    edge list (tiny inputs only); a below cuts[0] in subquery 0, at or above
+    cuts[-1] in the last."""
+    edges = set(zip(src.tolist(), dst.tolist()))
+    out = [0] * (len(cuts) - 1)
+    for a, b in edges:
+        for b2, c in edges:
+            if b2 == b and (c, a) in edges:
+                i = 0
+                while i + 1 < len(cuts) - 1 and cuts[i + 1] <= a:
+                    i += 1
+                out[i] += 1
+    return out
+
+
+def test_triangles_negative_ids_and_two_cycles_brute_force():
+    """Negative vertex ids (including -1 and INT32_MIN) and 2-cycles through -1:
+    a pair of int32 ids must map to one key only, and a closing pair (c, a)
+    with c == a is never an edge (no self-loops)."""
+    g = np.random.default_rng(11)
+    vs = np.array([-2**31, -7, -2, -1, 0, 1, 5, 2**31 - 1], dtype=np.int64)
+    pairs = {(int(a), int(b)) for a in vs for b in vs if a != b and g.random() < 0.55}
+    pairs |= {(-1, 0), (0, -1), (-1, 5), (5, -1), (-2, -1), (-1, -2)}  # 2-cycles through -1
+    src = np.array([p[0] for p in pairs], dtype=np.int32)
+    dst = np.array([p[1] for p in pairs], dtype=np.int32)
+    cuts = np.array([-5, 0, 3], dtype=np.int32)  # ids below -5 and at or above 3 clamp
+    got = oracle.triangle_counts(src, dst, cuts)
+    assert list(got) == _brute_triangles(src, dst, cuts)
+    assert got.sum() % 3 == 0
+    verts = [-1, 0, 5, -2**31]
+    per = oracle.triangle_counts_for(src, dst, verts)
+    e = set(zip(src.tolist(), dst.tolist()))
+    for v, cnt in zip(verts, per):
+        # per-vertex count by brute force over the full edge set
+        brute = sum(1 for a, b in e if a == v for b2, c in e if b2 == b and (c, a) in e)
+        assert cnt == brute
+
+
+def test_threaded_probe_gives_the_same_results():
+    """The probe of the oracle's join levels split over threads returns the
+    same COUNT / SUM, the same materialised rows in the same order, and the
+    same triangle counts as the serial probe."""
+    w = inputs.zipf_chain(nrows=60_000, domain=30_000, seed=4)
+    src, dst = inputs.rmat_edges(scale=9, nedges=3000, seed=6)
+    cuts = inputs.uneven_cuts(1 << 9, 5, seed=6)
+    try:
+        oracle.set_threads(1)
+        a = oracle.hash_join(w)
+        am = oracle.hash_join(w, mode=oracle.MATERIALIZE, refs=[(0, 0, 0), (3, 1, 0)])
+        at = oracle.triangle_counts(src, dst, cuts)
+        for t in (2, 7):
+            oracle.set_threads(t)
+            assert oracle.get_threads() == t
+            assert oracle.hash_join(w) == a
+            bm = oracle.hash_join(w, mode=oracle.MATERIALIZE, refs=[(0, 0, 0), (3, 1, 0)])
+            assert bm["count"] == am["count"]
+            assert all(np.array_equal(x, y) for x, y in zip(bm["cols"], am["cols"]))
+            assert np.array_equal(oracle.triangle_counts(src, dst, cuts), at)
+    finally:
+        oracle.set_threads(1)
