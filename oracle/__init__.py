@@ -9,6 +9,7 @@ Contents, each following the passage named in its docstring:
 
 * ``fmix64``, ``bloom_*``   -- the Bloom filter (Sec. 1; Sec. 2.1 step 1 and 3)
   under this project's reading of the unspecified hash family and layout.
+* ``filter_insert``         -- insert maintenance of a built filter (Sec. 2.4).
 * ``sieve``, ``sieve_path`` -- the pruning phase (Sec. 2.2): filters are built
   along the join tree and each relation keeps the tuples whose join keys pass
   the incoming filters; first toward the root, then back.
@@ -168,10 +169,12 @@ def bloom_positions(h: np.ndarray, nblocks: int, k: int, layout: int):
 
 
 def bloom_build(keys: np.ndarray, bits_per_key: int = 8, k: int = 3,
-                layout: int = REG32, seed: int = 0) -> dict:
-    """Build a filter: set every hash position of every key (Sec. 2.1 step 1)."""
+                layout: int = REG32, seed: int = 0, nblocks: int = None) -> dict:
+    """Build a filter: set every hash position of every key (Sec. 2.1 step 1).
+    ``nblocks`` fixes the size instead of deriving it from the key count."""
     keys = np.asarray(keys, dtype=np.int32)
-    nblocks = bloom_nblocks(len(keys), bits_per_key)
+    if nblocks is None:
+        nblocks = bloom_nblocks(len(keys), bits_per_key)
     words = np.zeros(nblocks * 8, dtype=np.uint32)
     h = key_hash(keys, seed)
     for word, mask in bloom_positions(h, nblocks, k, layout):
@@ -188,6 +191,38 @@ def bloom_contains(f: dict, keys: np.ndarray) -> np.ndarray:
     for word, mask in bloom_positions(h, f["nblocks"], f["k"], f["layout"]):
         ok &= (f["words"][word] & mask) != 0
     return ok
+
+
+INSERT_GATED, INSERT_CONTAINED, INSERT_NEW = 0, 1, 2
+
+
+def filter_insert(f: dict, cols, key_col: int, gates=()):
+    """Insert maintenance (Sec. 2.4): new tuples of the relation whose filter
+    ``f`` was built.  A tuple first meets the filters the relation receives
+    from its other neighbours (``gates``: (column, filter) pairs): one that
+    fails any of them cannot join and is dropped (INSERT_GATED).  A tuple
+    whose key the filter already contains needs no update (INSERT_CONTAINED).
+    Any other tuple's key bits are set (INSERT_NEW): the filter changed, and
+    that tuple is the one to follow to the adjacent relations.  Containment is
+    judged against the filter as it was before the call, so the outcome does
+    not depend on the order of the new tuples.  The filter keeps its size.
+    Returns (new filter dict, status array of int8)."""
+    n = len(cols[0]) if cols else 0
+    passes = np.ones(n, dtype=bool)
+    for col, g in gates:
+        passes &= bloom_contains(g, cols[col])
+    keys = np.asarray(cols[key_col], dtype=np.int32)
+    contained = bloom_contains(f, keys)
+    status = np.full(n, INSERT_GATED, dtype=np.int8)
+    status[passes & contained] = INSERT_CONTAINED
+    new = passes & ~contained
+    status[new] = INSERT_NEW
+    words = f["words"].copy()
+    h = key_hash(keys[new], f["seed"])
+    for word, mask in bloom_positions(h, f["nblocks"], f["k"], f["layout"]):
+        np.bitwise_or.at(words, word, mask)
+    out = dict(f, words=words, n_inserted=f["n_inserted"] + int(new.sum()))
+    return out, status
 
 
 # ----------------------------------------------------------------------------- selection / sieve

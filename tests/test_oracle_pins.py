@@ -448,3 +448,38 @@ def test_threaded_probe_gives_the_same_results():
             assert np.array_equal(oracle.triangle_counts(src, dst, cuts), at)
     finally:
         oracle.set_threads(1)
+
+
+@pytest.mark.parametrize("layout", [oracle.REG32, oracle.BLOCKED256, oracle.CLASSIC])
+def test_filter_insert_equals_build_over_union(layout):
+    """Sec. 2.4 insert maintenance: after inserting new tuples, the filter is
+    the one built over the old keys and the admitted new keys at the old size
+    (OR is order-free); every admitted key is contained (no false negatives);
+    a tuple is CONTAINED exactly when all its bits were set before the call,
+    and GATED exactly when it fails a neighbour's filter."""
+    g = np.random.default_rng(3)
+    old = g.integers(0, 40_000, 20_000, dtype=np.int32)
+    f = oracle.bloom_build(old, 8, 3, layout, seed=5)
+    other = g.integers(0, 40_000, 6_000, dtype=np.int32)
+    gate = oracle.bloom_build(g.integers(0, 40_000, 15_000, dtype=np.int32), 8, 3, layout, seed=6)
+    new_keys = np.concatenate([old[:500], g.integers(0, 60_000, 5_500, dtype=np.int32)])
+    cols = [new_keys, other]
+    f2, st = oracle.filter_insert(f, cols, 0, [(1, gate)])
+    admitted = oracle.bloom_contains(gate, other)
+    assert np.array_equal(st == oracle.INSERT_GATED, ~admitted)
+    before = oracle.bloom_contains(f, new_keys)
+    assert np.array_equal(st == oracle.INSERT_CONTAINED, admitted & before)
+    assert np.array_equal(st == oracle.INSERT_NEW, admitted & ~before)
+    union = np.concatenate([old, new_keys[admitted]])
+    rebuilt = oracle.bloom_build(union, 8, 3, layout, seed=5, nblocks=f["nblocks"])
+    assert np.array_equal(f2["words"], rebuilt["words"])
+    assert oracle.bloom_contains(f2, new_keys[admitted]).all()
+    assert oracle.bloom_contains(f2, old).all()
+    # order does not matter
+    perm = g.permutation(len(new_keys))
+    f3, st3 = oracle.filter_insert(f, [c[perm] for c in cols], 0, [(1, gate)])
+    assert np.array_equal(f3["words"], f2["words"]) and np.array_equal(st3, st[perm])
+    # no gates: every new key is admitted
+    f4, st4 = oracle.filter_insert(f, [new_keys], 0)
+    assert (st4 != oracle.INSERT_GATED).all()
+    assert oracle.bloom_contains(f4, new_keys).all()
