@@ -557,10 +557,20 @@ def cyclic_run(torch, sj, ctx, stream):
             e1.record(stream)
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1))
-        out[key] = {"ms": float(np.median(times)), "triangles": int(counts.sum()),
+        ms = float(np.median(times))
+        # algorithmic bytes of the enumeration: each pruned edge read (8 B) and
+        # its two adjacency lookups (2 x 32 B sectors), each candidate wedge's
+        # adjacency entry and far endpoint (8 B), and a 32 B pair-set sector
+        # for each candidate the pair filter passes (the filter itself is
+        # L2-resident and not counted)
+        alg = (8.0 + 64.0) * st["edges_sieved"] + 8.0 * st["candidates"] + 32.0 * st["filter_passed"]
+        gbps = alg / (ms / 1000.0) / 1e9
+        out[key] = {"ms": ms, "triangles": int(counts.sum()),
                     "edges_after_sieve": st["edges_sieved"], "closing_pairs_checked": st["candidates"],
                     "passed_pair_filter": st["filter_passed"],
-                    "edge_tuples_per_s": 3 * 50_000_000 / (float(np.median(times)) / 1000.0)}
+                    "edge_tuples_per_s": 3 * 50_000_000 / (ms / 1000.0),
+                    "roofline": {"bound": "hbm", "alg_bytes": alg, "achieved": gbps, "unit": "GB/s",
+                                 "peak": load_peaks()[0], "frac": gbps / load_peaks()[0]}}
     rel.free()
     return out
 

@@ -166,6 +166,32 @@ SJ_API sj_status sj_filter_probe(sj_ctx *ctx, sj_filter f, const int32_t *keys, 
 SJ_API sj_status sj_free_filter(sj_ctx *ctx, sj_filter f);
 
 /*
+ * Insert maintenance of a built filter (Sec. 2.4).  The `nrows` rows of
+ * `rel` are new tuples of the relation whose column the filter `f` was built
+ * over; `key_col` is that column in `rel`.  A row first meets the filters the
+ * relation receives from its other neighbours (ngate of them, 0 <= ngate <=
+ * SJ_MAX_PROBES: gates[j] tested on column gate_cols[j]): a row that fails any
+ * cannot reach the join result and is dropped (SJ_INSERT_GATED).  A row whose
+ * key the filter already contains needs no update (SJ_INSERT_CONTAINED).  The
+ * key bits of every other row are set (SJ_INSERT_NEW): the filter changed, and
+ * those rows are the ones whose effect must be followed to the adjacent
+ * relations -- their neighbours' tuples that join with them may now survive a
+ * sieve by this filter (the paper's search from the relation to its adjacent
+ * relations).  Containment is judged against the filter as it was before the
+ * call, so the outcome does not depend on row order; the filter keeps its size
+ * (its false-positive rate grows as keys are added) and its inserted-row count
+ * grows by the SJ_INSERT_NEW rows.  status_out is NULL or nrows device bytes
+ * receiving each row's outcome; counts is NULL or host int64[3] receiving the
+ * number of rows of each outcome (the call then synchronises).  Errors:
+ * SJ_EINVAL (null filter or relation, column out of range, ngate out of
+ * range), SJ_ENOMEM, SJ_ECUDA.
+ */
+enum { SJ_INSERT_GATED = 0, SJ_INSERT_CONTAINED = 1, SJ_INSERT_NEW = 2 };
+SJ_API sj_status sj_filter_insert(sj_ctx *ctx, sj_filter f, sj_rel rel, int key_col, int ngate,
+                                  const int *gate_cols, const sj_filter *gates, uint8_t *status_out,
+                                  int64_t *counts);
+
+/*
  * One sieve step (Sec. 2.2, pruning phase): keep, in input order, the rows of
  * `rel` that pass `pred` (NULL = none) and whose column key_cols[j] passes
  * filters[j] for every j < nprobe (0 <= nprobe <= SJ_MAX_PROBES).  The kept

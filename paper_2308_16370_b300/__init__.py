@@ -17,13 +17,14 @@ import numpy as np
 
 __all__ = ["Context", "Relation", "Filter", "SieveJoinError", "load_library", "LIB_PATH",
            "REGBLOCKED32", "BLOCKED256", "CLASSIC", "FWD_BWD", "BWD_ONLY", "NO_SIEVE", "COUNT_SUM",
-           "MATERIALIZE", "KERNEL_KINDS"]
+           "MATERIALIZE", "KERNEL_KINDS", "INSERT_GATED", "INSERT_CONTAINED", "INSERT_NEW"]
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libsievejoin.so")
 
 REGBLOCKED32, BLOCKED256, CLASSIC = 0, 1, 2
 FWD_BWD, BWD_ONLY, NO_SIEVE = 0, 1, 2
 COUNT_SUM, MATERIALIZE = 0, 1
+INSERT_GATED, INSERT_CONTAINED, INSERT_NEW = 0, 1, 2
 DEVICE_BORROW, DEVICE_COPY, HOST_COPY = 0, 1, 2
 MAX_COLS, MAX_REL, MAX_PROBES, MAX_TERMS, MAX_STEPS = 8, 8, 4, 8, 32
 KERNEL_KINDS = {"bloom_build": 0, "sieve": 1, "ht_build": 2, "ht_probe": 3, "ht_expand": 4,
@@ -38,7 +39,7 @@ EXPORTS = ["sj_create", "sj_destroy", "sj_sync", "sj_last_error", "sj_status_str
            "sj_prof_enable", "sj_prof_kinds", "sj_prof_reset", "sj_prof_read", "sj_counters", "sj_graph_stats", "sj_graphs_enable", "sj_sieve_noalloc",
            "sj_server_create", "sj_server_add_relation", "sj_server_submit", "sj_server_poll",
            "sj_server_stats_get", "sj_server_destroy", "sj_triangles", "sj_sieve_join", "sj_prof_gaps",
-           "sj_selftest_wait_timeout"]
+           "sj_selftest_wait_timeout", "sj_filter_insert"]
 
 
 class SieveJoinError(RuntimeError):
@@ -152,6 +153,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "sj_build_filter": [P, P, I, ctypes.POINTER(Pred), ctypes.POINTER(FilterParams), PP],
         "sj_filter_info": [P, P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64), PP],
         "sj_filter_probe": [P, P, P, I64, P],
+        "sj_filter_insert": [P, P, P, I, I, ctypes.POINTER(ctypes.c_int), PP, P, ctypes.POINTER(I64)],
         "sj_free_filter": [P, P],
         "sj_sieve": [P, P, I, ctypes.POINTER(ctypes.c_int), PP, ctypes.POINTER(Pred), PP,
                      ctypes.POINTER(I64)],
@@ -400,6 +402,21 @@ class Context:
         self._check(self.lib.sj_filter_probe(self.ctx, f.handle, ctypes.c_void_p(keys.data_ptr()),
                                              len(keys), ctypes.c_void_p(out.data_ptr())))
         return out
+
+    def filter_insert(self, f: Filter, rel: Relation, key_col: int, gates=()):
+        """Insert maintenance (Sec. 2.4): the rows of ``rel`` are new tuples of
+        the relation ``f`` was built over (key in column ``key_col``); ``gates``
+        are (column, filter) pairs of the neighbours' filters.  Returns (per-row
+        outcome as a uint8 tensor: INSERT_GATED / INSERT_CONTAINED / INSERT_NEW,
+        counts of the three)."""
+        torch = _torch()
+        status = torch.empty(max(rel.nrows, 1), dtype=torch.uint8, device=f"cuda:{self.device}")
+        gc = (ctypes.c_int * max(1, len(gates)))(*[int(g[0]) for g in gates])
+        gf = (ctypes.c_void_p * max(1, len(gates)))(*[g[1].handle.value for g in gates])
+        counts = (ctypes.c_int64 * 3)()
+        self._check(self.lib.sj_filter_insert(self.ctx, f.handle, rel.handle, int(key_col), len(gates),
+                                              gc, gf, ctypes.c_void_p(status.data_ptr()), counts))
+        return status[:rel.nrows], [int(x) for x in counts]
 
     def sieve(self, rel: Relation, key_cols=(), filters=(), pred=None) -> Relation:
         kc = (ctypes.c_int * max(1, len(key_cols)))(*key_cols)

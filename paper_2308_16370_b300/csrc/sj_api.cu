@@ -905,6 +905,55 @@ sj_status sj_filter_probe(sj_ctx* c, sj_filter f, const int32_t* keys, int64_t n
   return check_launch(c, "k_bloom_probe");
 }
 
+sj_status sj_filter_insert(sj_ctx* c, sj_filter f, sj_rel rel, int key_col, int ngate,
+                           const int* gate_cols, const sj_filter* gates, uint8_t* status_out,
+                           int64_t* counts) {
+  if (!c || !f || !rel) return fail(c, SJ_EINVAL, "null argument");
+  if (key_col < 0 || key_col >= rel->ncols) return fail(c, SJ_EINVAL, "key column out of range");
+  if (ngate < 0 || ngate > SJ_MAX_PROBES || (ngate > 0 && (!gate_cols || !gates)))
+    return fail(c, SJ_EINVAL, "bad gates");
+  for (int g = 0; g < ngate; ++g) {
+    if (!gates[g]) return fail(c, SJ_EINVAL, "null gate filter");
+    if (gate_cols[g] < 0 || gate_cols[g] >= rel->ncols) return fail(c, SJ_EINVAL, "gate column out of range");
+  }
+  if (rel->nrows < 0) return fail(c, SJ_EINVAL, "relation row count unknown");
+  const int64_t n = rel->nrows;
+  sj_status st = SJ_OK;
+  Temps tmp(c);
+  uint8_t* status = status_out ? status_out : tmp.get<uint8_t>((size_t)std::max<int64_t>(n, 1), &st);
+  unsigned long long* cnt = tmp.get<unsigned long long>(3, &st);
+  if (st != SJ_OK) return fail(c, st, "insert scratch allocation failed");
+  SJ_CUDA(c, cudaMemsetAsync(cnt, 0, 3 * sizeof(unsigned long long), c->stream));
+  InsertArgs a;
+  memset(&a, 0, sizeof(a));
+  a.f = view(f);
+  a.words = f->words;
+  a.hdr = f->hdr;
+  a.keys = rel->cols[key_col];
+  a.n = n;
+  a.ngate = ngate;
+  for (int g = 0; g < ngate; ++g) {
+    a.gate[g].col = rel->cols[gate_cols[g]];
+    a.gate[g].f = view(gates[g]);
+  }
+  a.status = status;
+  a.counts = cnt;
+  {
+    Launch L(c, SJ_K_BLOOM_BUILD, (4.0 + 4.0 * ngate + 1.0) * (double)n);
+    c->launches++;  // two kernels
+    launch_filter_insert(a, c->num_sms, c->stream);
+  }
+  SJ_TRY(check_launch(c, "k_insert_check + k_insert_or"));
+  if (counts) {
+    unsigned long long h[3];
+    SJ_CUDA(c, cudaMemcpyAsync(h, cnt, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    c->d2h_bytes += sizeof(h);
+    SJ_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < 3; ++k) counts[k] = (int64_t)h[k];
+  }
+  return SJ_OK;
+}
+
 sj_status sj_free_filter(sj_ctx* c, sj_filter f) {
   if (!c || !f) return SJ_EINVAL;
   free_filter(c, f);

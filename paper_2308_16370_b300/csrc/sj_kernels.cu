@@ -760,6 +760,65 @@ __global__ void __launch_bounds__(kCkThreads, K > 0 ? kCkMinBlocks : 4) k_sieve_
   ck_zero(a, prefix, prefix + total, t == 0);
 }
 
+// ---------------------------------------------------------------- insert maintenance
+__global__ void __launch_bounds__(kBlock) k_insert_check(InsertArgs a) {
+  __shared__ unsigned long long s_c[3];
+  if (threadIdx.x < 3) s_c[threadIdx.x] = 0ull;
+  __syncthreads();
+  const uint64_t nb = __ldg(a.f.hdr);
+  unsigned long long c[3] = {0ull, 0ull, 0ull};
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+    bool pass = true;
+    for (int g = 0; g < a.ngate && pass; ++g)
+      pass = filter_contains(a.gate[g].f, __ldg(a.gate[g].f.hdr), __ldg(a.gate[g].col + i));
+    uint8_t st = 0;
+    if (pass) st = filter_contains(a.f, nb, __ldg(a.keys + i)) ? 1 : 2;
+    a.status[i] = st;
+    c[st] += 1;
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    unsigned long long v = c[k];
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(&s_c[k], v);
+  }
+  __syncthreads();
+  if (threadIdx.x < 3 && s_c[threadIdx.x]) atomicAdd(a.counts + threadIdx.x, s_c[threadIdx.x]);
+}
+
+// Set the k bits of `key` in a filter of nb blocks (any layout).
+__device__ __forceinline__ void filter_or_key(uint32_t* words, uint64_t nb, uint32_t k, uint32_t layout,
+                                              uint64_t seed, int32_t key) {
+  const uint64_t h = key_hash(key, seed);
+  if (layout == 0) {
+    atomicOr(words + reg32_word(h, nb * 8), reg32_mask((uint32_t)h, k));
+  } else if (layout == 1) {
+    const uint64_t blk = ((h >> 32) * nb) >> 32;
+    for (uint32_t i = 0; i < k; ++i) {
+      const uint32_t bit = (uint32_t)(h >> (8 * i)) & 255u;
+      atomicOr(words + blk * 8 + (bit >> 5), 1u << (bit & 31));
+    }
+  } else {
+    const uint64_t m = nb * 256ull;
+    const uint64_t h1 = h & 0xffffffffull;
+    const uint64_t h2 = (h >> 32) | 1ull;
+    for (uint32_t i = 0; i < k; ++i) {
+      const uint64_t g = (h1 + (uint64_t)i * h2) % m;
+      atomicOr(words + (g >> 5), 1u << (g & 31));
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_insert_or(InsertArgs a) {
+  const uint64_t nb = __ldg(a.f.hdr);
+  if (blockIdx.x == 0 && threadIdx.x == 0) a.hdr[1] += a.counts[2];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride)
+    if (a.status[i] == 2) filter_or_key(a.words, nb, a.f.k, a.f.layout, a.f.seed, __ldg(a.keys + i));
+}
+
 // ---------------------------------------------------------------- group offsets
 __global__ void __launch_bounds__(kBlock) k_group_offsets(GroupOffArgs a) {
   __shared__ Vec<2> s_warp[kBlock / 32];
@@ -1569,6 +1628,12 @@ void launch_sieve_chunk(const SieveArgs& a, int64_t n_upper, int num_sms, cudaSt
     case 3: launch_hi(k_sieve_chunk<3>, (unsigned)g, kCkThreads, s, a); break;
     default: launch_hi(k_sieve_chunk<4>, (unsigned)g, kCkThreads, s, a); break;
   }
+}
+
+void launch_filter_insert(const InsertArgs& a, int num_sms, cudaStream_t s) {
+  const int g = host_grid(a.n, kBlock * 4, num_sms * 8);
+  k_insert_check<<<g, kBlock, 0, s>>>(a);
+  k_insert_or<<<g, kBlock, 0, s>>>(a);
 }
 
 void launch_group_offsets(const GroupOffArgs& a, int64_t n_upper, int num_sms, cudaStream_t s) {

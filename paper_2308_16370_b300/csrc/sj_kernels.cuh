@@ -88,6 +88,24 @@ void launch_sieve_chunk(const SieveArgs& a, int64_t n_upper, int num_sms, cudaSt
 
 
 
+// ------------------------------------------------------------------ insert maintenance
+// Sec. 2.4: new tuples of a relation whose filter exists.  k_insert_check
+// classifies every row against the filter as it was before the call (gated by
+// a neighbour's filter / key already contained / new); k_insert_or then sets
+// the bits of the new rows' keys and adds their number to the filter header.
+struct InsertArgs {
+  FilterView f;               // the filter being maintained
+  uint32_t* words;            // its words (written by k_insert_or)
+  uint64_t* hdr;              // its header: hdr[1] += rows inserted
+  const int32_t* keys;
+  int64_t n;
+  int ngate;
+  SieveTest gate[kMaxTests];  // filter tests of the neighbours' filters (col = gate column)
+  uint8_t* status;            // per row: 0 gated, 1 contained, 2 new
+  unsigned long long* counts; // [3], zeroed before k_insert_check
+};
+void launch_filter_insert(const InsertArgs& a, int num_sms, cudaStream_t s);
+
 // ------------------------------------------------------------------ group offsets
 // Start of every table slot's row group in a multimap (CSR by slot).  Groups
 // only need disjoint ranges, not slot order, so each tile of slots takes its
