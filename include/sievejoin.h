@@ -314,6 +314,28 @@ typedef struct {
 SJ_API sj_status sj_sieve_path(sj_ctx *ctx, const sj_path *path, const sj_sieve_opts *opts,
                         sj_rel *out_sieved, sj_sieve_stats *stats);
 
+/*
+ * The pruning phases (Sec. 2.2) of `nq` queries in one call, for a serving
+ * runtime that has several queries in hand at once.  paths[q] and, unless
+ * `opts` is NULL, opts[q] describe query q exactly as for sj_sieve_path
+ * (opts[q].leaf_filters hands in query q's reusable leaf filters, Sec. 2.3).
+ * The queries' sieve steps and filter builds run in lock step: an operation
+ * runs at one more than the level of everything it reads (the step that
+ * produced its input relation, the builds of the filters it probes), and all
+ * steps of one level, over all queries, are one kernel launch, as are all
+ * builds of one level.  A batch therefore takes two launches per level of its
+ * longest schedule instead of a launch per step and build of every query.
+ * On return out_sieved[q * SJ_MAX_REL + i] is query q's relation i after
+ * pruning (a new handle; free with sj_free_rel), identical, rows and order,
+ * to what sj_sieve_path returns for that query alone; stats (NULL, or nq
+ * entries) as for sj_sieve_path.  Every intermediate relation of the batch
+ * stays allocated until the call ends.  Synchronises once.  SJ_EINVAL if any
+ * query is invalid (nothing is then enqueued).  nq = 0 does nothing.
+ */
+SJ_API sj_status sj_sieve_path_batch(sj_ctx *ctx, int nq, const sj_path *paths,
+                                     const sj_sieve_opts *opts, sj_rel *out_sieved,
+                                     sj_sieve_stats *stats);
+
 enum { SJ_COUNT_SUM = 0, SJ_MATERIALIZE = 1 };
 
 /* A column reference: SUM term or projected output column.  wide = 1 reads an
@@ -403,6 +425,10 @@ typedef struct {
     int32_t passes;          /* sieve schedule (SJ_FWD_BWD, ...) */
     int32_t cache_filters;   /* 1 = reuse leaf filters across queries */
     sj_filter_params filter; /* parameters of every filter the server builds */
+    int32_t batch;           /* > 1: a worker takes up to `batch` queued queries at once and runs
+                                their pruning phases as one sj_sieve_path_batch call, then
+                                each query's join; 0 or 1 = one query at a time */
+    int32_t reserved;
 } sj_server_opts;
 
 typedef struct {
@@ -431,7 +457,8 @@ typedef struct {
     uint64_t cache_hits, cache_misses, cached_filters;
     uint64_t peak_inflight_bytes;
     int32_t peak_concurrency;
-    int32_t reserved;
+    int32_t peak_batch;      /* most queries pruned by one sj_sieve_path_batch call */
+    uint64_t batches;        /* sj_sieve_path_batch calls (batch mode) */
 } sj_server_stats;
 
 /* Create a server (starts its workers).  Errors: SJ_EINVAL, SJ_ECUDA, SJ_ENOMEM. */

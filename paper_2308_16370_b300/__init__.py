@@ -35,7 +35,7 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "out of device memory", 3: "hash ta
 # exported symbols of the C ABI (checked by the CPU tests against the header)
 EXPORTS = ["sj_create", "sj_destroy", "sj_sync", "sj_last_error", "sj_status_str", "sj_version",
            "sj_load_relation", "sj_rel_info", "sj_free_rel", "sj_build_filter", "sj_filter_info",
-           "sj_filter_probe", "sj_free_filter", "sj_sieve", "sj_sieve_path", "sj_join",
+           "sj_filter_probe", "sj_free_filter", "sj_sieve", "sj_sieve_path", "sj_sieve_path_batch", "sj_join",
            "sj_prof_enable", "sj_prof_kinds", "sj_prof_reset", "sj_prof_read", "sj_counters", "sj_graph_stats", "sj_graphs_enable", "sj_sieve_noalloc",
            "sj_server_create", "sj_server_add_relation", "sj_server_submit", "sj_server_poll",
            "sj_server_stats_get", "sj_server_destroy", "sj_triangles", "sj_sieve_join", "sj_prof_gaps",
@@ -94,7 +94,8 @@ class ColRef(ctypes.Structure):
 class ServerOpts(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("nslots", ctypes.c_int32),
                 ("hbm_budget", ctypes.c_uint64), ("passes", ctypes.c_int32),
-                ("cache_filters", ctypes.c_int32), ("filter", FilterParams)]
+                ("cache_filters", ctypes.c_int32), ("filter", FilterParams),
+                ("batch", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class Query(ctypes.Structure):
@@ -116,7 +117,7 @@ class ServerStats(ctypes.Structure):
                 ("failed", ctypes.c_uint64), ("cache_hits", ctypes.c_uint64),
                 ("cache_misses", ctypes.c_uint64), ("cached_filters", ctypes.c_uint64),
                 ("peak_inflight_bytes", ctypes.c_uint64), ("peak_concurrency", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("peak_batch", ctypes.c_int32), ("batches", ctypes.c_uint64)]
 
 
 class TriStats(ctypes.Structure):
@@ -159,6 +160,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                      ctypes.POINTER(I64)],
         "sj_sieve_path": [P, ctypes.POINTER(Path), ctypes.POINTER(SieveOpts), PP,
                           ctypes.POINTER(SieveStats)],
+        "sj_sieve_path_batch": [P, I, ctypes.POINTER(Path), ctypes.POINTER(SieveOpts), PP,
+                                ctypes.POINTER(SieveStats)],
         "sj_join": [P, ctypes.POINTER(Path), PP, I, I, ctypes.POINTER(ColRef), ctypes.POINTER(Result)],
         "sj_prof_enable": [P, I], "sj_prof_kinds": [P, ctypes.c_uint32], "sj_prof_reset": [P],
         "sj_prof_read": [P, I, ctypes.POINTER(I64), ctypes.POINTER(ctypes.c_double),
@@ -465,6 +468,42 @@ class Context:
         return sieved, {"steps": steps, "rows_final": [stats.rows_final[i] for i in range(len(rels))],
                         "filter_bytes": int(stats.filter_bytes)}
 
+    def sieve_path_batch(self, queries, passes=FWD_BWD, bits_per_key=8, k=3, layout=REGBLOCKED32,
+                         seed=0):
+        """Pruning phases of several queries in one call (lock-step launches).
+
+        ``queries``: dicts with ``rels``, ``edges`` and optionally ``preds``,
+        ``root`` and ``leaf_filters`` (as for sieve_path).  Returns one
+        (sieved relations, stats) pair per query, equal to sieve_path's."""
+        nq = len(queries)
+        paths = (Path * max(1, nq))()
+        opts = (SieveOpts * max(1, nq))()
+        keep = []
+        for i, q in enumerate(queries):
+            path, kp = self._path(q["rels"], q["edges"], q.get("preds"), q.get("root", -1))
+            paths[i] = path
+            keep.append(kp)
+            lf = None
+            if q.get("leaf_filters") is not None:
+                lf = (ctypes.c_void_p * len(q["rels"]))(*[(f.handle.value if f is not None else None)
+                                                          for f in q["leaf_filters"]])
+                keep.append(lf)
+            opts[i] = SieveOpts(int(passes), 0, _params(bits_per_key, k, layout, seed),
+                                ctypes.cast(lf, ctypes.POINTER(ctypes.c_void_p)) if lf is not None else None)
+        outs = (ctypes.c_void_p * (MAX_REL * max(1, nq)))()
+        stats = (SieveStats * max(1, nq))()
+        self._check(self.lib.sj_sieve_path_batch(self.ctx, nq, paths, opts, outs, stats))
+        res = []
+        for i, q in enumerate(queries):
+            n = len(q["rels"])
+            st = stats[i]
+            sieved = [Relation(self, outs[i * MAX_REL + j]) for j in range(n)]
+            steps = [(("select", "fwd", "bwd")[st.step[s].kind], st.step[s].rel,
+                      st.step[s].rows_in, st.step[s].rows_out) for s in range(st.nsteps)]
+            res.append((sieved, {"steps": steps, "rows_final": [st.rows_final[j] for j in range(n)],
+                                 "filter_bytes": int(st.filter_bytes)}))
+        return res
+
     def join(self, rels, edges, preds=None, root=-1, inputs=None, mode=COUNT_SUM, refs=()):
         """Left-deep hash join.  ``refs`` = [(rel, col, wide), ...]: SUM terms
         (COUNT_SUM) or projected columns (MATERIALIZE)."""
@@ -578,10 +617,13 @@ class Context:
 
 class Server:
     """Query server with continuous batching over `nslots` workers (one CUDA
-    stream each) and a device cache of reusable leaf filters (Sec. 2.3)."""
+    stream each) and a device cache of reusable leaf filters (Sec. 2.3).
+    ``batch`` > 1: a worker takes up to that many queued queries at once and
+    prunes them in one batched call (lock-step launches), then joins each."""
 
     def __init__(self, device: int = 0, nslots: int = 4, hbm_budget: int = 0, passes=FWD_BWD,
-                 cache_filters: bool = True, bits_per_key=8, k=3, layout=REGBLOCKED32, seed=0):
+                 cache_filters: bool = True, bits_per_key=8, k=3, layout=REGBLOCKED32, seed=0,
+                 batch: int = 0):
         torch = _torch()
         if not torch.cuda.is_available():
             raise RuntimeError("sievejoin needs a CUDA GPU; none is visible")
@@ -589,7 +631,8 @@ class Server:
         self.device = int(device)
         self._keep = []
         opts = ServerOpts(self.device, int(nslots), int(hbm_budget), int(passes),
-                          1 if cache_filters else 0, _params(bits_per_key, k, layout, seed))
+                          1 if cache_filters else 0, _params(bits_per_key, k, layout, seed),
+                          int(batch), 0)
         h = ctypes.c_void_p()
         st = self.lib.sj_server_create(ctypes.byref(h), ctypes.byref(opts))
         if st != 0:

@@ -108,6 +108,10 @@ struct sj_ctx {
   uint32_t prof_mask = 0xffffffffu;  // kernel classes profiled while prof_on
   std::vector<ProfRec> prof;
   std::vector<cudaEvent_t> ev_pool;
+  // pinned staging of sj_sieve_path_batch (launch arguments, counts read back)
+  uint8_t* h_batch = nullptr;
+  size_t h_batch_bytes = 0;
+  bool batch_pending = false;  // a copy from h_batch may still be in flight
   size_t ev_used = 0;
   double prof_ms[SJ_K_COUNT] = {};
   double prof_gap_ms[SJ_K_COUNT] = {};  // device idle after a launch of each class
@@ -787,6 +791,7 @@ sj_status sj_destroy(sj_ctx* c) {
   raw_free(c, c->d_misc, kMiscWords * sizeof(uint64_t));
   cudaStreamSynchronize(c->stream);
   cudaFreeHost(c->h_misc);
+  if (c->h_batch) cudaFreeHost(c->h_batch);
   for (auto e : c->ev_pool) cudaEventDestroy(e);
   if (c->ev_wait) cudaEventDestroy(c->ev_wait);
   delete c;
@@ -997,6 +1002,69 @@ namespace {
 // Called once per relation as soon as its last sieve step is enqueued.
 // `slot` is the statistics slot of its device row count (-1: not sieved, the
 // host knows the count).
+// The pruning schedule of one query (Sec. 2.2): predicate selections first;
+// with SJ_FWD_BWD pass 1 in post-order (a relation is sieved by its
+// children's filters, then builds the filter it sends to its parent) and
+// pass 2 in pre-order (a relation is sieved by its parent's filter, then
+// builds one filter per child).  A leaf's pass-1 filter may be handed in
+// (Sec. 2.3).  kOpFinal marks the point after which a relation is not
+// sieved again.  Filter ids index `given` (a handed-in filter, else null).
+enum { kOpStep, kOpBuild, kOpFinal };
+struct PruneOp {
+  int type, rel, kind;                      // kind: step kind for statistics
+  std::vector<std::pair<int, int>> probes;  // (column, filter id)
+  bool pred;
+  int col, fid;                             // build: column and filter id
+};
+struct PrunePlan {
+  std::vector<PruneOp> ops;
+  std::vector<sj_filter> given;
+};
+
+sj_status plan_pruning(sj_ctx* c, const sj_path* path, const Tree& tr, const sj_sieve_opts& o,
+                       PrunePlan* out) {
+  const int n = path->nrel;
+  std::vector<PruneOp>& ops = out->ops;
+  std::vector<sj_filter>& fl = out->given;
+  ops.clear();
+  fl.clear();
+  auto new_fid = [&]() { fl.push_back(nullptr); return (int)fl.size() - 1; };
+  for (int i = 0; i < n; ++i)
+    if (has_pred(path, i)) ops.push_back({kOpStep, i, 0, {}, true, -1, -1});
+  if (o.passes == SJ_NO_SIEVE || n == 1)
+    for (int i = 0; i < n; ++i) ops.push_back({kOpFinal, i, 0, {}, false, -1, -1});
+  if (o.passes == SJ_NO_SIEVE || n == 1) return SJ_OK;
+  std::vector<int> up(n, -1), down(n, -1);
+  if (o.passes == SJ_FWD_BWD) {
+    for (int v : tr.post) {
+      if (!tr.children[v].empty()) {
+        if ((int)tr.children[v].size() > SJ_MAX_PROBES)
+          return fail(c, SJ_EINVAL, "a relation has more than 4 children");
+        PruneOp op{kOpStep, v, 1, {}, false, -1, -1};
+        for (int ch : tr.children[v]) op.probes.push_back({edge_col(path->edges[tr.pedge[ch]], v), up[ch]});
+        ops.push_back(op);
+      }
+      if (tr.parent[v] >= 0) {
+        up[v] = new_fid();
+        if (tr.children[v].empty() && o.leaf_filters && o.leaf_filters[v])
+          fl[up[v]] = o.leaf_filters[v];  // reused (Sec. 2.3); owned by the caller
+        else
+          ops.push_back({kOpBuild, v, 0, {}, false, edge_col(path->edges[tr.pedge[v]], v), up[v]});
+      }
+    }
+  }
+  for (int v : tr.pre) {
+    if (tr.parent[v] >= 0)
+      ops.push_back({kOpStep, v, 2, {{edge_col(path->edges[tr.pedge[v]], v), down[v]}}, false, -1, -1});
+    ops.push_back({kOpFinal, v, 0, {}, false, -1, -1});  // v is not sieved again
+    for (int ch : tr.children[v]) {
+      down[ch] = new_fid();
+      ops.push_back({kOpBuild, v, 0, {}, false, edge_col(path->edges[tr.pedge[ch]], v), down[ch]});
+    }
+  }
+  return SJ_OK;
+}
+
 using FinalHook = std::function<sj_status(int rel, const sj_rel_s* r, int slot)>;
 sj_status sieve_path_impl(sj_ctx* c, const sj_path* path, const sj_sieve_opts* opts, sj_rel* out_sieved,
                           sj_sieve_stats* stats, bool sync_end, const FinalHook* on_final = nullptr);
@@ -1005,6 +1073,17 @@ sj_status sieve_path_impl(sj_ctx* c, const sj_path* path, const sj_sieve_opts* o
 extern "C" sj_status sj_sieve_path(sj_ctx* c, const sj_path* path, const sj_sieve_opts* opts,
                                    sj_rel* out_sieved, sj_sieve_stats* stats) {
   return sieve_path_impl(c, path, opts, out_sieved, stats, true);
+}
+
+namespace {
+sj_status sieve_path_batch_impl(sj_ctx* c, int nq, const sj_path* paths, const sj_sieve_opts* opts,
+                                sj_rel* out_sieved, sj_sieve_stats* stats);
+}
+
+extern "C" sj_status sj_sieve_path_batch(sj_ctx* c, int nq, const sj_path* paths,
+                                         const sj_sieve_opts* opts, sj_rel* out_sieved,
+                                         sj_sieve_stats* stats) {
+  return sieve_path_batch_impl(c, nq, paths, opts, out_sieved, stats);
 }
 
 namespace {
@@ -1037,53 +1116,10 @@ sj_status sieve_path_impl(sj_ctx* c, const sj_path* path, const sj_sieve_opts* o
   // The schedule is planned first, then run: a sieve step knows which filters
   // are built from its output next (before that relation is sieved again) and
   // clears their words itself.  Filter ids index `fl`.
-  enum { kOpStep, kOpBuild, kOpFinal };
-  struct Op {
-    int type, rel, kind;                    // kind: step kind for statistics
-    std::vector<std::pair<int, int>> probes;  // (column, filter id)
-    bool pred;
-    int col, fid;                           // build: column and filter id
-  };
-  std::vector<Op> ops;
-  std::vector<sj_filter> fl;
-  std::vector<char> fl_given;               // handed-in leaf filter (not built here)
-  auto new_fid = [&]() { fl.push_back(nullptr); fl_given.push_back(0); return (int)fl.size() - 1; };
-  for (int i = 0; i < n; ++i)
-    if (has_pred(path, i)) ops.push_back({kOpStep, i, 0, {}, true, -1, -1});
-  if (o.passes == SJ_NO_SIEVE || n == 1)
-    for (int i = 0; i < n; ++i) ops.push_back({kOpFinal, i, 0, {}, false, -1, -1});
-  if (o.passes != SJ_NO_SIEVE && n > 1) {
-    std::vector<int> up(n, -1), down(n, -1);
-    if (o.passes == SJ_FWD_BWD) {
-      for (int v : tr.post) {
-        if (!tr.children[v].empty()) {
-          if ((int)tr.children[v].size() > SJ_MAX_PROBES)
-            return fail(c, SJ_EINVAL, "a relation has more than 4 children");
-          Op op{kOpStep, v, 1, {}, false, -1, -1};
-          for (int ch : tr.children[v]) op.probes.push_back({edge_col(path->edges[tr.pedge[ch]], v), up[ch]});
-          ops.push_back(op);
-        }
-        if (tr.parent[v] >= 0) {
-          up[v] = new_fid();
-          if (tr.children[v].empty() && o.leaf_filters && o.leaf_filters[v]) {
-            fl[up[v]] = o.leaf_filters[v];  // reused (Sec. 2.3); owned by the caller
-            fl_given[up[v]] = 1;
-          } else {
-            ops.push_back({kOpBuild, v, 0, {}, false, edge_col(path->edges[tr.pedge[v]], v), up[v]});
-          }
-        }
-      }
-    }
-    for (int v : tr.pre) {
-      if (tr.parent[v] >= 0)
-        ops.push_back({kOpStep, v, 2, {{edge_col(path->edges[tr.pedge[v]], v), down[v]}}, false, -1, -1});
-      ops.push_back({kOpFinal, v, 0, {}, false, -1, -1});  // v is not sieved again
-      for (int ch : tr.children[v]) {
-        down[ch] = new_fid();
-        ops.push_back({kOpBuild, v, 0, {}, false, edge_col(path->edges[tr.pedge[ch]], v), down[ch]});
-      }
-    }
-  }
+  PrunePlan plan;
+  SJ_TRY(plan_pruning(c, path, tr, o, &plan));
+  const std::vector<PruneOp>& ops = plan.ops;
+  std::vector<sj_filter> fl = plan.given;
 
   auto cleanup = [&]() {
     for (auto f : filters) free_filter(c, f);
@@ -1097,7 +1133,7 @@ sj_status sieve_path_impl(sj_ctx* c, const sj_path* path, const sj_sieve_opts* o
   std::vector<char> cleared(fl.size(), 0);
   sj_status st = SJ_OK;
   for (size_t q = 0; q < ops.size() && st == SJ_OK; ++q) {
-    const Op& op = ops[q];
+    const PruneOp& op = ops[q];
     const int i = op.rel;
     if (op.type == kOpFinal) {
       if (on_final) st = (*on_final)(i, rel_of(i), last_slot[i]);
@@ -1176,6 +1212,457 @@ sj_status sieve_path_impl(sj_ctx* c, const sj_path* path, const sj_sieve_opts* o
     for (int i = 0; i < n; ++i) stats->rows_final[i] = out_sieved[i]->nrows;
     stats->filter_bytes = filter_bytes;
   }
+  return SJ_OK;
+}
+
+// ------------------------------------------------------------ batched pruning
+// The pruning phases of many queries in lock step (the serving runtime's
+// batches).  Every sieve step and filter build of every query gets a level,
+// one more than the levels of what it reads: the step that produced its input
+// relation and the builds of the filters it probes.  The steps of one level,
+// over all queries, run as one k_sieve_batch launch and the builds of one
+// level as one k_bloom_build_batch launch, so a batch takes as many launches
+// as its longest schedule has levels instead of the sum over its queries.
+// Each query gets exactly the filters and sieved relations its own
+// sj_sieve_path computes: same schedule, same filter sizes, same order of
+// surviving rows.  All relation versions stay allocated until the call ends.
+struct BVer {
+  const sj_rel_s* in = nullptr;  // version 0: the caller's relation
+  sj_rel r = nullptr;            // later versions: a step's output
+  int step = -1;                 // producing step
+  int level = 0;
+  int64_t cap = 0;
+};
+struct BFilter {
+  sj_filter f = nullptr;
+  int q = -1, ver = -1, col = 0, level = 0;
+  bool given = false, cleared = false;
+};
+struct BStep {
+  int q, rel, kind, level, ver_in, ver_out;
+  bool pred;
+  int32_t lo, hi;
+  int pred_col;
+  std::vector<std::pair<int, int>> probes;  // (column, batch filter id)
+  std::vector<int> zero;                    // batch filter ids cleared by this step
+  int chunk_rows = 0;
+  int64_t nchunks = 0, chunk_g = 0;         // chunk_g: first chunk state of the call
+};
+
+sj_status sieve_path_batch_impl(sj_ctx* c, int nq, const sj_path* paths, const sj_sieve_opts* opts,
+                                sj_rel* out_sieved, sj_sieve_stats* stats) {
+  if (!c || nq < 0 || (nq > 0 && (!paths || !out_sieved))) return fail(c, SJ_EINVAL, "null argument");
+  if (nq == 0) return SJ_OK;
+  std::vector<BVer> vers;
+  std::vector<BFilter> bf;
+  std::vector<BStep> steps;
+  std::vector<std::vector<int>> final_ver(nq);
+  std::vector<sj_filter_params> qp(nq);
+  int maxL = 0;
+
+  // plan every query and give each operation its level
+  for (int q = 0; q < nq; ++q) {
+    const sj_path* path = &paths[q];
+    Tree tr;
+    SJ_TRY(validate_path(c, path, path->rels, &tr));
+    const int n = path->nrel;
+    for (int i = 0; i < n; ++i)
+      if (path->rels[i]->nrows < 0) return fail(c, SJ_EINVAL, "relation row count unknown");
+    sj_sieve_opts o{};
+    if (opts) o = opts[q];
+    qp[q] = norm_params(&o.filter);
+    SJ_TRY(check_params(c, qp[q]));
+    if (o.passes < SJ_FWD_BWD || o.passes > SJ_NO_SIEVE) return fail(c, SJ_EINVAL, "bad passes");
+    PrunePlan pl;
+    SJ_TRY(plan_pruning(c, path, tr, o, &pl));
+    std::vector<int> fid(pl.given.size(), -1), cur(n);
+    for (size_t k = 0; k < pl.given.size(); ++k) {
+      if (!pl.given[k]) continue;
+      BFilter b;
+      b.f = pl.given[k];
+      b.q = q;
+      b.given = true;
+      fid[k] = (int)bf.size();
+      bf.push_back(b);
+    }
+    for (int i = 0; i < n; ++i) {
+      BVer v;
+      v.in = path->rels[i];
+      v.cap = rel_cap(path->rels[i]);
+      cur[i] = (int)vers.size();
+      vers.push_back(v);
+    }
+    int nsteps_q = 0;
+    for (size_t u = 0; u < pl.ops.size(); ++u) {
+      const PruneOp& op = pl.ops[u];
+      const int i = op.rel;
+      if (op.type == kOpFinal) continue;
+      if (op.type == kOpBuild) {
+        if (fid[op.fid] < 0) {
+          fid[op.fid] = (int)bf.size();
+          bf.push_back(BFilter());
+        }
+        BFilter& b = bf[fid[op.fid]];
+        b.q = q;
+        b.ver = cur[i];
+        b.col = op.col;
+        b.level = vers[cur[i]].level + 1;
+        maxL = std::max(maxL, b.level);
+        continue;
+      }
+      if (++nsteps_q > SJ_MAX_STEPS) return fail(c, SJ_EINVAL, "too many sieve steps");
+      BStep st{};
+      st.q = q;
+      st.rel = i;
+      st.kind = op.kind;
+      st.ver_in = cur[i];
+      st.pred = op.pred;
+      st.pred_col = op.pred ? path->preds[i].col : -1;
+      st.lo = op.pred ? path->preds[i].lo : 0;
+      st.hi = op.pred ? path->preds[i].hi : 0;
+      st.level = vers[cur[i]].level + 1;
+      for (auto& pr : op.probes) {
+        st.probes.push_back({pr.first, fid[pr.second]});
+        st.level = std::max(st.level, bf[fid[pr.second]].level + 1);
+      }
+      // the filters built from this step's output before relation i is sieved again
+      for (size_t w = u + 1; w < pl.ops.size(); ++w) {
+        const PruneOp& nx = pl.ops[w];
+        if (nx.rel != i) continue;
+        if (nx.type == kOpStep) break;
+        if (nx.type != kOpBuild || (int)st.zero.size() == kMaxZero || fid[nx.fid] >= 0) continue;
+        fid[nx.fid] = (int)bf.size();
+        BFilter b;
+        b.cleared = true;
+        bf.push_back(b);
+        st.zero.push_back(fid[nx.fid]);
+      }
+      maxL = std::max(maxL, st.level);
+      BVer v;
+      v.step = (int)steps.size();
+      v.level = st.level;
+      v.cap = vers[cur[i]].cap;
+      st.ver_out = (int)vers.size();
+      vers.push_back(v);
+      cur[i] = st.ver_out;
+      steps.push_back(st);
+    }
+    final_ver[q] = cur;
+  }
+
+  // allocations: step outputs, one block for all built filters (the ones no
+  // step clears first, then the cleared ones), one block for the launch
+  // arguments and the per-step counts
+  void* fblock = nullptr;
+  size_t fblock_bytes = 0, fclear_bytes = 0;
+  void* ablock = nullptr;
+  size_t ablock_bytes = 0;
+  auto cleanup = [&]() {
+    for (auto& v : vers) free_rel(c, v.r);
+    for (auto& b : bf)
+      if (!b.given) delete b.f;
+    dfree(c, fblock, fblock_bytes);
+    dfree(c, ablock, ablock_bytes);
+  };
+  for (auto& st : steps) {
+    const BVer& vin = vers[st.ver_in];
+    const sj_rel_s* in = vin.r ? vin.r : vin.in;
+    vers[st.ver_out].r = new_rel(c, in->ncols, vin.cap);
+    if (!vers[st.ver_out].r) {
+      cleanup();
+      return fail(c, SJ_ENOMEM, "sieve output allocation failed");
+    }
+  }
+  std::vector<uint64_t> qfilter_bytes(nq, 0);
+  for (int pass = 0; pass < 2; ++pass) {
+    for (auto& b : bf) {
+      if (b.given || b.cleared != (pass == 1)) continue;
+      const sj_filter_params& p = qp[b.q];
+      uint64_t nbc = ((uint64_t)p.bits_per_key * (uint64_t)vers[b.ver].cap + 255) / 256;
+      if (nbc < 1) nbc = 1;
+      b.f = new sj_filter_s();
+      b.f->p = p;
+      b.f->nblocks_cap = nbc;
+      b.f->mem_bytes = fblock_bytes;  // offset until the block exists
+      fblock_bytes += kAlign + round_up(nbc * 32);
+      qfilter_bytes[b.q] += nbc * 32;
+    }
+    if (pass == 0) fclear_bytes = fblock_bytes;
+  }
+  if (fblock_bytes) {
+    fblock = dalloc(c, fblock_bytes);
+    if (!fblock) {
+      cleanup();
+      return fail(c, SJ_ENOMEM, "filter allocation failed");
+    }
+    for (auto& b : bf) {
+      if (b.given) continue;
+      uint8_t* base = static_cast<uint8_t*>(fblock) + b.f->mem_bytes;
+      b.f->mem = nullptr;  // part of the block
+      b.f->mem_bytes = 0;
+      b.f->hdr = reinterpret_cast<uint64_t*>(base);
+      b.f->words = reinterpret_cast<uint32_t*>(base + kAlign);
+    }
+  }
+
+  // per level: the steps and builds, their argument arrays and prefixes
+  std::vector<std::vector<int>> lsteps(maxL + 1), lbuilds(maxL + 1);
+  for (size_t s = 0; s < steps.size(); ++s) lsteps[steps[s].level].push_back((int)s);
+  for (size_t k = 0; k < bf.size(); ++k)
+    if (!bf[k].given) lbuilds[bf[k].level].push_back((int)k);
+  int64_t total_chunks = 0;
+  for (auto& st : steps) {
+    st.chunk_rows = sieve_chunk_rows(vers[st.ver_in].cap, c->num_sms);
+    st.nchunks = std::max<int64_t>(1, (vers[st.ver_in].cap + st.chunk_rows - 1) / st.chunk_rows);
+    st.chunk_g = total_chunks;
+    total_chunks += st.nchunks;
+  }
+  struct LevelOff { size_t sargs, schunk0, bargs, brow0; int64_t nchunks, nrows; int k_all; };
+  std::vector<LevelOff> lo(maxL + 1);
+  size_t off = 0;
+  auto take = [&](size_t bytes) { const size_t o = off; off = round_up(off + bytes, 16); return o; };
+  for (int L = 1; L <= maxL; ++L) {
+    lo[L].sargs = take(sizeof(SieveArgs) * lsteps[L].size());
+    lo[L].schunk0 = take(sizeof(int64_t) * (lsteps[L].size() + 1));
+    lo[L].bargs = take(sizeof(BloomBuildArgs) * lbuilds[L].size());
+    lo[L].brow0 = take(sizeof(int64_t) * (lbuilds[L].size() + 1));
+  }
+  const size_t args_bytes = off;
+  const size_t counts_off = take(sizeof(uint64_t) * std::max<size_t>(steps.size(), 1));
+  ablock_bytes = off;
+  ablock = dalloc(c, ablock_bytes);
+  if (!ablock) {
+    cleanup();
+    return fail(c, SJ_ENOMEM, "batch argument allocation failed");
+  }
+  uint8_t* dA = static_cast<uint8_t*>(ablock);
+  uint64_t* d_counts = reinterpret_cast<uint64_t*>(dA + counts_off);
+  // pinned staging: the arguments, then the counts read back
+  if (c->batch_pending) {
+    cudaStreamSynchronize(c->stream);
+    c->batch_pending = false;
+  }
+  if (c->h_batch_bytes < ablock_bytes) {
+    if (c->h_batch) cudaFreeHost(c->h_batch);
+    c->h_batch = nullptr;
+    c->h_batch_bytes = 0;
+    void* h = nullptr;
+    if (cudaHostAlloc(&h, round_up(ablock_bytes * 2), cudaHostAllocDefault) != cudaSuccess) {
+      cudaGetLastError();
+      cleanup();
+      return fail(c, SJ_ENOMEM, "pinned staging allocation failed");
+    }
+    c->h_batch = static_cast<uint8_t*>(h);
+    c->h_batch_bytes = round_up(ablock_bytes * 2);
+  }
+  uint8_t* hA = c->h_batch;
+  uint32_t* ticket = nullptr;
+  LookBack<1> lb;
+  sj_status st = scratch_for<1>(c, total_chunks, &ticket, &lb);
+  if (st != SJ_OK) {
+    cleanup();
+    return st;
+  }
+  auto rel_of_ver = [&](int v) -> const sj_rel_s* { return vers[v].r ? vers[v].r : vers[v].in; };
+  for (int L = 1; L <= maxL; ++L) {
+    SieveArgs* sa = reinterpret_cast<SieveArgs*>(hA + lo[L].sargs);
+    int64_t* c0 = reinterpret_cast<int64_t*>(hA + lo[L].schunk0);
+    int64_t acc = 0;
+    int k_all = -1;
+    for (size_t t = 0; t < lsteps[L].size(); ++t) {
+      const BStep& S = steps[lsteps[L][t]];
+      const sj_rel_s* in = rel_of_ver(S.ver_in);
+      const sj_rel_s* r = vers[S.ver_out].r;
+      SieveArgs& a = sa[t];
+      memset(&a, 0, sizeof(a));
+      if (S.pred) {
+        a.test[a.ntest].col = in->cols[S.pred_col];
+        a.test[a.ntest].is_pred = 1;
+        a.test[a.ntest].lo = S.lo;
+        a.test[a.ntest].hi = S.hi;
+        a.ntest++;
+      }
+      for (auto& pr : S.probes) {
+        a.test[a.ntest].col = in->cols[pr.first];
+        a.test[a.ntest].f = view(bf[pr.second].f);
+        a.ntest++;
+      }
+      const int vec_col = S.pred ? S.pred_col : (S.probes.empty() ? -1 : S.probes[0].first);
+      a.nout = in->ncols;
+      for (int j = 0; j < in->ncols; ++j) {
+        a.in[j] = in->cols[j];
+        a.out[j] = r->cols[j];
+        a.out_is_vec[j] = j == vec_col ? 1 : 0;
+      }
+      a.n_host = in->d_n ? 0 : in->nrows;
+      a.n_dev = in->d_n;
+      a.out_n = r->d_n;
+      a.out_n2 = d_counts + lsteps[L][t];
+      a.tile_counter = ticket;
+      a.lb = lb;
+      a.lb.st = lb.st + S.chunk_g;
+      a.fast_words_ok = 1;
+      if (!S.pred && !S.probes.empty() && bf[S.probes[0].second].f->nblocks_cap * 8 >= (1ull << 32))
+        a.fast_words_ok = 0;
+      for (int z : S.zero) {
+        a.zero_words[a.nzero] = bf[z].f->words;
+        a.zero_bpk[a.nzero] = bf[z].f->p.bits_per_key;
+        a.zero_cap_words[a.nzero] = bf[z].f->nblocks_cap * 8;
+        a.nzero++;
+      }
+      a.chunk_rows = S.chunk_rows;
+      c0[t] = acc;
+      acc += S.nchunks;
+      const bool fast = a.ntest == 1 && !a.test[0].is_pred && a.test[0].f.layout == 0 &&
+                        a.test[0].f.k >= 1 && a.test[0].f.k <= 4 && a.fast_words_ok;
+      const int kk = fast ? (int)a.test[0].f.k : 0;
+      k_all = (k_all < 0 || k_all == kk) ? kk : 0;
+    }
+    c0[lsteps[L].size()] = acc;
+    lo[L].nchunks = acc;
+    lo[L].k_all = k_all < 0 ? 0 : k_all;
+    BloomBuildArgs* ba = reinterpret_cast<BloomBuildArgs*>(hA + lo[L].bargs);
+    int64_t* r0 = reinterpret_cast<int64_t*>(hA + lo[L].brow0);
+    int64_t racc = 0;
+    for (size_t t = 0; t < lbuilds[L].size(); ++t) {
+      const BFilter& b = bf[lbuilds[L][t]];
+      const sj_rel_s* rel = rel_of_ver(b.ver);
+      BloomBuildArgs& a = ba[t];
+      memset(&a, 0, sizeof(a));
+      a.keys = rel->cols[b.col];
+      a.n_host = rel->d_n ? 0 : rel->nrows;
+      a.n_dev = rel->d_n;
+      a.hdr = b.f->hdr;
+      a.words = b.f->words;
+      a.nblocks_cap = b.f->nblocks_cap;
+      a.bits_per_key = b.f->p.bits_per_key;
+      a.k = b.f->p.k;
+      a.layout = b.f->p.layout;
+      a.seed = b.f->p.seed;
+      r0[t] = racc;
+      racc += std::max<int64_t>(1, vers[b.ver].cap);
+    }
+    r0[lbuilds[L].size()] = racc;
+    lo[L].nrows = racc;
+  }
+
+  // enqueue: clear the filters no step clears, copy the arguments, then two
+  // launches per level; one synchronisation at the end
+  const size_t p0 = c->prof.size();
+  struct LRec { int L; bool build; size_t idx; };
+  std::vector<LRec> recs;
+  if (fclear_bytes) {
+    cudaError_t e = cudaMemsetAsync(fblock, 0, fclear_bytes, c->stream);
+    if (e != cudaSuccess) {
+      cleanup();
+      return fail(c, SJ_ECUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
+    }
+  }
+  cudaError_t e = cudaMemcpyAsync(dA, hA, args_bytes, cudaMemcpyHostToDevice, c->stream);
+  if (e != cudaSuccess) {
+    cleanup();
+    return fail(c, SJ_ECUDA, std::string("cudaMemcpyAsync: ") + cudaGetErrorString(e));
+  }
+  c->h2d_bytes += (int64_t)args_bytes;
+  c->batch_pending = true;
+  for (int L = 1; L <= maxL && st == SJ_OK; ++L) {
+    if (!lbuilds[L].empty()) {
+      BuildBatchArgs b;
+      b.tasks = reinterpret_cast<const BloomBuildArgs*>(dA + lo[L].bargs);
+      b.row0 = reinterpret_cast<const int64_t*>(dA + lo[L].brow0);
+      b.ntask = (int)lbuilds[L].size();
+      const size_t before = c->prof.size();
+      {
+        Launch rec(c, SJ_K_BLOOM_BUILD, 0.0);
+        launch_bloom_build_batch(b, lo[L].nrows, c->num_sms, c->stream);
+      }
+      if (c->prof.size() > before) recs.push_back({L, true, before});
+      st = check_launch(c, "k_bloom_build_batch");
+    }
+    if (st == SJ_OK && !lsteps[L].empty()) {
+      SieveBatchArgs b;
+      b.tasks = reinterpret_cast<const SieveArgs*>(dA + lo[L].sargs);
+      b.chunk0 = reinterpret_cast<const int64_t*>(dA + lo[L].schunk0);
+      b.ntask = (int)lsteps[L].size();
+      b.ticket = ticket;
+      const size_t before = c->prof.size();
+      {
+        Launch rec(c, SJ_K_SIEVE, 0.0);
+        launch_sieve_batch(b, lo[L].nchunks, lo[L].k_all, c->stream);
+      }
+      if (c->prof.size() > before) recs.push_back({L, false, before});
+      st = check_launch(c, "k_sieve_batch");
+    }
+  }
+  uint64_t* h_counts = reinterpret_cast<uint64_t*>(hA + counts_off);
+  if (st == SJ_OK && !steps.empty()) {
+    e = cudaMemcpyAsync(h_counts, d_counts, sizeof(uint64_t) * steps.size(), cudaMemcpyDeviceToHost,
+                        c->stream);
+    if (e != cudaSuccess) st = fail(c, SJ_ECUDA, std::string("cudaMemcpyAsync: ") + cudaGetErrorString(e));
+    c->d2h_bytes += (int64_t)(sizeof(uint64_t) * steps.size());
+  }
+  if (st == SJ_OK) st = sync_read(c);
+  if (st != SJ_OK) {
+    cudaStreamSynchronize(c->stream);
+    c->batch_pending = false;
+    cleanup();
+    return st;
+  }
+  c->batch_pending = false;
+  auto rows_of_ver = [&](int v) -> int64_t {
+    return vers[v].step >= 0 ? (int64_t)h_counts[vers[v].step] : vers[v].in->nrows;
+  };
+  // algorithmic bytes of the profiled launches, as for the one-query launches
+  for (auto& R : recs) {
+    double bytes = 0;
+    if (R.build) {
+      for (int k : lbuilds[R.L])
+        bytes += (4.0 + bf[k].f->p.bits_per_key / 8.0) * (double)rows_of_ver(bf[k].ver);
+    } else {
+      for (int s : lsteps[R.L]) {
+        const BStep& S = steps[s];
+        const int ncols = rel_of_ver(S.ver_in)->ncols;
+        bytes += 4.0 * (double)rows_of_ver(S.ver_in) +
+                 (4.0 * (ncols - 1) + 4.0 * ncols) * (double)h_counts[s];
+      }
+    }
+    c->prof[R.idx].bytes = bytes;
+  }
+  prof_resolve(c, p0);
+  // hand out the final versions; free the rest
+  std::vector<char> is_final(vers.size(), 0);
+  for (int q = 0; q < nq; ++q)
+    for (int i = 0; i < paths[q].nrel; ++i) is_final[final_ver[q][i]] = 1;
+  for (size_t v = 0; v < vers.size(); ++v) {
+    if (!vers[v].r) continue;
+    vers[v].r->nrows = rows_of_ver((int)v);
+    if (!is_final[v]) free_rel(c, vers[v].r);
+    vers[v].r = is_final[v] ? vers[v].r : nullptr;
+  }
+  for (int q = 0; q < nq; ++q) {
+    for (int i = 0; i < paths[q].nrel; ++i) {
+      const int v = final_ver[q][i];
+      out_sieved[(size_t)q * SJ_MAX_REL + i] = vers[v].r ? vers[v].r : view_of(vers[v].in);
+    }
+    if (stats) {
+      sj_sieve_stats& S = stats[q];
+      memset(&S, 0, sizeof(S));
+      for (const BStep& b : steps) {
+        if (b.q != q) continue;
+        auto& x = S.step[S.nsteps++];
+        x.kind = b.kind;
+        x.rel = b.rel;
+        x.rows_in = rows_of_ver(b.ver_in);
+        x.rows_out = rows_of_ver(b.ver_out);
+      }
+      for (int i = 0; i < paths[q].nrel; ++i) S.rows_final[i] = rows_of_ver(final_ver[q][i]);
+      S.filter_bytes = qfilter_bytes[q];
+    }
+  }
+  for (auto& b : bf)
+    if (!b.given) delete b.f;
+  dfree(c, fblock, fblock_bytes);
+  dfree(c, ablock, ablock_bytes);
   return SJ_OK;
 }
 

@@ -645,20 +645,27 @@ __device__ __forceinline__ uint64_t ck_list_and_write(const SieveArgs& a, int64_
   return prefix;
 }
 
+// Shared memory of one chunk of the chunked sieve.
+struct CkSmem {
+  static constexpr int kMaxTiles = kCkMaxRows / kCkTileRows;
+  __align__(16) uint32_t bits[kMaxTiles * 8];
+  uint32_t toff[kMaxTiles + 1];
+  uint16_t list[kCkList];
+  Vec<1> warp[kCkThreads / 32];
+  uint64_t red[kCkThreads / 32];
+  int stop;
+};
+
+// Chunk t of the sieve step `a` (steps 1-6 of k_sieve_chunk); every thread of
+// the CTA calls it.
 template <int K>
-__global__ void __launch_bounds__(kCkThreads, K > 0 ? kCkMinBlocks : 4) k_sieve_chunk(SieveArgs a) {
-  constexpr int kMaxTiles = kCkMaxRows / kCkTileRows;
-  __shared__ __align__(16) uint32_t s_bits[kMaxTiles * 8];
-  __shared__ uint32_t s_toff[kMaxTiles + 1];
-  __shared__ uint16_t s_list[kCkList];
-  __shared__ Vec<1> s_warp[kCkThreads / 32];
-  __shared__ uint64_t s_red[kCkThreads / 32];
-  __shared__ uint32_t s_ticket;
-  __shared__ int s_stop;
+__device__ __forceinline__ void ck_run_chunk(const SieveArgs& a, uint32_t t, CkSmem& sm) {
+  uint32_t* s_bits = sm.bits;
+  uint32_t* s_toff = sm.toff;
+  uint16_t* s_list = sm.list;
+  Vec<1>* s_warp = sm.warp;
+  uint64_t* s_red = sm.red;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) s_ticket = draw_ticket(a.tile_counter);
-  __syncthreads();
-  const uint32_t t = s_ticket;
   const int64_t n = a.n_dev ? (int64_t)(*a.n_dev) : a.n_host;
   const int64_t C = a.chunk_rows;
   const int64_t nchunks = (n + C - 1) / C;
@@ -742,7 +749,7 @@ __global__ void __launch_bounds__(kCkThreads, K > 0 ? kCkMinBlocks : 4) k_sieve_
   const uint64_t prefix = ck_list_and_write(a, cbase, ntile, total, s_bits, s_toff, s_list, [&]() {
     uint64_t p = 0;
     if (t > 0) {
-      p = ck_lookback(a.lb, t, &s_stop, s_red);
+      p = ck_lookback(a.lb, t, &sm.stop, s_red);
       if (tid == 0) {
         Vec<1> inc;
         inc.v[0] = p + total;
@@ -758,6 +765,46 @@ __global__ void __launch_bounds__(kCkThreads, K > 0 ? kCkMinBlocks : 4) k_sieve_
 
   // 6. clear the next filters' words
   ck_zero(a, prefix, prefix + total, t == 0);
+}
+
+template <int K>
+__global__ void __launch_bounds__(kCkThreads, K > 0 ? kCkMinBlocks : 4) k_sieve_chunk(SieveArgs a) {
+  __shared__ CkSmem sm;
+  __shared__ uint32_t s_ticket;
+  if (threadIdx.x == 0) s_ticket = draw_ticket(a.tile_counter);
+  __syncthreads();
+  ck_run_chunk<K>(a, s_ticket, sm);
+}
+
+// Many sieve steps in one launch (the serving runtime's batches): task i's
+// chunks are the global tickets [chunk0[i], chunk0[i + 1]), numbered from the
+// tasks' row bounds; a CTA draws a global ticket, finds its task by binary
+// search, copies the task's arguments to shared memory and runs that chunk
+// of that task.  A chunk waits (look-back) only on earlier chunks of its own
+// task, which hold earlier tickets, so the tasks run as one stream of work.
+template <int K>
+__global__ void __launch_bounds__(kCkThreads, 4) k_sieve_batch(SieveBatchArgs b) {
+  __shared__ CkSmem sm;
+  __shared__ SieveArgs s_args;
+  __shared__ uint32_t s_ticket;
+  __shared__ int s_task;
+  if (threadIdx.x == 0) {
+    const uint32_t g = draw_ticket(b.ticket);
+    int lo = 0, hi = b.ntask - 1;  // last task whose first chunk is <= g
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if ((uint64_t)__ldg(b.chunk0 + mid) <= g) lo = mid;
+      else hi = mid - 1;
+    }
+    s_task = lo;
+    s_ticket = g - (uint32_t)__ldg(b.chunk0 + lo);
+  }
+  __syncthreads();
+  const uint32_t* src = reinterpret_cast<const uint32_t*>(b.tasks + s_task);
+  uint32_t* dst = reinterpret_cast<uint32_t*>(&s_args);
+  for (int i = threadIdx.x; i < (int)(sizeof(SieveArgs) / 4); i += kCkThreads) dst[i] = __ldg(src + i);
+  __syncthreads();
+  ck_run_chunk<K>(s_args, s_ticket, sm);
 }
 
 // ---------------------------------------------------------------- insert maintenance
@@ -817,6 +864,39 @@ __global__ void __launch_bounds__(kBlock) k_insert_or(InsertArgs a) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride)
     if (a.status[i] == 2) filter_or_key(a.words, nb, a.f.k, a.f.layout, a.f.seed, __ldg(a.keys + i));
+}
+
+// ---------------------------------------------------------------- batched Bloom build
+// Many filter builds in one launch: task i's rows are the global rows
+// [row0[i], row0[i + 1]) (from the tasks' row bounds); each thread takes rows
+// by grid stride, finds the task by binary search and ORs the key's bits in
+// (any layout).  The row with local index 0 writes the task's header.
+__global__ void __launch_bounds__(kBlock) k_bloom_build_batch(BuildBatchArgs b) {
+  const int64_t total = __ldg(b.row0 + b.ntask);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int task = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
+    if (__ldg(b.row0 + task + 1) <= i || __ldg(b.row0 + task) > i) {
+      int lo = 0, hi = b.ntask - 1;  // last task starting at or before i
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(b.row0 + mid) <= i) lo = mid;
+        else hi = mid - 1;
+      }
+      task = lo;
+    }
+    const BloomBuildArgs& t = b.tasks[task];
+    const int64_t r = i - __ldg(b.row0 + task);
+    const int64_t n = t.n_dev ? (int64_t)__ldg(t.n_dev) : t.n_host;
+    uint64_t nb = ((uint64_t)t.bits_per_key * (uint64_t)n + 255ull) / 256ull;
+    if (nb < 1) nb = 1;
+    if (nb > t.nblocks_cap) nb = t.nblocks_cap;
+    if (r == 0) {
+      t.hdr[0] = nb;
+      t.hdr[1] = (uint64_t)n;
+    }
+    if (r < n) filter_or_key(t.words, nb, t.k, t.layout, t.seed, __ldg(t.keys + r));
+  }
 }
 
 // ---------------------------------------------------------------- group offsets
@@ -1634,6 +1714,21 @@ void launch_filter_insert(const InsertArgs& a, int num_sms, cudaStream_t s) {
   const int g = host_grid(a.n, kBlock * 4, num_sms * 8);
   k_insert_check<<<g, kBlock, 0, s>>>(a);
   k_insert_or<<<g, kBlock, 0, s>>>(a);
+}
+
+void launch_bloom_build_batch(const BuildBatchArgs& b, int64_t total_rows, int num_sms, cudaStream_t s) {
+  launch_hi(k_bloom_build_batch, (unsigned)host_grid(total_rows, kBlock * 4, num_sms * 8), kBlock, s, b);
+}
+
+void launch_sieve_batch(const SieveBatchArgs& b, int64_t total_chunks, int k_all, cudaStream_t s) {
+  const unsigned g = (unsigned)(total_chunks > 0 ? total_chunks : 1);
+  switch (k_all) {
+    case 1: launch_hi(k_sieve_batch<1>, g, kCkThreads, s, b); break;
+    case 2: launch_hi(k_sieve_batch<2>, g, kCkThreads, s, b); break;
+    case 3: launch_hi(k_sieve_batch<3>, g, kCkThreads, s, b); break;
+    case 4: launch_hi(k_sieve_batch<4>, g, kCkThreads, s, b); break;
+    default: launch_hi(k_sieve_batch<0>, g, kCkThreads, s, b); break;
+  }
 }
 
 void launch_group_offsets(const GroupOffArgs& a, int64_t n_upper, int num_sms, cudaStream_t s) {

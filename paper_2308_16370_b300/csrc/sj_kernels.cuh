@@ -88,6 +88,30 @@ void launch_sieve_chunk(const SieveArgs& a, int64_t n_upper, int num_sms, cudaSt
 
 
 
+// Many sieve steps in one launch (k_sieve_batch): tasks[i] is a full sieve
+// step (chunk_rows, lb.st pointing at its own chunk states; tile_counter is
+// not used), chunk0[i] the global ticket of its first chunk (chunk0[ntask] =
+// the total), both in device memory; `ticket` is 0 at launch and reset by the
+// kernel.  k_all: the k of every task when all are single register-blocked
+// filter tests with k <= 4 and fewer than 2^32 words, else 0.
+struct SieveBatchArgs {
+  const SieveArgs* tasks;
+  const int64_t* chunk0;
+  int ntask;
+  uint32_t* ticket;
+};
+void launch_sieve_batch(const SieveBatchArgs& b, int64_t total_chunks, int k_all, cudaStream_t s);
+
+// Many filter builds in one launch (k_bloom_build_batch): tasks[i] and
+// row0[i] (the global index of its first row; row0[ntask] = the total of the
+// tasks' row bounds) in device memory.  Words must be cleared beforehand.
+struct BuildBatchArgs {
+  const BloomBuildArgs* tasks;
+  const int64_t* row0;
+  int ntask;
+};
+void launch_bloom_build_batch(const BuildBatchArgs& b, int64_t total_rows, int num_sms, cudaStream_t s);
+
 // ------------------------------------------------------------------ insert maintenance
 // Sec. 2.4: new tuples of a relation whose filter exists.  k_insert_check
 // classifies every row against the filter as it was before the call (gated by

@@ -8,6 +8,11 @@
 // whole budget runs alone).  Cached filters are built once, on the stream of
 // the worker that first needs them; other workers order their use after the
 // build with an event, so no worker waits on the host for another's GPU work.
+// In batch mode a free worker takes up to `batch` queued queries that fit the
+// budget together and prunes them with one sj_sieve_path_batch call (two
+// launches per schedule level for the whole group), then runs each query's
+// join over its pruned relations (sj_sieve_join with SJ_NO_SIEVE and no
+// predicates, which were applied while pruning).
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -170,10 +175,90 @@ void run_query(sj_server* s, int w, const Pending& p, sj_completion* c) {
   c->sum = res.sum;
 }
 
+// Hand a finished query to the pollers.
+void deliver(sj_server* s, sj_completion c) {
+  c.done_ms = s->now_ms();
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->done.push_back(c);
+    s->st.completed++;
+    if (c.status != SJ_OK) s->st.failed++;
+  }
+  s->cv_done.notify_all();
+}
+
+// Batch mode: prune the group in one call, then join each query over its
+// pruned relations.  If the batched call fails (out of memory, say), every
+// query of the group runs alone instead.  Each query is delivered as soon as
+// its join is done.
+void run_group(sj_server* s, int w, const std::vector<Pending>& ps, std::vector<sj_completion>* cs) {
+  const int nq = (int)ps.size();
+  sj_ctx* ctx = s->ctxs[w];
+  std::vector<sj_rel> rels((size_t)nq * SJ_MAX_REL, nullptr);
+  std::vector<sj_filter> leaf((size_t)nq * SJ_MAX_REL, nullptr);
+  std::vector<sj_path> paths(nq);
+  std::vector<sj_sieve_opts> opts(nq);
+  for (int k = 0; k < nq; ++k) {
+    const sj_query& q = ps[k].q;
+    sj_rel* r = &rels[(size_t)k * SJ_MAX_REL];
+    for (int i = 0; i < q.nrel; ++i) r[i] = s->rels[q.rel[i]];
+    paths[k].nrel = q.nrel;
+    paths[k].root = q.root;
+    paths[k].rels = r;
+    paths[k].edges = q.edges;
+    paths[k].preds = q.preds;
+    (*cs)[k].cache_hits = 0;
+    sj_filter* lf = &leaf[(size_t)k * SJ_MAX_REL];
+    if (s->opts.cache_filters) {
+      const int root = q.root < 0 ? q.nrel - 1 : q.root;
+      for (int v : leaves_of(q, root)) {
+        bool hit = false;
+        lf[v] = cached_filter(s, w, q.rel[v], leaf_col(q, v), q.preds[v], &hit);
+        (*cs)[k].cache_hits += hit ? 1 : 0;
+      }
+    }
+    opts[k] = sj_sieve_opts{};
+    opts[k].passes = s->opts.passes;
+    opts[k].filter = s->opts.filter;
+    opts[k].leaf_filters = s->opts.cache_filters ? lf : nullptr;
+  }
+  std::vector<sj_rel> sieved((size_t)nq * SJ_MAX_REL, nullptr);
+  if (sj_sieve_path_batch(ctx, nq, paths.data(), opts.data(), sieved.data(), nullptr) != SJ_OK) {
+    for (int k = 0; k < nq; ++k) {
+      run_query(s, w, ps[k], &(*cs)[k]);
+      deliver(s, (*cs)[k]);
+    }
+    return;
+  }
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->st.batches++;
+    if (nq > s->st.peak_batch) s->st.peak_batch = nq;
+  }
+  for (int k = 0; k < nq; ++k) {
+    const sj_query& q = ps[k].q;
+    sj_path jp = paths[k];
+    jp.rels = &sieved[(size_t)k * SJ_MAX_REL];
+    jp.preds = nullptr;
+    sj_sieve_opts o{};
+    o.passes = SJ_NO_SIEVE;
+    o.filter = s->opts.filter;
+    sj_result res{};
+    const sj_status st = sj_sieve_join(ctx, &jp, &o, SJ_COUNT_SUM, q.nterms, q.terms, &res, nullptr);
+    (*cs)[k].status = st;
+    (*cs)[k].count = res.count;
+    (*cs)[k].sum = res.sum;
+    for (int i = 0; i < q.nrel; ++i) sj_free_rel(ctx, jp.rels[i]);
+    deliver(s, (*cs)[k]);
+  }
+}
+
 void worker(sj_server* s, int w) {
   cudaSetDevice(s->opts.device);
+  const int batch = s->opts.batch > 1 ? s->opts.batch : 1;
   while (true) {
-    Pending p;
+    std::vector<Pending> ps;
+    uint64_t bytes = 0;
     {
       std::unique_lock<std::mutex> lk(s->mu);
       while (true) {
@@ -185,28 +270,39 @@ void worker(sj_server* s, int w) {
         }
         s->cv_work.wait_for(lk, std::chrono::milliseconds(50));
       }
-      p = s->queue.front();
-      s->queue.pop_front();
-      s->inflight_bytes += p.est_bytes;
-      s->running++;
+      // the head of the queue, then (batch mode) the queries behind it that
+      // fit the budget next to it, in arrival order
+      while (!s->queue.empty() && (int)ps.size() < batch) {
+        const uint64_t need = s->queue.front().est_bytes;
+        if (!ps.empty() && s->inflight_bytes + bytes + need > s->opts.hbm_budget) break;
+        ps.push_back(s->queue.front());
+        s->queue.pop_front();
+        bytes += need;
+      }
+      s->inflight_bytes += bytes;
+      s->running += (int)ps.size();
       if (s->inflight_bytes > s->st.peak_inflight_bytes) s->st.peak_inflight_bytes = s->inflight_bytes;
       if (s->running > s->st.peak_concurrency) s->st.peak_concurrency = s->running;
     }
-    sj_completion c{};
-    c.ticket = p.ticket;
-    c.submit_ms = p.submit_ms;
-    c.start_ms = s->now_ms();
-    run_query(s, w, p, &c);
-    c.done_ms = s->now_ms();
+    std::vector<sj_completion> cs(ps.size());
+    const double start = s->now_ms();
+    for (size_t k = 0; k < ps.size(); ++k) {
+      cs[k] = sj_completion{};
+      cs[k].ticket = ps[k].ticket;
+      cs[k].submit_ms = ps[k].submit_ms;
+      cs[k].start_ms = start;
+    }
+    if (batch > 1) {
+      run_group(s, w, ps, &cs);
+    } else {
+      run_query(s, w, ps[0], &cs[0]);
+      deliver(s, cs[0]);
+    }
     {
       std::lock_guard<std::mutex> lk(s->mu);
-      s->inflight_bytes -= p.est_bytes;
-      s->running--;
-      s->done.push_back(c);
-      s->st.completed++;
-      if (c.status != SJ_OK) s->st.failed++;
+      s->inflight_bytes -= bytes;
+      s->running -= (int)ps.size();
     }
-    s->cv_done.notify_all();
     s->cv_work.notify_all();
   }
 }
@@ -221,6 +317,7 @@ sj_status sj_server_create(sj_server** out, const sj_server_opts* opts) {
   s->opts = *opts;
   if (s->opts.nslots <= 0) s->opts.nslots = 4;
   if (s->opts.nslots > 64) s->opts.nslots = 64;
+  if (s->opts.batch > 1024) s->opts.batch = 1024;
   s->t0 = Clock::now();
   if (cudaSetDevice(s->opts.device) != cudaSuccess) {
     delete s;

@@ -31,8 +31,8 @@ def workload_of(pool_np, q):
             "root": q["root"], "sum": q["sum"]}
 
 
-def serve(dev_pool, queries, nslots, budget=0, cache=True, sequential=False):
-    with sj.Server(nslots=nslots, hbm_budget=budget, cache_filters=cache) as srv:
+def serve(dev_pool, queries, nslots, budget=0, cache=True, sequential=False, batch=0):
+    with sj.Server(nslots=nslots, hbm_budget=budget, cache_filters=cache, batch=batch) as srv:
         ids = [srv.add_relation(cols) for cols in dev_pool]
         out = {}
         if sequential:
@@ -66,6 +66,36 @@ def test_mix_equals_alone_and_oracle(pool):
         exp = oracle.agg_propagation(workload_of(pool_np, q))
         assert (m["count"], m["sum"]) == (exp["count"], exp["sum"])
         assert m["submit_ms"] <= m["start_ms"] <= m["done_ms"]
+
+
+@pytest.mark.parametrize("cache", [True, False])
+def test_batch_mode_mix_equals_alone_and_oracle(pool, cache):
+    """Batch mode (pruning of up to 8 queued queries in one batched call):
+    every result equals the query run alone and the oracle."""
+    pool_np, dev = pool
+    qs = inputs.serving_queries([len(r[0]) for r in pool_np], 80, domain=DOMAIN, max_len=6,
+                                ntemplates=3, seed=23)
+    mixed, st = serve(dev, qs, nslots=2, cache=cache, batch=8)
+    alone, _ = serve(dev, qs, nslots=1, cache=False, sequential=True)
+    assert st["completed"] == len(qs) and st["failed"] == 0
+    assert st["batches"] > 0 and st["peak_batch"] > 1
+    for q, m, a in zip(qs, mixed, alone):
+        assert m["status"] == 0
+        assert (m["count"], m["sum"]) == (a["count"], a["sum"])
+        exp = oracle.agg_propagation(workload_of(pool_np, q))
+        assert (m["count"], m["sum"]) == (exp["count"], exp["sum"])
+        assert m["submit_ms"] <= m["start_ms"] <= m["done_ms"]
+
+
+def test_batch_mode_tiny_budget_takes_one_query_per_batch(pool):
+    pool_np, dev = pool
+    qs = inputs.serving_queries([len(r[0]) for r in pool_np], 10, domain=DOMAIN, max_len=4,
+                                ntemplates=2, seed=24)
+    res, st = serve(dev, qs, nslots=2, budget=1, batch=8)
+    assert st["peak_concurrency"] == 1 and st["peak_batch"] <= 1
+    for q, r in zip(qs, res):
+        exp = oracle.agg_propagation(workload_of(pool_np, q))
+        assert (r["count"], r["sum"]) == (exp["count"], exp["sum"])
 
 
 def test_tiny_budget_admits_one_at_a_time(pool):
