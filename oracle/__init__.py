@@ -18,6 +18,8 @@ Contents, each following the passage named in its docstring:
 * ``nested_loop``           -- brute-force enumeration of the same join.
 * ``agg_propagation``       -- a second exact method: per-key (count, sum)
   messages pushed toward the root of the join tree (Yannakakis-style counting).
+* ``chain_agg``             -- the same counting for many chain queries over one
+  relation pool, with dense per-key messages in C (checks served results).
 
 Parity status: every function here is pinned by the CPU tests in
 ``tests/test_oracle_pins.py`` (brute force, closed forms, invariants and
@@ -81,6 +83,8 @@ def _load():
         lib.orc_nested_loop.restype = ctypes.c_int
         lib.orc_nested_loop.argtypes = [ctypes.c_int, P, P, P, ctypes.c_int, P, P,
                                         ctypes.c_int, P, P]
+        lib.orc_chain_agg.restype = ctypes.c_int
+        lib.orc_chain_agg.argtypes = [ctypes.c_int, P, P, P, P, P, P, P, i64, P, P]
         _lib = lib
     return _lib
 
@@ -525,6 +529,68 @@ def agg_propagation(w: dict, rels=None, presieved: bool = False):
         np.add.at(CF, inv, cf)
         msgs[v] = (K, C, S, CF)
     raise AssertionError("unreachable")
+
+
+def chain_agg(pool, queries, domain: int):
+    """COUNT(*) and SUM(first.x + last.y) of chain queries over a pool of
+    two-column relations (x, y), the same counting as ``agg_propagation``
+    with per-key messages held densely over the keys [0, domain) (C, over the
+    oracle's threads, one query per thread at a time).
+
+    A query is a dict with ``rels`` (pool indices r_0 .. r_k, joined on
+    r_i.y = r_{i+1}.x as ``edges`` (i, 1, i + 1, 0) say), ``preds`` (a range
+    (0, lo, hi) on r_0.x, or None; nothing on the others) and ``sum`` =
+    [(0, 0, 0), (k, 1, 0)].  Anything else raises ValueError.  Returns one
+    {"count", "sum"} per query, both modulo 2^64."""
+    pool_x = [np.ascontiguousarray(r[0], dtype=np.int32) for r in pool]
+    pool_y = [np.ascontiguousarray(r[1], dtype=np.int32) for r in pool]
+    for x, y in zip(pool_x, pool_y):
+        if len(x) != len(y):
+            raise ValueError("pool relations need two columns of equal length")
+        for c in (x, y):
+            if len(c) and (int(c.min()) < 0 or int(c.max()) >= domain):
+                raise ValueError("pool key outside [0, domain)")
+    qoff, qrel, qlo, qhi = [0], [], [], []
+    for q in queries:
+        rels = list(q["rels"])
+        k = len(rels) - 1
+        if k < 0 or any(r < 0 or r >= len(pool) for r in rels):
+            raise ValueError("bad relation index")
+        if [tuple(e) for e in q["edges"]] != [(i, 1, i + 1, 0) for i in range(k)]:
+            raise ValueError("not a chain on r_i.y = r_{i+1}.x")
+        preds = q.get("preds") or [None] * (k + 1)
+        if any(p is not None for p in preds[1:]):
+            raise ValueError("predicates only on r_0")
+        p0 = preds[0]
+        if p0 is not None and p0[0] != 0:
+            raise ValueError("predicate only on r_0.x")
+        if [tuple(t) for t in q["sum"]] != [(0, 0, 0), (k, 1, 0)]:
+            raise ValueError("SUM terms must be r_0.x and r_k.y")
+        # no predicate: [0, domain) lies inside [-2^31, 2^31 - 1)
+        lo, hi = (int(p0[1]), int(p0[2])) if p0 is not None else (-(1 << 31), (1 << 31) - 1)
+        qrel += rels
+        qoff.append(len(qrel))
+        qlo.append(lo)
+        qhi.append(hi)
+    nq = len(queries)
+    if nq == 0:
+        return []
+    if not 0 < domain < (1 << 31):
+        raise ValueError("domain must be in 1 .. 2^31 - 1")
+    lib = _load()
+    qoff = np.asarray(qoff, dtype=np.int32)
+    qrel = np.asarray(qrel, dtype=np.int32)
+    qlo = np.asarray(qlo, dtype=np.int32)
+    qhi = np.asarray(qhi, dtype=np.int32)
+    pool_n = np.asarray([len(x) for x in pool_x], dtype=np.int64)
+    px = np.asarray([x.ctypes.data for x in pool_x], dtype=np.uint64)
+    py = np.asarray([y.ctypes.data for y in pool_y], dtype=np.uint64)
+    cnt = np.zeros(nq, dtype=np.uint64)
+    tot = np.zeros(nq, dtype=np.uint64)
+    if lib.orc_chain_agg(nq, _ptr(qoff), _ptr(qrel), _ptr(qlo), _ptr(qhi), _ptr(pool_n), _ptr(px),
+                         _ptr(py), int(domain), _ptr(cnt), _ptr(tot)):
+        raise MemoryError("orc_chain_agg: message buffers")
+    return [{"count": int(c), "sum": int(t)} for c, t in zip(cnt, tot)]
 
 
 def semijoin_reduction(w: dict, rels=None):

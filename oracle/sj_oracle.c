@@ -13,11 +13,14 @@
  *
  *   - a chained-bucket binary hash join level (pairs of matching rows, and the
  *     aggregate form used at the last level), whose probe can be split over
- *     threads (orc_set_threads) with the same results, and
+ *     threads (orc_set_threads) with the same results,
  *   - a nested-loop enumeration of a whole tree-shaped join (the brute force
- *     used on tiny inputs).
+ *     used on tiny inputs), and
+ *   - the per-key (count, sum) message counting of chain queries over one
+ *     relation pool, with dense messages (checks many served results).
  *
- * COUNT is kept in 128 bits so overflow of 2^63 can be reported; SUM is the
+ * COUNT is kept in 128 bits so overflow of 2^63 can be reported (the chain
+ * counting keeps it modulo 2^64); SUM is the
  * int64 sum taken modulo 2^64 (two's complement wrap), which is order-free.
  */
 #include <pthread.h>
@@ -265,4 +268,119 @@ int orc_nested_loop(int nrel, const int64_t *nrows, const int32_t *const *cols,
     out[1] = (uint64_t)(s.count >> 64);
     out[2] = s.sum;
     return 0;
+}
+
+/* ---------------- chain aggregate of many queries over one pool ------------
+ *
+ * The counting of agg_propagation (per-key (count, sum) messages pushed toward
+ * relation 0 of the join tree; (c, s) (x) (c', s') = (c c', s c' + s' c))
+ * restricted to one query family and with the messages held densely over the
+ * key domain: query q joins pool relations r_0 .. r_k (two columns, x = 0 and
+ * y = 1) on r_i.y = r_{i+1}.x, keeps the rows of r_0 with lo <= x < hi and
+ * returns COUNT(*) and SUM(r_0.x + r_k.y), both modulo 2^64.  Every key must
+ * lie in [0, domain).  The queries are taken one at a time by the oracle's
+ * threads (orc_set_threads); each query is computed the same way by any
+ * thread, so the results do not depend on the thread count.
+ */
+typedef struct { uint64_t c, s; } cs_pair;
+
+typedef struct {
+    int nq;
+    const int32_t *qoff, *qrel, *qlo, *qhi;
+    const int64_t *pool_n;
+    const int32_t *const *pool_x, *const *pool_y;
+    int64_t domain;
+    uint64_t *out_count, *out_sum;
+    int64_t next;   /* next query to take (atomic) */
+    int failed;
+} chain_job;
+
+/* Zero a message written by relation r: its x positions, or the whole
+ * buffer when that is cheaper. */
+static void chain_clear(const chain_job *J, int r, cs_pair *m) {
+    const int64_t n = J->pool_n[r];
+    if (n > J->domain / 4) { memset(m, 0, sizeof(cs_pair) * (size_t)J->domain); return; }
+    const int32_t *x = J->pool_x[r];
+    for (int64_t i = 0; i < n; ++i) { m[x[i]].c = 0; m[x[i]].s = 0; }
+}
+
+/* One query; both buffers are all zero on entry and on return. */
+static void chain_one(const chain_job *J, int q, cs_pair *cur, cs_pair *nxt) {
+    const int32_t *rel = J->qrel + J->qoff[q];
+    const int k = J->qoff[q + 1] - J->qoff[q] - 1;
+    const int32_t lo = J->qlo[q], hi = J->qhi[q];
+    uint64_t count = 0, sum = 0;
+    if (k == 0) {
+        const int32_t *x = J->pool_x[rel[0]], *y = J->pool_y[rel[0]];
+        for (int64_t i = 0; i < J->pool_n[rel[0]]; ++i)
+            if (x[i] >= lo && x[i] < hi) { count += 1; sum += (uint64_t)(int64_t)x[i] + (uint64_t)(int64_t)y[i]; }
+        J->out_count[q] = count;
+        J->out_sum[q] = sum;
+        return;
+    }
+    /* the message of r_k to r_{k-1}: per x, (rows, SUM of y) */
+    {
+        const int32_t *x = J->pool_x[rel[k]], *y = J->pool_y[rel[k]];
+        for (int64_t i = 0; i < J->pool_n[rel[k]]; ++i) {
+            cur[x[i]].c += 1;
+            cur[x[i]].s += (uint64_t)(int64_t)y[i];
+        }
+    }
+    /* middle relations: a row's pair is its child's message at y (no term of
+     * its own); the message to the parent adds the rows' pairs per x */
+    for (int j = k - 1; j >= 1; --j) {
+        const int32_t *x = J->pool_x[rel[j]], *y = J->pool_y[rel[j]];
+        for (int64_t i = 0; i < J->pool_n[rel[j]]; ++i) {
+            const cs_pair m = cur[y[i]];
+            nxt[x[i]].c += m.c;
+            nxt[x[i]].s += m.s;
+        }
+        chain_clear(J, rel[j + 1], cur);
+        cs_pair *t = cur; cur = nxt; nxt = t;
+    }
+    /* r_0: the predicate, then (1, x) (x) message at y */
+    {
+        const int32_t *x = J->pool_x[rel[0]], *y = J->pool_y[rel[0]];
+        for (int64_t i = 0; i < J->pool_n[rel[0]]; ++i) {
+            if (x[i] < lo || x[i] >= hi) continue;
+            const cs_pair m = cur[y[i]];
+            count += m.c;
+            sum += m.s + (uint64_t)(int64_t)x[i] * m.c;
+        }
+    }
+    chain_clear(J, rel[1], cur);
+    J->out_count[q] = count;
+    J->out_sum[q] = sum;
+}
+
+static void chain_slice(void *p, int64_t lo, int64_t hi, int s) {
+    (void)lo; (void)hi; (void)s;
+    chain_job *J = (chain_job *)p;
+    cs_pair *a = (cs_pair *)calloc((size_t)J->domain, sizeof(cs_pair));
+    cs_pair *b = (cs_pair *)calloc((size_t)J->domain, sizeof(cs_pair));
+    if (!a || !b) {
+        __atomic_store_n(&J->failed, 1, __ATOMIC_RELAXED);
+        free(a); free(b);
+        return;
+    }
+    for (;;) {
+        const int64_t q = __atomic_fetch_add(&J->next, 1, __ATOMIC_RELAXED);
+        if (q >= J->nq) break;
+        chain_one(J, (int)q, a, b);
+    }
+    free(a); free(b);
+}
+
+int orc_chain_agg(int nq, const int32_t *qoff, const int32_t *qrel, const int32_t *qlo,
+                  const int32_t *qhi, const int64_t *pool_n, const int32_t *const *pool_x,
+                  const int32_t *const *pool_y, int64_t domain, uint64_t *out_count,
+                  uint64_t *out_sum) {
+    chain_job J;
+    J.nq = nq; J.qoff = qoff; J.qrel = qrel; J.qlo = qlo; J.qhi = qhi;
+    J.pool_n = pool_n; J.pool_x = pool_x; J.pool_y = pool_y; J.domain = domain;
+    J.out_count = out_count; J.out_sum = out_sum; J.next = 0; J.failed = 0;
+    int nt = g_threads < nq ? g_threads : nq;
+    if (nt < 1) nt = 1;
+    run_slices(chain_slice, &J, nt, nt);
+    return J.failed ? -1 : 0;
 }

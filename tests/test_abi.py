@@ -5,6 +5,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 import paper_2308_16370_b300 as sj
@@ -66,3 +67,14 @@ def test_create_rejects_mismatched_allocator(lib_path):
     # alloc given without free: rejected before any device call
     cb = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)(lambda n, u: None)
     assert lib.sj_create(ctypes.byref(h), 0, None, ctypes.cast(cb, ctypes.c_void_p), None, None) == 1
+
+
+def test_serving_pool_same_columns_through_torch():
+    """The pool generator's torch path (used for full-size pools on the GPU)
+    gives the numpy path's columns exactly."""
+    from paper_2308_16370_b300 import inputs
+    a = inputs.serving_pool(nrel=4, min_rows=100, max_rows=50_000, domain=1 << 12, seed=3)
+    b = inputs.serving_pool(nrel=4, min_rows=100, max_rows=50_000, domain=1 << 12, seed=3, device="cpu")
+    for ra, rb in zip(a, b):
+        for ca, cb in zip(ra, rb):
+            assert ca.dtype == cb.dtype == np.int32 and np.array_equal(ca, cb)

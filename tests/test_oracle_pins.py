@@ -483,3 +483,70 @@ def test_filter_insert_equals_build_over_union(layout):
     f4, st4 = oracle.filter_insert(f, [new_keys], 0)
     assert (st4 != oracle.INSERT_GATED).all()
     assert oracle.bloom_contains(f4, new_keys).all()
+
+
+def _chain_pool(g, nrel, domain, max_rows):
+    pool = []
+    for j in range(nrel):
+        n = 0 if j == 4 else int(g.integers(1, max_rows))  # relation 4 is empty
+        pool.append([g.integers(0, domain, n, dtype=np.int32) for _ in range(2)])
+    return pool
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_chain_agg_equals_propagation_and_brute_force(seed):
+    """The dense chain counting used to check served results: every query's
+    COUNT and SUM equal agg_propagation's (mod 2^64) on random chains of 1-6
+    relations with and without a predicate (some relations empty), and the
+    nested loop's on tiny ones; the thread count changes nothing."""
+    g = np.random.default_rng(600 + seed)
+    # small domains clear whole message buffers, large ones clear the keys used
+    domain = [37, 300, 5000, 20000][seed]
+    pool = _chain_pool(g, 9, domain, 400)
+    qs = []
+    for i in range(40):
+        n = int(g.integers(1, 7))
+        rels = [int(x) for x in g.choice(len(pool), n, replace=False)]
+        lo = int(g.integers(-5, domain))
+        pred = None if i % 5 == 0 else (0, lo, lo + int(g.integers(0, domain)))
+        qs.append({"rels": rels, "edges": [(j, 1, j + 1, 0) for j in range(n - 1)],
+                   "preds": [pred] + [None] * (n - 1), "root": n - 1,
+                   "sum": [(0, 0, 0), (n - 1, 1, 0)]})
+    oracle.set_threads(1)
+    got1 = oracle.chain_agg(pool, qs, domain)
+    oracle.set_threads(4)
+    got4 = oracle.chain_agg(pool, qs, domain)
+    oracle.set_threads(1)
+    assert got1 == got4
+    for q, r in zip(qs, got1):
+        w = {"rels": [pool[j] for j in q["rels"]], "edges": q["edges"], "preds": q["preds"],
+             "root": q["root"], "sum": q["sum"]}
+        e = oracle.agg_propagation(w)
+        assert (r["count"], r["sum"]) == (e["count"] & oracle._MASK64, e["sum"] & oracle._MASK64)
+    # tiny relations: brute force
+    tiny = []
+    for n in g.integers(0, 7, 5):
+        tiny.append([g.integers(0, 6, int(n), dtype=np.int32) for _ in range(2)])
+    for n in range(1, 5):
+        q = {"rels": list(range(n)), "edges": [(j, 1, j + 1, 0) for j in range(n - 1)],
+             "preds": [(0, 1, 5)] + [None] * (n - 1), "root": n - 1, "sum": [(0, 0, 0), (n - 1, 1, 0)]}
+        (r,) = oracle.chain_agg(tiny, [q], 6)
+        w = {"rels": tiny[:n], "edges": q["edges"], "preds": q["preds"], "root": q["root"], "sum": q["sum"]}
+        e = oracle.nested_loop(w)
+        assert (r["count"], r["sum"]) == (e["count"], e["sum"] & oracle._MASK64)
+
+
+def test_chain_agg_hand_example_and_rejections():
+    """R0 = {(1, 2), (3, 2), (7, 4)}, R1 = {(2, 5), (2, 6), (4, 9)}: with 0 <= x < 5
+    on R0 the join is (1,2,2,5), (1,2,2,6), (3,2,2,5), (3,2,2,6): COUNT 4 and
+    SUM(R0.x + R1.y) = (1+5) + (1+6) + (3+5) + (3+6) = 30."""
+    pool = [[np.array([1, 3, 7], np.int32), np.array([2, 2, 4], np.int32)],
+            [np.array([2, 2, 4], np.int32), np.array([5, 6, 9], np.int32)]]
+    q = {"rels": [0, 1], "edges": [(0, 1, 1, 0)], "preds": [(0, 0, 5), None], "sum": [(0, 0, 0), (1, 1, 0)]}
+    assert oracle.chain_agg(pool, [q], 10) == [{"count": 4, "sum": 30}]
+    q2 = dict(q, preds=[None, None])  # adds (7,4,4,9): 5 rows, 30 + 16
+    assert oracle.chain_agg(pool, [q2], 10) == [{"count": 5, "sum": 46}]
+    with pytest.raises(ValueError):
+        oracle.chain_agg(pool, [dict(q, edges=[(0, 0, 1, 0)])], 10)
+    with pytest.raises(ValueError):
+        oracle.chain_agg(pool, [q], 8)  # key 9 outside the domain
