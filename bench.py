@@ -67,10 +67,16 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving run")
-    ap.add_argument("--serve-queries", type=int, default=2000)
-    ap.add_argument("--serve-max-rows", type=int, default=5_000_000,
-                    help="largest pool relation (50M in the full-size serving workload)")
+    ap.add_argument("--serve-queries", type=int, default=10_000)
+    ap.add_argument("--serve-max-rows", type=int, default=50_000_000,
+                    help="largest pool relation")
     ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--serve-batch", type=int, default=16,
+                    help="queries per batched pruning call in the second serving mode (<= 1: skip it)")
+    ap.add_argument("--serve-check-s", type=float, default=45.0,
+                    help="CPU seconds for the oracle check of served results (0: check all)")
+    ap.add_argument("--serve-only", action="store_true",
+                    help="run the serving workload alone and print its JSON")
     ap.add_argument("--no-cyclic", action="store_true", help="skip the triangle-query run")
     ap.add_argument("--no-star", action="store_true", help="skip the star-join run")
     ap.add_argument("--no-rst", action="store_true", help="skip the Sec. 3.1.1 R,S,T closed-form run")
@@ -367,22 +373,28 @@ def profiled_traffic(kernel: str, workload: str):
 # ----------------------------------------------------------------------------- serving
 def serving_run(args, torch, sj):
     """Poisson stream of chain queries (2-6 relations) over a resident pool of
-    40 relations with Zipf(0.8) keys over 2^22; first a closed loop (all
-    queries at once) for capacity, then an open loop at 0.7x that rate."""
+    40 relations (log-uniform 1e4 .. --serve-max-rows rows, Zipf(0.8) keys
+    over 2^22).  Per mode (one query per worker; batched pruning of up to
+    --serve-batch queued queries per call): a closed loop (all queries at
+    once) for capacity, then open loops at fractions of that rate.  Every
+    mode must give the same results; they are checked against the oracle's
+    chain counting within a CPU time budget (--serve-check-s, 0 = all)."""
     from paper_2308_16370_b300 import inputs
     import oracle
     domain = 1 << 22
+    t0 = time.perf_counter()
     pool = inputs.serving_pool(nrel=40, min_rows=10_000, max_rows=args.serve_max_rows,
-                               domain=domain, seed=5)
+                               domain=domain, seed=5, device="cuda")
+    gen_s = time.perf_counter() - t0
     dev = [[torch.from_numpy(c).cuda() for c in r] for r in pool]
     sizes = [len(r[0]) for r in pool]
     qs = inputs.serving_queries(sizes, args.serve_queries, domain=domain, seed=6)
 
-    def run(rate):
-        with sj.Server(nslots=args.serve_slots) as srv:
+    def run(rate, batch):
+        with sj.Server(nslots=args.serve_slots, batch=batch) as srv:
             ids = [srv.add_relation(c) for c in dev]
-            warm = srv.submit([ids[r] for r in qs[0]["rels"]], qs[0]["edges"], qs[0]["preds"],
-                              qs[0]["sum"], qs[0]["root"])
+            srv.submit([ids[r] for r in qs[0]["rels"]], qs[0]["edges"], qs[0]["preds"],
+                       qs[0]["sum"], qs[0]["root"])
             srv.poll(1, wait_ms=60_000)
             done = {}
             g = np.random.default_rng(7)
@@ -405,32 +417,68 @@ def serving_run(args, torch, sj):
                     done[c["ticket"]] = c
             span = time.perf_counter() - t0
             st = srv.stats()
-        res = [done[t] for t in tickets]
-        return res, span, st
+        return [done[t] for t in tickets], span, st
 
-    closed, span_c, _ = run(None)
-    qps_closed = len(qs) / span_c
-    lam = 0.7 * qps_closed
-    opened, span_o, st = run(lam)
-    lat = np.array([c["done_ms"] - c["submit_ms"] for c in opened])
-    same = all((a["count"], a["sum"]) == (b["count"], b["sum"]) for a, b in zip(closed, opened))
-    # oracle check on a bounded sample of the served queries
-    g = np.random.default_rng(8)
-    sample = [int(i) for i in g.choice(len(qs), min(8, len(qs)), replace=False)]
-    ok = 0
-    for i in sample:
-        q = qs[i]
-        w = {"rels": [pool[r] for r in q["rels"]], "edges": q["edges"], "preds": q["preds"],
-             "root": q["root"], "sum": q["sum"]}
-        e = oracle.agg_propagation(w)
-        ok += int((e["count"], e["sum"]) == (opened[i]["count"], opened[i]["sum"]))
+    def results(rs):
+        return [(c["status"], c["count"], c["sum"]) for c in rs]
+
+    modes = {}
+    ref = None
+    for name, batch, fracs in (("one_query_per_worker", 0, (0.3, 0.5, 0.7, 0.9)),
+                               ("batched_pruning", args.serve_batch, (0.7,))):
+        if name == "batched_pruning" and args.serve_batch <= 1:
+            continue
+        closed, span_c, st_c = run(None, batch)
+        qps_closed = len(qs) / span_c
+        ref = ref or results(closed)
+        same = results(closed) == ref
+        sweep = []
+        for f in fracs:
+            opened, span_o, st = run(f * qps_closed, batch)
+            lat = np.array([c["done_ms"] - c["submit_ms"] for c in opened])
+            same = same and results(opened) == ref
+            sweep.append({"load": f, "rate_qps": f * qps_closed, "qps": len(qs) / span_o,
+                          "p50_ms": float(np.percentile(lat, 50)),
+                          "p99_ms": float(np.percentile(lat, 99))})
+        modes[name] = {"batch": batch, "closed_loop_qps": qps_closed,
+                       "closed_loop_p99_ms": float(np.percentile(
+                           [c["done_ms"] - c["submit_ms"] for c in closed], 99)),
+                       "open_loop": sweep, "same_results": bool(same),
+                       "failed": int(sum(c["status"] != 0 for c in closed)),
+                       "filter_cache_hits": st_c["cache_hits"],
+                       "filter_cache_misses": st_c["cache_misses"],
+                       "peak_concurrency": st_c["peak_concurrency"],
+                       "batches": st_c["batches"], "peak_batch": st_c["peak_batch"]}
+    # every result (or as many as the CPU budget allows, in a seeded random
+    # order) against the oracle's chain counting over all host cores
+    nth = os.cpu_count() or 1
+    oracle.set_threads(nth)
+    order = [int(i) for i in np.random.default_rng(8).permutation(len(qs))]
+    checked = agree = 0
+    tc = time.perf_counter()
+    cpool = oracle.ChainPool(pool, domain)
+    chunk = 8 * nth
+    for c0 in range(0, len(order), chunk):
+        if args.serve_check_s > 0 and time.perf_counter() - tc > args.serve_check_s:
+            break
+        idx = order[c0:c0 + chunk]
+        exp = oracle.chain_agg(cpool, [qs[i] for i in idx])
+        for i, e in zip(idx, exp):
+            checked += 1
+            agree += int(ref[i] == (0, e["count"], e["sum"]))
+    check_s = time.perf_counter() - tc
+    oracle.set_threads(1)
+    base = modes["one_query_per_worker"]
+    at07 = [x for x in base["open_loop"] if x["load"] == 0.7][0]
     return {"queries": len(qs), "slots": args.serve_slots, "arrival": "Poisson",
-            "rate_qps": lam, "qps": len(qs) / span_o, "closed_loop_qps": qps_closed,
-            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "failed": int(sum(c["status"] != 0 for c in opened)),
-            "mix_equals_closed_loop": bool(same), "oracle_checked": len(sample),
-            "oracle_agree": ok, "filter_cache_hits": st["cache_hits"],
-            "filter_cache_misses": st["cache_misses"], "peak_concurrency": st["peak_concurrency"],
+            "rate_qps": at07["rate_qps"], "qps": at07["qps"], "closed_loop_qps": base["closed_loop_qps"],
+            "p50_ms": at07["p50_ms"], "p99_ms": at07["p99_ms"], "failed": base["failed"],
+            "modes": modes, "mix_equals_closed_loop": all(m["same_results"] for m in modes.values()),
+            "oracle_checked": checked, "oracle_agree": agree, "oracle_threads": nth,
+            "oracle_check_s": check_s,
+            "oracle_check": "all queries" if checked == len(qs) else
+                            f"a seeded random {checked} of {len(qs)} (CPU budget {args.serve_check_s} s)",
+            "pool_rows": int(sum(sizes)), "pool_gen_s": gen_s,
             "pool": f"40 relations (x, y), log-uniform 1e4..{args.serve_max_rows:.0e} rows, "
                     f"Zipf(0.8) keys over 2^22; chains of 2-6, predicate on the first relation "
                     f"from 8 templates; COUNT and SUM"}
@@ -676,6 +724,10 @@ def main():
     import paper_2308_16370_b300 as sj
 
     torch.cuda.set_device(local)
+    if args.serve_only:
+        if rank == 0:
+            print(json.dumps({"serving": serving_run(args, torch, sj)}))
+        return
     spec = WORKLOADS[args.workload]
     w = spec["gen"]()
     tuples = sum(len(r[0]) for r in w["rels"])

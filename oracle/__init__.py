@@ -531,25 +531,44 @@ def agg_propagation(w: dict, rels=None, presieved: bool = False):
     raise AssertionError("unreachable")
 
 
-def chain_agg(pool, queries, domain: int):
+class ChainPool:
+    """A relation pool checked once for ``chain_agg``: two int32 columns per
+    relation, every key in [0, domain)."""
+
+    def __init__(self, pool, domain: int):
+        if not 0 < domain < (1 << 31):
+            raise ValueError("domain must be in 1 .. 2^31 - 1")
+        self.domain = int(domain)
+        self.x = [np.ascontiguousarray(r[0], dtype=np.int32) for r in pool]
+        self.y = [np.ascontiguousarray(r[1], dtype=np.int32) for r in pool]
+        for x, y in zip(self.x, self.y):
+            if len(x) != len(y):
+                raise ValueError("pool relations need two columns of equal length")
+            for c in (x, y):
+                if len(c) and (int(c.min()) < 0 or int(c.max()) >= domain):
+                    raise ValueError("pool key outside [0, domain)")
+        self.n = np.asarray([len(x) for x in self.x], dtype=np.int64)
+        self.px = np.asarray([x.ctypes.data for x in self.x], dtype=np.uint64)
+        self.py = np.asarray([y.ctypes.data for y in self.y], dtype=np.uint64)
+
+    def __len__(self):
+        return len(self.x)
+
+
+def chain_agg(pool, queries, domain: int = None):
     """COUNT(*) and SUM(first.x + last.y) of chain queries over a pool of
     two-column relations (x, y), the same counting as ``agg_propagation``
     with per-key messages held densely over the keys [0, domain) (C, over the
     oracle's threads, one query per thread at a time).
 
-    A query is a dict with ``rels`` (pool indices r_0 .. r_k, joined on
-    r_i.y = r_{i+1}.x as ``edges`` (i, 1, i + 1, 0) say), ``preds`` (a range
-    (0, lo, hi) on r_0.x, or None; nothing on the others) and ``sum`` =
-    [(0, 0, 0), (k, 1, 0)].  Anything else raises ValueError.  Returns one
-    {"count", "sum"} per query, both modulo 2^64."""
-    pool_x = [np.ascontiguousarray(r[0], dtype=np.int32) for r in pool]
-    pool_y = [np.ascontiguousarray(r[1], dtype=np.int32) for r in pool]
-    for x, y in zip(pool_x, pool_y):
-        if len(x) != len(y):
-            raise ValueError("pool relations need two columns of equal length")
-        for c in (x, y):
-            if len(c) and (int(c.min()) < 0 or int(c.max()) >= domain):
-                raise ValueError("pool key outside [0, domain)")
+    ``pool``: a ``ChainPool`` or a list of relations (checked here against
+    ``domain``).  A query is a dict with ``rels`` (pool indices r_0 .. r_k,
+    joined on r_i.y = r_{i+1}.x as ``edges`` (i, 1, i + 1, 0) say), ``preds``
+    (a range (0, lo, hi) on r_0.x, or None; nothing on the others) and
+    ``sum`` = [(0, 0, 0), (k, 1, 0)].  Anything else raises ValueError.
+    Returns one {"count", "sum"} per query, both modulo 2^64."""
+    if not isinstance(pool, ChainPool):
+        pool = ChainPool(pool, domain)
     qoff, qrel, qlo, qhi = [0], [], [], []
     for q in queries:
         rels = list(q["rels"])
@@ -575,20 +594,15 @@ def chain_agg(pool, queries, domain: int):
     nq = len(queries)
     if nq == 0:
         return []
-    if not 0 < domain < (1 << 31):
-        raise ValueError("domain must be in 1 .. 2^31 - 1")
     lib = _load()
     qoff = np.asarray(qoff, dtype=np.int32)
     qrel = np.asarray(qrel, dtype=np.int32)
     qlo = np.asarray(qlo, dtype=np.int32)
     qhi = np.asarray(qhi, dtype=np.int32)
-    pool_n = np.asarray([len(x) for x in pool_x], dtype=np.int64)
-    px = np.asarray([x.ctypes.data for x in pool_x], dtype=np.uint64)
-    py = np.asarray([y.ctypes.data for y in pool_y], dtype=np.uint64)
     cnt = np.zeros(nq, dtype=np.uint64)
     tot = np.zeros(nq, dtype=np.uint64)
-    if lib.orc_chain_agg(nq, _ptr(qoff), _ptr(qrel), _ptr(qlo), _ptr(qhi), _ptr(pool_n), _ptr(px),
-                         _ptr(py), int(domain), _ptr(cnt), _ptr(tot)):
+    if lib.orc_chain_agg(nq, _ptr(qoff), _ptr(qrel), _ptr(qlo), _ptr(qhi), _ptr(pool.n),
+                         _ptr(pool.px), _ptr(pool.py), pool.domain, _ptr(cnt), _ptr(tot)):
         raise MemoryError("orc_chain_agg: message buffers")
     return [{"count": int(c), "sum": int(t)} for c, t in zip(cnt, tot)]
 

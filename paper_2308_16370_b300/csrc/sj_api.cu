@@ -1636,6 +1636,9 @@ sj_status sieve_path_batch_impl(sj_ctx* c, int nq, const sj_path* paths, const s
   for (size_t v = 0; v < vers.size(); ++v) {
     if (!vers[v].r) continue;
     vers[v].r->nrows = rows_of_ver((int)v);
+    // the count is known now: later calls size their work by it, not by the
+    // input's row bound
+    vers[v].r->cap = vers[v].r->nrows;
     if (!is_final[v]) free_rel(c, vers[v].r);
     vers[v].r = is_final[v] ? vers[v].r : nullptr;
   }
