@@ -73,6 +73,8 @@ def parse():
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--serve-batch", type=int, default=16,
                     help="queries per batched pruning call in the second serving mode (<= 1: skip it)")
+    ap.add_argument("--serve-batch-max-rows", type=int, default=4_000_000,
+                    help="batched mode: queries over more rows than this run alone")
     ap.add_argument("--serve-check-s", type=float, default=45.0,
                     help="CPU seconds for the oracle check of served results (0: check all)")
     ap.add_argument("--serve-only", action="store_true",
@@ -391,7 +393,8 @@ def serving_run(args, torch, sj):
     qs = inputs.serving_queries(sizes, args.serve_queries, domain=domain, seed=6)
 
     def run(rate, batch):
-        with sj.Server(nslots=args.serve_slots, batch=batch) as srv:
+        with sj.Server(nslots=args.serve_slots, batch=batch,
+                       batch_max_rows=args.serve_batch_max_rows if batch > 1 else 0) as srv:
             ids = [srv.add_relation(c) for c in dev]
             srv.submit([ids[r] for r in qs[0]["rels"]], qs[0]["edges"], qs[0]["preds"],
                        qs[0]["sum"], qs[0]["root"])
@@ -440,7 +443,9 @@ def serving_run(args, torch, sj):
             sweep.append({"load": f, "rate_qps": f * qps_closed, "qps": len(qs) / span_o,
                           "p50_ms": float(np.percentile(lat, 50)),
                           "p99_ms": float(np.percentile(lat, 99))})
-        modes[name] = {"batch": batch, "closed_loop_qps": qps_closed,
+        modes[name] = {"batch": batch,
+                       "batch_max_rows": args.serve_batch_max_rows if batch > 1 else None,
+                       "closed_loop_qps": qps_closed,
                        "closed_loop_p99_ms": float(np.percentile(
                            [c["done_ms"] - c["submit_ms"] for c in closed], 99)),
                        "open_loop": sweep, "same_results": bool(same),

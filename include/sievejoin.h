@@ -429,6 +429,9 @@ typedef struct {
                                 their pruning phases as one sj_sieve_path_batch call, then
                                 each query's join; 0 or 1 = one query at a time */
     int32_t reserved;
+    uint64_t batch_max_rows; /* batch mode: a query whose relations hold more rows than this
+                                in all runs alone, so it does not hold back a batch of small
+                                ones (0 = no limit) */
 } sj_server_opts;
 
 typedef struct {

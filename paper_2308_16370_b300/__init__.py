@@ -95,7 +95,8 @@ class ServerOpts(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("nslots", ctypes.c_int32),
                 ("hbm_budget", ctypes.c_uint64), ("passes", ctypes.c_int32),
                 ("cache_filters", ctypes.c_int32), ("filter", FilterParams),
-                ("batch", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("batch", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("batch_max_rows", ctypes.c_uint64)]
 
 
 class Query(ctypes.Structure):
@@ -619,11 +620,12 @@ class Server:
     """Query server with continuous batching over `nslots` workers (one CUDA
     stream each) and a device cache of reusable leaf filters (Sec. 2.3).
     ``batch`` > 1: a worker takes up to that many queued queries at once and
-    prunes them in one batched call (lock-step launches), then joins each."""
+    prunes them in one batched call (lock-step launches), then joins each;
+    queries over more than ``batch_max_rows`` rows (0 = no limit) run alone."""
 
     def __init__(self, device: int = 0, nslots: int = 4, hbm_budget: int = 0, passes=FWD_BWD,
                  cache_filters: bool = True, bits_per_key=8, k=3, layout=REGBLOCKED32, seed=0,
-                 batch: int = 0):
+                 batch: int = 0, batch_max_rows: int = 0):
         torch = _torch()
         if not torch.cuda.is_available():
             raise RuntimeError("sievejoin needs a CUDA GPU; none is visible")
@@ -632,7 +634,7 @@ class Server:
         self._keep = []
         opts = ServerOpts(self.device, int(nslots), int(hbm_budget), int(passes),
                           1 if cache_filters else 0, _params(bits_per_key, k, layout, seed),
-                          int(batch), 0)
+                          int(batch), 0, int(batch_max_rows))
         h = ctypes.c_void_p()
         st = self.lib.sj_server_create(ctypes.byref(h), ctypes.byref(opts))
         if st != 0:

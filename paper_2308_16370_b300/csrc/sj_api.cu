@@ -1083,7 +1083,12 @@ sj_status sieve_path_batch_impl(sj_ctx* c, int nq, const sj_path* paths, const s
 extern "C" sj_status sj_sieve_path_batch(sj_ctx* c, int nq, const sj_path* paths,
                                          const sj_sieve_opts* opts, sj_rel* out_sieved,
                                          sj_sieve_stats* stats) {
-  return sieve_path_batch_impl(c, nq, paths, opts, out_sieved, stats);
+  if (!c) return SJ_EINVAL;
+  // temporaries from the context's arena (the handed-out relations are not)
+  arena_begin(c);
+  const sj_status st = sieve_path_batch_impl(c, nq, paths, opts, out_sieved, stats);
+  arena_end(c);
+  return st;
 }
 
 namespace {
@@ -1364,10 +1369,13 @@ sj_status sieve_path_batch_impl(sj_ctx* c, int nq, const sj_path* paths, const s
     dfree(c, fblock, fblock_bytes);
     dfree(c, ablock, ablock_bytes);
   };
+  std::vector<char> is_final(vers.size(), 0);
+  for (int q = 0; q < nq; ++q)
+    for (int i = 0; i < paths[q].nrel; ++i) is_final[final_ver[q][i]] = 1;
   for (auto& st : steps) {
     const BVer& vin = vers[st.ver_in];
     const sj_rel_s* in = vin.r ? vin.r : vin.in;
-    vers[st.ver_out].r = new_rel(c, in->ncols, vin.cap);
+    vers[st.ver_out].r = new_rel(c, in->ncols, vin.cap, is_final[st.ver_out] != 0);
     if (!vers[st.ver_out].r) {
       cleanup();
       return fail(c, SJ_ENOMEM, "sieve output allocation failed");
@@ -1630,9 +1638,6 @@ sj_status sieve_path_batch_impl(sj_ctx* c, int nq, const sj_path* paths, const s
   }
   prof_resolve(c, p0);
   // hand out the final versions; free the rest
-  std::vector<char> is_final(vers.size(), 0);
-  for (int q = 0; q < nq; ++q)
-    for (int i = 0; i < paths[q].nrel; ++i) is_final[final_ver[q][i]] = 1;
   for (size_t v = 0; v < vers.size(); ++v) {
     if (!vers[v].r) continue;
     vers[v].r->nrows = rows_of_ver((int)v);
@@ -1800,7 +1805,12 @@ sj_status join_impl(sj_ctx* c, const sj_path* path, const sj_rel* inputs, int mo
 
 extern "C" sj_status sj_join(sj_ctx* c, const sj_path* path, const sj_rel* inputs, int mode,
                              int nrefs, const sj_colref* refs, sj_result* result) {
-  return join_impl(c, path, inputs, mode, nrefs, refs, result, nullptr);
+  if (!c) return SJ_EINVAL;
+  // temporaries from the context's arena (results are allocated outside it)
+  arena_begin(c);
+  const sj_status st = join_impl(c, path, inputs, mode, nrefs, refs, result, nullptr);
+  arena_end(c);
+  return st;
 }
 
 // The enumeration phase with host-known sizes (one synchronisation per level);

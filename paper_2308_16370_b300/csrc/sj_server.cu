@@ -11,8 +11,9 @@
 // In batch mode a free worker takes up to `batch` queued queries that fit the
 // budget together and prunes them with one sj_sieve_path_batch call (two
 // launches per schedule level for the whole group), then runs each query's
-// join over its pruned relations (sj_sieve_join with SJ_NO_SIEVE and no
-// predicates, which were applied while pruning).
+// join over its pruned relations (sj_join with them as inputs).  A query over
+// more than batch_max_rows rows runs alone: a batch moves in lock step, so
+// one large query would hold back every small one in it.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -36,6 +37,7 @@ struct Pending {
   sj_query q;
   uint64_t ticket;
   uint64_t est_bytes;
+  uint64_t rows;  // rows of its relations in all
   double submit_ms;
 };
 
@@ -56,6 +58,7 @@ struct sj_server {
   Clock::time_point t0;
   std::vector<sj_rel> rels;
   std::vector<uint64_t> rel_bytes;
+  std::vector<int64_t> rel_rows;
   std::vector<int> rel_ncols;
   std::vector<sj_ctx*> ctxs;
   std::vector<cudaStream_t> streams;
@@ -237,18 +240,13 @@ void run_group(sj_server* s, int w, const std::vector<Pending>& ps, std::vector<
   }
   for (int k = 0; k < nq; ++k) {
     const sj_query& q = ps[k].q;
-    sj_path jp = paths[k];
-    jp.rels = &sieved[(size_t)k * SJ_MAX_REL];
-    jp.preds = nullptr;
-    sj_sieve_opts o{};
-    o.passes = SJ_NO_SIEVE;
-    o.filter = s->opts.filter;
+    sj_rel* in = &sieved[(size_t)k * SJ_MAX_REL];
     sj_result res{};
-    const sj_status st = sj_sieve_join(ctx, &jp, &o, SJ_COUNT_SUM, q.nterms, q.terms, &res, nullptr);
+    const sj_status st = sj_join(ctx, &paths[k], in, SJ_COUNT_SUM, q.nterms, q.terms, &res);
     (*cs)[k].status = st;
     (*cs)[k].count = res.count;
     (*cs)[k].sum = res.sum;
-    for (int i = 0; i < q.nrel; ++i) sj_free_rel(ctx, jp.rels[i]);
+    for (int i = 0; i < q.nrel; ++i) sj_free_rel(ctx, in[i]);
     deliver(s, (*cs)[k]);
   }
 }
@@ -259,6 +257,7 @@ void worker(sj_server* s, int w) {
   while (true) {
     std::vector<Pending> ps;
     uint64_t bytes = 0;
+    bool grouped = false;  // pruned by one batched call (possibly a group of one)
     {
       std::unique_lock<std::mutex> lk(s->mu);
       while (true) {
@@ -270,14 +269,29 @@ void worker(sj_server* s, int w) {
         }
         s->cv_work.wait_for(lk, std::chrono::milliseconds(50));
       }
-      // the head of the queue, then (batch mode) the queries behind it that
-      // fit the budget next to it, in arrival order
-      while (!s->queue.empty() && (int)ps.size() < batch) {
-        const uint64_t need = s->queue.front().est_bytes;
-        if (!ps.empty() && s->inflight_bytes + bytes + need > s->opts.hbm_budget) break;
-        ps.push_back(s->queue.front());
-        s->queue.pop_front();
-        bytes += need;
+      // the head of the queue; in batch mode, unless it is a large query,
+      // then the small queries behind it (within a window of the queue, in
+      // arrival order) that fit the budget next to it
+      auto small = [&](const Pending& x) {
+        return s->opts.batch_max_rows == 0 || x.rows <= s->opts.batch_max_rows;
+      };
+      ps.push_back(s->queue.front());
+      s->queue.pop_front();
+      bytes += ps[0].est_bytes;
+      grouped = batch > 1 && small(ps[0]);
+      if (grouped) {
+        const size_t window = 4 * (size_t)batch;
+        for (size_t i = 0; i < s->queue.size() && i < window && (int)ps.size() < batch;) {
+          const Pending& x = s->queue[i];
+          if (!small(x)) {
+            ++i;
+            continue;
+          }
+          if (s->inflight_bytes + bytes + x.est_bytes > s->opts.hbm_budget) break;
+          bytes += x.est_bytes;
+          ps.push_back(x);
+          s->queue.erase(s->queue.begin() + (long)i);
+        }
       }
       s->inflight_bytes += bytes;
       s->running += (int)ps.size();
@@ -292,7 +306,7 @@ void worker(sj_server* s, int w) {
       cs[k].submit_ms = ps[k].submit_ms;
       cs[k].start_ms = start;
     }
-    if (batch > 1) {
+    if (grouped) {
       run_group(s, w, ps, &cs);
     } else {
       run_query(s, w, ps[0], &cs[0]);
@@ -361,6 +375,7 @@ sj_status sj_server_add_relation(sj_server* s, int ncols, const int32_t* const* 
   *rel_id = (int32_t)s->rels.size();
   s->rels.push_back(r);
   s->rel_bytes.push_back((uint64_t)nrows * 4 * (uint64_t)ncols);
+  s->rel_rows.push_back(nrows);
   s->rel_ncols.push_back(ncols);
   return SJ_OK;
 }
@@ -370,12 +385,14 @@ sj_status sj_server_submit(sj_server* s, const sj_query* q, uint64_t* ticket) {
     return SJ_EINVAL;
   Pending p;
   p.q = *q;
+  p.rows = 0;
   uint64_t bytes = 64ull << 20;
   {
     std::lock_guard<std::mutex> lk(s->mu);
     for (int i = 0; i < q->nrel; ++i) {
       if (q->rel[i] < 0 || q->rel[i] >= (int32_t)s->rels.size()) return SJ_EINVAL;
       bytes += 3 * s->rel_bytes[q->rel[i]];  // sieved copies, filters and tables
+      p.rows += (uint64_t)s->rel_rows[q->rel[i]];
     }
     for (int e = 0; e < q->nrel - 1; ++e) {
       const sj_edge& E = q->edges[e];

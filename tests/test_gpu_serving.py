@@ -31,8 +31,9 @@ def workload_of(pool_np, q):
             "root": q["root"], "sum": q["sum"]}
 
 
-def serve(dev_pool, queries, nslots, budget=0, cache=True, sequential=False, batch=0):
-    with sj.Server(nslots=nslots, hbm_budget=budget, cache_filters=cache, batch=batch) as srv:
+def serve(dev_pool, queries, nslots, budget=0, cache=True, sequential=False, batch=0, batch_max_rows=0):
+    with sj.Server(nslots=nslots, hbm_budget=budget, cache_filters=cache, batch=batch,
+                   batch_max_rows=batch_max_rows) as srv:
         ids = [srv.add_relation(cols) for cols in dev_pool]
         out = {}
         if sequential:
@@ -68,14 +69,15 @@ def test_mix_equals_alone_and_oracle(pool):
         assert m["submit_ms"] <= m["start_ms"] <= m["done_ms"]
 
 
-@pytest.mark.parametrize("cache", [True, False])
-def test_batch_mode_mix_equals_alone_and_oracle(pool, cache):
-    """Batch mode (pruning of up to 8 queued queries in one batched call):
-    every result equals the query run alone and the oracle."""
+@pytest.mark.parametrize("cache,max_rows", [(True, 0), (False, 0), (True, 150_000)])
+def test_batch_mode_mix_equals_alone_and_oracle(pool, cache, max_rows):
+    """Batch mode (pruning of up to 8 queued queries in one batched call;
+    with a row limit, larger queries run alone): every result equals the
+    query run alone and the oracle."""
     pool_np, dev = pool
     qs = inputs.serving_queries([len(r[0]) for r in pool_np], 80, domain=DOMAIN, max_len=6,
                                 ntemplates=3, seed=23)
-    mixed, st = serve(dev, qs, nslots=2, cache=cache, batch=8)
+    mixed, st = serve(dev, qs, nslots=2, cache=cache, batch=8, batch_max_rows=max_rows)
     alone, _ = serve(dev, qs, nslots=1, cache=False, sequential=True)
     assert st["completed"] == len(qs) and st["failed"] == 0
     assert st["batches"] > 0 and st["peak_batch"] > 1
