@@ -365,8 +365,10 @@ typedef struct {
  * `inputs` NULL joins the path's own relations after applying its predicates;
  * otherwise inputs[i] replaces relation i and is taken as already filtered by
  * predicate i (the output of sj_sieve_path).  Synchronises at every level.
- * Errors: SJ_EINVAL, SJ_ENOMEM, SJ_EOVERFLOW (COUNT >= 2^63), SJ_ETABLEFULL,
- * SJ_ETIMEOUT, SJ_ECUDA.
+ * A hash table's build side holds at most 2^30 rows (SJ_EINVAL beyond: slot
+ * counts and row ids are 32-bit on the device); sj_sieve_join has the same
+ * limit.  Errors: SJ_EINVAL, SJ_ENOMEM, SJ_EOVERFLOW (COUNT >= 2^63),
+ * SJ_ETABLEFULL, SJ_ETIMEOUT, SJ_ECUDA.
  */
 SJ_API sj_status sj_join(sj_ctx *ctx, const sj_path *path, const sj_rel *inputs, int mode, int nrefs,
                   const sj_colref *refs, sj_result *result);

@@ -1744,7 +1744,12 @@ struct Table2 {
   uint64_t nslots;
 };
 
+// Largest hash-table build side: slot counts (up to 2^31 here) and row ids
+// are held in 32 bits on the device.
+constexpr int64_t kMaxTableRows = int64_t(1) << 30;
+
 sj_status make_table(sj_ctx* c, Temps& tmp, int64_t nrows, Table2* out) {
+  if (nrows > kMaxTableRows) return fail(c, SJ_EINVAL, "hash-table build side above 2^30 rows");
   sj_status st = SJ_OK;
   const uint64_t nslots = pow2_at_least(std::max<uint64_t>(64, 2 * (uint64_t)nrows));
   unsigned long long* slots = tmp.get<unsigned long long>(nslots, &st);
@@ -2216,6 +2221,7 @@ struct AsyncInter {
 sj_status build_adjacency_dev(sj_ctx* c, Temps& tmp, const int32_t* keys, const uint64_t* n_dev,
                               int64_t n_host, int64_t cap, uint32_t* mask, uint32_t* nslots_dev,
                               Adjacency* g, int n_slot) {
+  if (cap > kMaxTableRows) return fail(c, SJ_EINVAL, "hash-table build side above 2^30 rows");
   sj_status st = SJ_OK;
   const int sms = c->num_sms;
   const int64_t capn = std::max<int64_t>(cap, 1);
