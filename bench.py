@@ -893,7 +893,7 @@ def main():
         "e2e": e2e,
         "plain_gpu_hash_join": plain,
         "fwd_bwd_same_params": fwd_bwd,
-        "roofline": {"bound": "hbm", "kernel": "k_sieve", "achieved": achieved, "peak": peak,
+        "roofline": {"bound": "hbm", "kernel": "k_sieve_chunk", "achieved": achieved, "peak": peak,
                      "frac_of_nominal_7700": achieved / 7700.0,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "launches": sv["launches"],
