@@ -67,6 +67,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving run")
+    ap.add_argument("--no-chain3", action="store_true", help="skip the 3-way chain latency run")
     ap.add_argument("--serve-queries", type=int, default=10_000)
     ap.add_argument("--serve-max-rows", type=int, default=50_000_000,
                     help="largest pool relation")
@@ -489,6 +490,79 @@ def serving_run(args, torch, sj):
                     f"from 8 templates; COUNT and SUM"}
 
 
+# ----------------------------------------------------------------------------- CPU oracle timing
+def cpu_rates(fn, units, budget_s=8.0, max_reps=20):
+    """The oracle call `fn` timed at 1 thread and at os.cpu_count() threads on
+    the host cores: units per second, repetitions and seconds of each."""
+    import oracle
+    nproc = os.cpu_count() or 1
+    out = {}
+    for threads in (1, nproc):
+        oracle.set_threads(threads)
+        t_tot, reps = 0.0, 0
+        while reps < max_reps and (reps == 0 or t_tot < budget_s):
+            t0 = time.perf_counter()
+            fn()
+            t_tot += time.perf_counter() - t0
+            reps += 1
+        out[threads] = {"value": units * reps / t_tot, "cores": threads, "runs": reps, "s": t_tot}
+    oracle.set_threads(1)
+    return {"1_thread": out[1], "nproc": out[nproc]}
+
+
+# ----------------------------------------------------------------------------- C1 latency
+def chain3_run(torch, sj, ctx, stream):
+    """The 3-way chain R(a,b) S(b,c) T(c,d), 100k rows each, keys uniform in
+    [0, 50000), 8 bits per key and k = 3: the latency of one query as a caller
+    sees it (host clock around the call, which synchronises), first call and
+    repeated; the materialised result against the oracle; the plain GPU join;
+    the CPU oracle on the same input."""
+    from paper_2308_16370_b300 import inputs
+    import oracle
+    w = inputs.uniform_chain()
+    tuples = sum(len(r[0]) for r in w["rels"])
+    rels = [ctx.load_relation([torch.from_numpy(c).cuda() for c in r], where="copy") for r in w["rels"]]
+    q = dict(refs=w["sum"], bits_per_key=8, k=3, layout=sj.REGBLOCKED32, passes=sj.FWD_BWD)
+    exp = oracle.hash_join(w)
+
+    def lat(fn, n):
+        ts = []
+        for _ in range(n):
+            t0 = time.perf_counter()
+            r = fn()
+            ts.append((time.perf_counter() - t0) * 1000.0)
+        return ts, r
+
+    first, r0 = lat(lambda: ctx.sieve_join(rels, w["edges"], w["preds"], w["root"], **q), 1)
+    ts, r = lat(lambda: ctx.sieve_join(rels, w["edges"], w["preds"], w["root"], **q), 50)
+    assert (r0["count"], r0["sum"]) == (r["count"], r["sum"]) == (exp["count"], exp["sum"])
+    pts, pr = lat(lambda: ctx.join(rels, w["edges"], w["preds"], w["root"], refs=w["sum"]), 20)
+    assert (pr["count"], pr["sum"]) == (exp["count"], exp["sum"])
+    refs = [(0, 0), (0, 1), (1, 1), (2, 1)]
+    m = ctx.sieve_join(rels, w["edges"], w["preds"], w["root"], mode=sj.MATERIALIZE, refs=refs,
+                       bits_per_key=8, k=3)
+    got = m["rows"].to_numpy() if m["rows"] is not None else [np.zeros(0, np.int32)] * 4
+    om = oracle.hash_join(w, mode=oracle.MATERIALIZE, refs=[(a, b, 0) for a, b in refs])
+    same_rows = sorted(zip(*[c.tolist() for c in got])) == sorted(zip(*[c.tolist() for c in om["cols"]]))
+    assert same_rows and m["count"] == exp["count"]
+    cpu = cpu_rates(lambda: oracle.hash_join(w), tuples)
+    for x in rels:
+        x.free()
+    return {"workload": "3-way chain, 100k rows per relation, keys uniform in [0, 50000); "
+                        "8 bits/key, k = 3, forward + backward",
+            "input_tuples": tuples, "count": r["count"], "sum": r["sum"],
+            "first_call_ms": first[0], "latency_ms_p50": float(np.median(ts)),
+            "latency_ms_p99": float(np.percentile(ts, 99)),
+            "tuples_per_s": tuples / (float(np.median(ts)) / 1000.0),
+            "path": "sj_sieve_join, repeated (device-sized, CUDA-graph replay after the second call)",
+            "materialised_rows": int(m["count"]), "materialised_equals_oracle": bool(same_rows),
+            "plain_gpu": {"latency_ms_p50": float(np.median(pts)),
+                          "tuples_per_s": tuples / (float(np.median(pts)) / 1000.0),
+                          "path": "sj_join (one sync per level)"},
+            "cpu_oracle": dict(cpu, unit=UNIT, kind="oracle",
+                               sample="the full 3-way chain; the oracle's plain binary hash join")}
+
+
 # ----------------------------------------------------------------------------- star join
 def freitag_run(torch, sj, ctx, stream, r=1_000_000, d=4):
     """The synthetic R, S, T benchmark of Sec. 3.1.1 at r = 1e6, d = 4: unary
@@ -584,6 +658,12 @@ def star_run(torch, sj, ctx, stream):
                     "intermediate_tuples": r["intermediate"]}
     for x in rels:
         x.free()
+    import oracle
+    ws = inputs.star(nfact=20_000_000)
+    stuples = sum(len(r[0]) for r in ws["rels"])
+    out["cpu_oracle"] = dict(cpu_rates(lambda: oracle.hash_join(ws), stuples), unit=UNIT, kind="oracle",
+                             sample="the same star at 20M fact rows (same dimensions and predicates); "
+                                    "the oracle's plain binary hash join")
     return out
 
 
@@ -625,6 +705,23 @@ def cyclic_run(torch, sj, ctx, stream):
                     "roofline": {"bound": "hbm", "alg_bytes": alg, "achieved": gbps, "unit": "GB/s",
                                  "peak": load_peaks()[0], "frac": gbps / load_peaks()[0]}}
     rel.free()
+    # the CPU oracle on a bounded sample of the same shape, and the GPU's
+    # counts on that sample against it
+    import oracle
+    s_src, s_dst = inputs.rmat_edges(scale=16, nedges=500_000, seed=4)
+    s_cuts = inputs.uneven_cuts(1 << 16, 64, seed=4)
+    exp = oracle.triangle_counts(s_src, s_dst, s_cuts)
+    srel = ctx.load_relation([torch.from_numpy(s_src).cuda(), torch.from_numpy(s_dst).cuda()], "copy")
+    got, _ = ctx.triangles(srel, s_cuts, sieve_rounds=2)
+    srel.free()
+    sample_equal = bool(np.array_equal(np.asarray(got, dtype=np.int64), np.asarray(exp, dtype=np.int64)))
+    assert sample_equal, "triangle counts differ from the oracle on the sample graph"
+    cpu = cpu_rates(lambda: oracle.triangle_counts(s_src, s_dst, s_cuts), 3 * len(s_src), budget_s=8.0,
+                    max_reps=3)
+    out["cpu_oracle"] = dict(cpu, unit="edge tuples/s", kind="oracle",
+                             sample="R-MAT 2^16 vertices, 500k distinct edges, 64 uneven subqueries; "
+                                    "the oracle's binary hash join of E with E, then the closing-edge "
+                                    "lookup", gpu_counts_equal_on_sample=sample_equal)
     return out
 
 
@@ -845,6 +942,10 @@ def main():
                "h2d_bytes_per_step": ec["h2d_bytes"] // (esteps + 1),
                "d2h_bytes_per_step": ec["d2h_bytes"] // (esteps + 1)}
 
+    chain3 = None
+    if not args.no_chain3:
+        chain3 = chain3_run(torch, sj, ctx, stream)
+
     serving = None
     if not args.no_serve:
         serving = serving_run(args, torch, sj)
@@ -904,6 +1005,7 @@ def main():
                     **{k: {"launches": v["launches"], "ms_per_step": v["ms"] / bsteps,
                            "GBps": (v["bytes"] / (v["ms"] / 1000.0) / 1e9) if v["ms"] > 0 else None}
                        for k, v in kstats.items() if v["launches"]}},
+        "chain3_latency": chain3,
         "serving": serving,
         "cyclic_triangles": cyclic,
         "star": star,
