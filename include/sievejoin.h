@@ -94,7 +94,9 @@ SJ_API const char *sj_version(void);
 enum {
     SJ_DEVICE_BORROW = 0, /* keep the caller's device pointers; they must outlive the handle */
     SJ_DEVICE_COPY = 1,   /* copy device columns into library memory */
-    SJ_HOST_COPY = 2      /* copy host columns (pinned memory is fastest) to the device */
+    SJ_HOST_COPY = 2,     /* copy host columns (pinned memory is fastest) to the device */
+    SJ_HOST_MAPPED = 3    /* keep page-locked host columns where they are; kernels read them
+                             over the host link each time they touch them */
 };
 
 /*
@@ -102,8 +104,21 @@ enum {
  * `cols` is an array of `ncols` column pointers with `nrows` int32 values
  * each.  With SJ_HOST_COPY the copies are enqueued on the context stream and
  * the host buffers must stay valid until the next sj_sync (or any call that
- * synchronises).  Errors: SJ_EINVAL (ncols outside 1..SJ_MAX_COLS, nrows < 0
- * or >= 2^31, a null or misaligned device pointer), SJ_ENOMEM.
+ * synchronises).  With SJ_HOST_MAPPED nothing is copied: every column must be
+ * page-locked host memory the device can address (cudaHostAlloc or
+ * cudaHostRegister with the mapped flag, or any pinned allocation on a system
+ * with unified addressing), 16-byte aligned, and it must outlive the handle.
+ * Kernels read such columns from host memory, so only what they touch
+ * crosses the link: sj_sieve_join copies the columns it reads in full (a
+ * relation's first tested key column, the column a filter is built from
+ * before that, the join columns of a relation it never sieves) to the device
+ * in bulk on a copy stream, in the order the pruning needs them, and the
+ * pruning of each relation waits only for its own columns; the surviving rows
+ * of the other columns and the SUM terms of matching rows are read in place
+ * (the paper's point: tuples that cannot reach the result are dropped before
+ * they are moved).  Other calls read mapped columns in place.  Errors:
+ * SJ_EINVAL (ncols outside 1..SJ_MAX_COLS, nrows < 0 or >= 2^31, a null or
+ * misaligned pointer, host memory the device cannot address), SJ_ENOMEM.
  */
 SJ_API sj_status sj_load_relation(sj_ctx *ctx, int ncols, const int32_t *const *cols, int64_t nrows,
                            int where, sj_rel *out);

@@ -25,7 +25,7 @@ REGBLOCKED32, BLOCKED256, CLASSIC = 0, 1, 2
 FWD_BWD, BWD_ONLY, NO_SIEVE = 0, 1, 2
 COUNT_SUM, MATERIALIZE = 0, 1
 INSERT_GATED, INSERT_CONTAINED, INSERT_NEW = 0, 1, 2
-DEVICE_BORROW, DEVICE_COPY, HOST_COPY = 0, 1, 2
+DEVICE_BORROW, DEVICE_COPY, HOST_COPY, HOST_MAPPED = 0, 1, 2, 3
 MAX_COLS, MAX_REL, MAX_PROBES, MAX_TERMS, MAX_STEPS = 8, 8, 4, 8, 32
 KERNEL_KINDS = {"bloom_build": 0, "sieve": 1, "ht_build": 2, "ht_probe": 3, "ht_expand": 4,
                 "agg": 5, "other": 6}
@@ -356,10 +356,13 @@ class Context:
 
     # --------------------------------------------------------------- relations
     def load_relation(self, cols, where: str = "borrow") -> Relation:
-        """``cols``: torch int32 CUDA tensors (``borrow``/``copy``) or numpy /
-        CPU tensors (``host``; copied on the context stream)."""
+        """``cols``: torch int32 CUDA tensors (``borrow``/``copy``), numpy /
+        CPU tensors (``host``; copied on the context stream), or pinned CPU
+        tensors (``mapped``; not copied: kernels read them over the host link,
+        and they are kept alive with the handle)."""
         torch = _torch()
-        mode = {"borrow": DEVICE_BORROW, "copy": DEVICE_COPY, "host": HOST_COPY}[where]
+        mode = {"borrow": DEVICE_BORROW, "copy": DEVICE_COPY, "host": HOST_COPY,
+                "mapped": HOST_MAPPED}[where]
         keep = []
         ptrs = (ctypes.c_void_p * len(cols))()
         n = None
@@ -372,6 +375,10 @@ class Context:
                     c = c.contiguous()
                     assert c.dtype == torch.int32 and not c.is_cuda
                     ptrs[j] = c.data_ptr()
+            elif mode == HOST_MAPPED:
+                if not (c.dtype == torch.int32 and not c.is_cuda and c.is_contiguous() and c.is_pinned()):
+                    raise ValueError("'mapped' columns must be contiguous pinned int32 CPU tensors")
+                ptrs[j] = c.data_ptr()
             else:
                 assert c.dtype == torch.int32 and c.is_cuda and c.is_contiguous()
                 ptrs[j] = c.data_ptr()

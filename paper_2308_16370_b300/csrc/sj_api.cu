@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <functional>
 #include <map>
+#include <memory>
 #include <string>
 #include <utility>
 #include <vector>
@@ -108,6 +109,10 @@ struct sj_ctx {
   uint32_t prof_mask = 0xffffffffu;  // kernel classes profiled while prof_on
   std::vector<ProfRec> prof;
   std::vector<cudaEvent_t> ev_pool;
+  // copy stream of host-mapped relations' staged columns, in plan order
+  cudaStream_t copy = nullptr;
+  cudaEvent_t ev_copy_fork = nullptr;
+  cudaEvent_t ev_copied[SJ_MAX_REL] = {};
   // pinned staging of sj_sieve_path_batch (launch arguments, counts read back)
   uint8_t* h_batch = nullptr;
   size_t h_batch_bytes = 0;
@@ -127,6 +132,7 @@ struct sj_rel_s {
   uint64_t* d_n = nullptr;  // device row count (compacted relations), else null
   void* mem = nullptr;
   size_t mem_bytes = 0;
+  bool host_mapped = false;  // columns are page-locked host memory (SJ_HOST_MAPPED)
 };
 
 struct sj_filter_s {
@@ -783,6 +789,13 @@ sj_status sj_destroy(sj_ctx* c) {
   }
   for (auto& kv : c->graphs) drop_graph(kv.second);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->copy) {
+    cudaStreamSynchronize(c->copy);
+    cudaStreamDestroy(c->copy);
+  }
+  if (c->ev_copy_fork) cudaEventDestroy(c->ev_copy_fork);
+  for (auto e : c->ev_copied)
+    if (e) cudaEventDestroy(e);
   if (c->ev_ready) cudaEventDestroy(c->ev_ready);
   for (auto e : c->ev_built)
     if (e) cudaEventDestroy(e);
@@ -808,18 +821,34 @@ sj_status sj_load_relation(sj_ctx* c, int ncols, const int32_t* const* cols, int
   if (!c || !out || !cols) return fail(c, SJ_EINVAL, "null argument");
   if (ncols < 1 || ncols > SJ_MAX_COLS) return fail(c, SJ_EINVAL, "ncols out of range");
   if (nrows < 0 || nrows >= (int64_t(1) << 31)) return fail(c, SJ_EINVAL, "nrows out of range");
-  if (where < SJ_DEVICE_BORROW || where > SJ_HOST_COPY) return fail(c, SJ_EINVAL, "bad 'where'");
+  if (where < SJ_DEVICE_BORROW || where > SJ_HOST_MAPPED) return fail(c, SJ_EINVAL, "bad 'where'");
   for (int j = 0; j < ncols; ++j) {
     if (!cols[j] && nrows > 0) return fail(c, SJ_EINVAL, "null column pointer");
     if (where != SJ_HOST_COPY && (reinterpret_cast<uintptr_t>(cols[j]) & 15))
-      return fail(c, SJ_EINVAL, "device columns must be 16-byte aligned");
+      return fail(c, SJ_EINVAL, "columns must be 16-byte aligned");
   }
-  if (where == SJ_DEVICE_BORROW) {
+  if (where == SJ_DEVICE_BORROW || where == SJ_HOST_MAPPED) {
+    int32_t* dcols[SJ_MAX_COLS] = {};
+    for (int j = 0; j < ncols; ++j) {
+      dcols[j] = const_cast<int32_t*>(cols[j]);
+      if (where == SJ_HOST_MAPPED && cols[j]) {
+        // the device address of a page-locked host buffer (equal to the host
+        // address under unified addressing)
+        void* d = nullptr;
+        if (cudaHostGetDevicePointer(&d, const_cast<int32_t*>(cols[j]), 0) != cudaSuccess || !d) {
+          cudaGetLastError();
+          return fail(c, SJ_EINVAL, "SJ_HOST_MAPPED column is not page-locked host memory the device can address");
+        }
+        if (reinterpret_cast<uintptr_t>(d) & 15) return fail(c, SJ_EINVAL, "columns must be 16-byte aligned");
+        dcols[j] = static_cast<int32_t*>(d);
+      }
+    }
     sj_rel r = new sj_rel_s();
     r->ncols = ncols;
     r->nrows = nrows;
     r->cap = nrows;
-    for (int j = 0; j < ncols; ++j) r->cols[j] = const_cast<int32_t*>(cols[j]);
+    r->host_mapped = where == SJ_HOST_MAPPED;
+    for (int j = 0; j < ncols; ++j) r->cols[j] = dcols[j];
     *out = r;
     return SJ_OK;
   }
@@ -1065,9 +1094,112 @@ sj_status plan_pruning(sj_ctx* c, const sj_path* path, const Tree& tr, const sj_
   return SJ_OK;
 }
 
+// Columns of host-mapped relations that the query reads in full -- the
+// column a filter is built from before the relation's first sieve step, the
+// first tested column of that step, the join columns of a relation the
+// pruning never sieves -- are copied to the device on the context's copy
+// stream, relation by relation in the order the schedule first touches them,
+// each relation's copies followed by an event that the pruning waits on
+// before its first operation on that relation; so later copies overlap the
+// earlier relations' work, and each such column crosses the host link once
+// as one bulk copy.  Every other read of a mapped column (the surviving rows
+// a sieve step gathers, the terms of matching rows) stays on the host.
+// `staged` receives the path with those relations replaced by views over the
+// copies, and the events.
+struct StagedPath {
+  sj_path path{};
+  sj_rel rels[SJ_MAX_REL] = {};
+  cudaEvent_t ready[SJ_MAX_REL] = {};
+  std::vector<std::unique_ptr<sj_rel_s>> views;
+};
+
+sj_status ensure_copy_stream(sj_ctx* c) {
+  if (!c->copy && cudaStreamCreateWithFlags(&c->copy, cudaStreamNonBlocking) != cudaSuccess)
+    return fail(c, SJ_ECUDA, "copy stream creation failed");
+  if (!c->ev_copy_fork && cudaEventCreateWithFlags(&c->ev_copy_fork, cudaEventDisableTiming) != cudaSuccess)
+    return fail(c, SJ_ECUDA, "event creation failed");
+  for (auto& e : c->ev_copied)
+    if (!e && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+      return fail(c, SJ_ECUDA, "event creation failed");
+  return SJ_OK;
+}
+
+sj_status stage_mapped(sj_ctx* c, const sj_path* path, const sj_sieve_opts* opts, Temps& tmp,
+                       StagedPath* staged) {
+  staged->path = *path;
+  bool any = false;
+  for (int i = 0; i < path->nrel; ++i) {
+    staged->rels[i] = path->rels[i];
+    any = any || (path->rels[i] && path->rels[i]->host_mapped && path->rels[i]->nrows > 0);
+  }
+  staged->path.rels = staged->rels;
+  if (!any) return SJ_OK;
+  Tree tr;
+  SJ_TRY(validate_path(c, path, path->rels, &tr));
+  sj_sieve_opts o{};
+  if (opts) o = *opts;
+  PrunePlan pl;
+  SJ_TRY(plan_pruning(c, path, tr, o, &pl));
+  // full reads per column, and the order in which relations are first used
+  std::vector<std::vector<int>> reads(path->nrel, std::vector<int>(SJ_MAX_COLS, 0));
+  std::vector<char> stepped(path->nrel, 0), seen(path->nrel, 0);
+  std::vector<int> order;
+  for (const PruneOp& op : pl.ops) {
+    const int i = op.rel;
+    if (!seen[i]) {
+      seen[i] = 1;
+      order.push_back(i);
+    }
+    if (stepped[i]) continue;
+    if (op.type == kOpBuild) reads[i][op.col]++;
+    if (op.type == kOpStep) {
+      reads[i][op.pred ? path->preds[i].col : op.probes[0].first]++;
+      stepped[i] = 1;
+    }
+  }
+  for (int i = 0; i < path->nrel; ++i)
+    if (!stepped[i])
+      for (int e = 0; e + 1 < path->nrel; ++e) {
+        const sj_edge& E = path->edges[e];
+        if (E.rel_a == i) reads[i][E.col_a]++;
+        if (E.rel_b == i) reads[i][E.col_b]++;
+      }
+  SJ_TRY(ensure_copy_stream(c));
+  bool forked = false;
+  for (int i : order) {
+    const sj_rel_s* r = path->rels[i];
+    if (!r->host_mapped || r->nrows == 0) continue;
+    std::unique_ptr<sj_rel_s> v;
+    for (int j = 0; j < r->ncols; ++j) {
+      if (reads[i][j] < 1) continue;
+      if (!forked) {
+        // the copy stream starts after everything already on the context stream
+        SJ_CUDA(c, cudaEventRecord(c->ev_copy_fork, c->stream));
+        SJ_CUDA(c, cudaStreamWaitEvent(c->copy, c->ev_copy_fork, 0));
+        forked = true;
+      }
+      if (!v) v.reset(view_of(r));
+      sj_status st = SJ_OK;
+      int32_t* d = tmp.get<int32_t>((size_t)r->nrows, &st);
+      if (st != SJ_OK) return fail(c, st, "staging allocation failed");
+      SJ_CUDA(c, cudaMemcpyAsync(d, r->cols[j], (size_t)r->nrows * 4, cudaMemcpyHostToDevice, c->copy));
+      c->h2d_bytes += r->nrows * 4;
+      v->cols[j] = d;
+    }
+    if (v) {
+      SJ_CUDA(c, cudaEventRecord(c->ev_copied[i], c->copy));
+      staged->ready[i] = c->ev_copied[i];
+      staged->rels[i] = v.get();
+      staged->views.push_back(std::move(v));
+    }
+  }
+  return SJ_OK;
+}
+
 using FinalHook = std::function<sj_status(int rel, const sj_rel_s* r, int slot)>;
 sj_status sieve_path_impl(sj_ctx* c, const sj_path* path, const sj_sieve_opts* opts, sj_rel* out_sieved,
-                          sj_sieve_stats* stats, bool sync_end, const FinalHook* on_final = nullptr);
+                          sj_sieve_stats* stats, bool sync_end, const FinalHook* on_final = nullptr,
+                          const cudaEvent_t* ready = nullptr);
 }
 
 extern "C" sj_status sj_sieve_path(sj_ctx* c, const sj_path* path, const sj_sieve_opts* opts,
@@ -1095,8 +1227,11 @@ namespace {
 // The pruning phase.  With sync_end the call ends with one synchronisation and
 // every output handle knows its row count; without it the outputs keep their
 // counts on the device only (nrows = -1) for a device-sized join to read.
+// `ready` (optional, one per relation): an event the context stream waits on
+// before the first operation on that relation (its columns are being staged).
 sj_status sieve_path_impl(sj_ctx* c, const sj_path* path, const sj_sieve_opts* opts, sj_rel* out_sieved,
-                          sj_sieve_stats* stats, bool sync_end, const FinalHook* on_final) {
+                          sj_sieve_stats* stats, bool sync_end, const FinalHook* on_final,
+                          const cudaEvent_t* ready) {
   if (!c || !path || !out_sieved) return fail(c, SJ_EINVAL, "null argument");
   Tree tr;
   SJ_TRY(validate_path(c, path, path->rels, &tr));
@@ -1136,10 +1271,18 @@ sj_status sieve_path_impl(sj_ctx* c, const sj_path* path, const sj_sieve_opts* o
   };
   auto rel_of = [&](int i) -> const sj_rel_s* { return cur[i] ? cur[i] : path->rels[i]; };
   std::vector<char> cleared(fl.size(), 0);
+  std::vector<char> waited(n, 0);
   sj_status st = SJ_OK;
   for (size_t q = 0; q < ops.size() && st == SJ_OK; ++q) {
     const PruneOp& op = ops[q];
     const int i = op.rel;
+    if (ready && ready[i] && !waited[i]) {
+      waited[i] = 1;
+      if (cudaStreamWaitEvent(c->stream, ready[i], 0) != cudaSuccess) {
+        st = fail(c, SJ_ECUDA, "cudaStreamWaitEvent failed");
+        break;
+      }
+    }
     if (op.type == kOpFinal) {
       if (on_final) st = (*on_final)(i, rel_of(i), last_slot[i]);
     } else if (op.type == kOpBuild) {
@@ -1998,8 +2141,9 @@ sj_status join_impl(sj_ctx* c, const sj_path* path, const sj_rel* inputs, int mo
       ap.result = reinterpret_cast<unsigned long long*>(c->d_misc + kMiscResult);
       ap.status = status_ptr(c);
       {
-        const double per = 4.0 + (ap.psum_in ? 8.0 : 4.0 * ap.probe_terms.n);
-        Launch Lk(c, SJ_K_AGG, per * (double)ap.n);
+        // the key of every probe row; a matching row's terms are not counted
+        // (their count is not known on the host, and they are a few per cent)
+        Launch Lk(c, SJ_K_AGG, 4.0 * (double)ap.n);
         launch_agg_probe(ap, nsm, c->stream);
       }
       if ((st = check_launch(c, "k_agg_probe")) != SJ_OK) break;
@@ -2420,9 +2564,9 @@ sj_status join_async(sj_ctx* c, const sj_path* path, const sj_rel* in_rels, int 
       ap.result = reinterpret_cast<unsigned long long*>(c->d_misc + kMiscResult);
       ap.status = status_ptr(c);
       {
-        // key and SUM terms (or the partial sum) per probe row
-        Launch Lk = rows_launch(c, SJ_K_AGG, 4.0 + 4.0 * ap.probe_terms.n + (ap.psum_in ? 8.0 : 0.0),
-                                pslot, phost);
+        // the key of every probe row (a matching row's SUM terms or partial
+        // sum are read too but not counted: a few per cent of the rows)
+        Launch Lk = rows_launch(c, SJ_K_AGG, 4.0, pslot, phost);
         launch_agg_probe(ap, c->num_sms, c->stream);
       }
       SJ_TRY(check_launch(c, "k_agg_probe"));
@@ -2543,9 +2687,11 @@ uint64_t path_signature(const sj_path* p, const sj_sieve_opts* o, int mode, int 
   h = mix_in(h, (uint64_t)p->nrel);
   h = mix_in(h, (uint64_t)(int64_t)p->root);
   for (int i = 0; i < p->nrel; ++i) {
-    // the device addresses too: a graph of this shape reads them directly
+    // the device addresses, not the handle: a graph of this shape reads the
+    // columns directly, so a new handle over the same buffers (a relation
+    // reloaded each request) replays it; changed contents are caught by the
+    // buffer-overflow check of the device-sized run
     const sj_rel_s* r = p->rels[i];
-    h = mix_in(h, (uint64_t)reinterpret_cast<uintptr_t>(r));
     h = mix_in(h, (uint64_t)r->nrows);
     h = mix_in(h, (uint64_t)reinterpret_cast<uintptr_t>(r->d_n));
     for (int j = 0; j < r->ncols; ++j) h = mix_in(h, (uint64_t)reinterpret_cast<uintptr_t>(r->cols[j]));
@@ -2838,6 +2984,9 @@ sj_status run_device_sized(sj_ctx* c, const sj_path* path, const sj_sieve_opts* 
   sj_status st = SJ_OK;
   uint32_t* smallb = bt.get<uint32_t>(2 * SJ_MAX_REL, &st);
   if (st != SJ_OK) return fail(c, st, "allocation failed");
+  StagedPath sp;
+  SJ_TRY(stage_mapped(c, path, opts, bt, &sp));
+  path = &sp.path;
   std::vector<int> level_of(path->nrel, -1);
   for (int L = 0; L < nlev; ++L) level_of[plan[L].rel] = L;
   SJ_TRY(ensure_side(c, nlev));
@@ -2857,9 +3006,10 @@ sj_status run_device_sized(sj_ctx* c, const sj_path* path, const sj_sieve_opts* 
     SJ_CUDA(c, cudaEventRecord(c->ev_built[L], c->stream));
     return SJ_OK;
   };
-  st = sieve_path_impl(c, path, opts, sieved, nullptr, false, &hook);
+  st = sieve_path_impl(c, path, opts, sieved, nullptr, false, &hook, sp.ready);
   if (st == SJ_OK) st = join_async(c, path, sieved, nrefs, refs, caps, result, T, &built, finish, &rel_slot);
   if (c->side && !c->capturing) cudaStreamSynchronize(c->side);  // before the arena is released
+  if (c->copy && !c->capturing) cudaStreamSynchronize(c->copy);  // idem (a call that failed midway)
   return st;
 }
 
@@ -3042,9 +3192,15 @@ extern "C" sj_status sj_sieve_join(sj_ctx* c, const sj_path* path, const sj_siev
   }
   if (exact) {
     arena_begin(c);
-    st = sieve_path_impl(c, path, opts, sieved, stats, true);
-    if (st == SJ_OK) st = join_impl(c, path, sieved, mode, nrefs, refs, result, &T);
-    for (int i = 0; i < path->nrel; ++i) free_rel(c, sieved[i]);
+    {
+      Temps stage_mem(c);
+      StagedPath sp;
+      st = stage_mapped(c, path, opts, stage_mem, &sp);
+      if (st == SJ_OK) st = sieve_path_impl(c, &sp.path, opts, sieved, stats, true, nullptr, sp.ready);
+      if (st == SJ_OK) st = join_impl(c, &sp.path, sieved, mode, nrefs, refs, result, &T);
+      for (int i = 0; i < path->nrel; ++i) free_rel(c, sieved[i]);
+      if (c->copy) cudaStreamSynchronize(c->copy);  // before the arena is released
+    }
     arena_end(c);
   }
   if (st == SJ_OK && mode == SJ_COUNT_SUM && path->nrel >= 2) {

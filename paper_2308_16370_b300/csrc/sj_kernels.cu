@@ -1345,8 +1345,8 @@ __device__ __forceinline__ void add128(U128& x, uint64_t lo, uint64_t hi) {
 
 // Probe of the final level's (count, sum) table.  The common shape -- a long
 // probe relation whose SUM term is at most one int32 column -- takes 4 rows per
-// thread with the next 4 keys and terms already in flight, so each iteration
-// waits on two table round trips only.
+// thread with the next 4 keys already in flight, so each iteration waits on two
+// table round trips only; a row's term is read only if its key matches.
 __global__ void __launch_bounds__(kBlock, 4) k_agg_probe(AggProbeArgs a) {
   __shared__ uint64_t s_red[3][kBlock / 32];
   a.t = resolve(a.t);
@@ -1364,20 +1364,13 @@ __global__ void __launch_bounds__(kBlock, 4) k_agg_probe(AggProbeArgs a) {
     const int64_t n4 = a.n / 4;
     tail = n4 * 4;
     const int4* k4 = reinterpret_cast<const int4*>(a.keys);
-    const int4* v4 = reinterpret_cast<const int4*>(tcol);
-    int4 k = make_int4(0, 0, 0, 0), v = make_int4(0, 0, 0, 0);
-    if (tid < n4) {
-      k = __ldcs(k4 + tid);
-      if (tcol) v = __ldcs(v4 + tid);
-    }
+    int4 k = make_int4(0, 0, 0, 0);
+    if (tid < n4) k = __ldcs(k4 + tid);
     for (int64_t g = tid; g < n4; g += stride) {
-      int4 kn = make_int4(0, 0, 0, 0), vn = make_int4(0, 0, 0, 0);
-      if (g + stride < n4) {
-        kn = __ldcs(k4 + g + stride);
-        if (tcol) vn = __ldcs(v4 + g + stride);
-      }
+      int4 kn = make_int4(0, 0, 0, 0);
+      if (g + stride < n4) kn = __ldcs(k4 + g + stride);
       const int32_t kk[4] = {k.x, k.y, k.z, k.w};
-      const int32_t vv[4] = {v.x, v.y, v.z, v.w};
+      int32_t vv[4];
       uint32_t b[4];
       ulonglong2 q[4];
 #pragma unroll
@@ -1388,16 +1381,20 @@ __global__ void __launch_bounds__(kBlock, 4) k_agg_probe(AggProbeArgs a) {
       int64_t sl[4];
 #pragma unroll
       for (int e = 0; e < 4; ++e) sl[e] = table_find_first(a.t, kk[e], b[e], q[e]);
+      // the SUM term of a row is read only when its key matches (a few per
+      // cent of the rows here), so the term column is not streamed
       ulonglong2 cs[4];
 #pragma unroll
-      for (int e = 0; e < 4; ++e) cs[e] = sl[e] >= 0 ? __ldg(a.cs + sl[e]) : make_ulonglong2(0ull, 0ull);
+      for (int e = 0; e < 4; ++e) {
+        cs[e] = sl[e] >= 0 ? __ldg(a.cs + sl[e]) : make_ulonglong2(0ull, 0ull);
+        vv[e] = (sl[e] >= 0 && tcol) ? __ldcs(tcol + 4 * g + e) : 0;
+      }
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         add128(cnt, cs[e].x, 0);
         sum += (uint64_t)(int64_t)vv[e] * cs[e].x + cs[e].y;
       }
       k = kn;
-      v = vn;
     }
   }
   for (int64_t i = tail + tid; i < a.n; i += stride) {

@@ -6,6 +6,8 @@ bit, sieved relations row for row in input order, COUNT and SUM (int64 mod
 unspecified).  Sizes span several tiles (4096 rows per sieve tile) with ragged
 tails, plus the full-size workloads on exact or sampled checks.
 """
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -482,3 +484,35 @@ def test_graphs_disabled_still_exact(ctx):
         got = ctx.sieve_join(rels, w["edges"], w["preds"], w["root"], refs=w["sum"])
         assert (got["count"], got["sum"]) == (exp["count"], exp["sum"])
     assert ctx.graph_stats()["replays"] - g1["replays"] == 2
+
+
+def test_host_mapped_relations_equal_device_and_oracle(ctx):
+    """Relations left in pinned host memory (SJ_HOST_MAPPED), read by the
+    kernels over the host link: new handles over the same buffers on every
+    call (exact, device-sized, then graph-replay paths) give the oracle's
+    COUNT and SUM; the pruning over them equals the oracle's row for row;
+    pageable memory is rejected."""
+    import torch
+    w = inputs.zipf_chain(nrows=1_000_000, domain=500_000)
+    host = [[torch.from_numpy(c).pin_memory() for c in r] for r in w["rels"]]
+    exp = oracle.agg_propagation(w)
+    for params in (dict(bits_per_key=8, k=4, layout=sj.REGBLOCKED32, passes=sj.BWD_ONLY), dict()):
+        for _ in range(4):
+            rels = [ctx.load_relation(cols, where="mapped") for cols in host]
+            r = ctx.sieve_join(rels, w["edges"], w["preds"], w["root"], refs=w["sum"], **params)
+            assert (r["count"], r["sum"]) == (exp["count"], exp["sum"])
+            for x in rels:
+                x.free()
+    rels = [ctx.load_relation(cols, where="mapped") for cols in host]
+    sv, st = ctx.sieve_path(rels, w["edges"], w["preds"], w["root"])
+    osv, osteps = oracle.sieve_path(w)
+    assert st["steps"] == [tuple(s) for s in osteps]
+    for i in range(len(rels)):
+        assert_rel_equal(rel_np(sv[i]), osv[i])
+    with pytest.raises(ValueError):
+        ctx.load_relation([torch.zeros(1024, dtype=torch.int32)], where="mapped")
+    lib = sj.load_library()
+    pageable = np.zeros(1024, dtype=np.int32)
+    ptrs = (ctypes.c_void_p * 1)(pageable.ctypes.data)
+    h = ctypes.c_void_p()
+    assert lib.sj_load_relation(ctx.ctx, 1, ptrs, 1024, sj.HOST_MAPPED, ctypes.byref(h)) == 1
