@@ -693,10 +693,10 @@ def cyclic_run(torch, sj, ctx, stream):
         ms = float(np.median(times))
         # algorithmic bytes of the enumeration: each pruned edge read (8 B) and
         # its two adjacency lookups (2 x 32 B sectors), each candidate wedge's
-        # adjacency entry and far endpoint (8 B), and a 32 B pair-set sector
-        # for each candidate the pair filter passes (the filter itself is
-        # L2-resident and not counted)
-        alg = (8.0 + 64.0) * st["edges_sieved"] + 8.0 * st["candidates"] + 32.0 * st["filter_passed"]
+        # far endpoint (4 B, read contiguously from the neighbour array), and a
+        # 32 B pair-set sector for each candidate the pair filter passes (the
+        # filter itself is L2-resident and not counted)
+        alg = (8.0 + 64.0) * st["edges_sieved"] + 4.0 * st["candidates"] + 32.0 * st["filter_passed"]
         gbps = alg / (ms / 1000.0) / 1e9
         out[key] = {"ms": ms, "triangles": int(counts.sum()),
                     "edges_after_sieve": st["edges_sieved"], "closing_pairs_checked": st["candidates"],

@@ -2898,6 +2898,17 @@ extern "C" sj_status sj_triangles(sj_ctx* c, sj_rel edges, int nsub, const int32
   Adjacency out{}, in{};
   SJ_TRY(build_adjacency(c, tmp, E->cols[0], ne, &out));
   SJ_TRY(build_adjacency(c, tmp, E->cols[1], ne, &in));
+  // each adjacency's far endpoints in its own row order, so the enumeration
+  // reads them contiguously instead of one random edge lookup per candidate
+  int32_t* out_nbr = tmp.get<int32_t>((size_t)ne, &st);
+  int32_t* in_nbr = tmp.get<int32_t>((size_t)ne, &st);
+  if (st != SJ_OK) return fail(c, st, "neighbour array allocation failed");
+  {
+    Launch L(c, SJ_K_HT_BUILD, 24.0 * (double)ne);
+    launch_gather_i32(E->cols[1], out.rows, ne, out_nbr, c->num_sms, c->stream);
+    launch_gather_i32(E->cols[0], in.rows, ne, in_nbr, c->num_sms, c->stream);
+  }
+  SJ_TRY(check_launch(c, "k_gather_i32"));
 
   // closing-pair filter, rebuilt from the pruned edges (Sec. 2.3)
   uint64_t nb = ((uint64_t)fp.bits_per_key * (uint64_t)ne + 255) / 256;
@@ -2935,6 +2946,8 @@ extern "C" sj_status sj_triangles(sj_ctx* c, sj_rel edges, int nsub, const int32
   ta.ne = ne;
   ta.out = out;
   ta.in = in;
+  ta.out_nbr = out_nbr;
+  ta.in_nbr = in_nbr;
   ta.pf.words = pf.words;
   ta.pf.hdr = pf.hdr;
   ta.pf.k = fp.k;

@@ -1583,11 +1583,12 @@ __global__ void __launch_bounds__(kBlock) k_triangles(TriangleArgs a) {
       const int32_t A = __shfl_sync(0xffffffffu, va, j);
       const int32_t B = __shfl_sync(0xffffffffu, vb, j);
       const int SB = __shfl_sync(0xffffffffu, sub, j);
-      const int32_t* rows = S ? a.in.rows : a.out.rows;
+      // the far endpoints, read contiguously from the neighbour arrays
+      const int32_t* nbr = S ? a.in_nbr : a.out_nbr;
       unsigned long long found = 0;
       for (uint32_t t = lane; t < L; t += 32) {
-        const int32_t row = __ldg(rows + O + t);
-        const uint64_t pair = S ? pack_pair(B, __ldg(a.src + row)) : pack_pair(__ldg(a.dst + row), A);
+        const int32_t v = __ldg(nbr + O + t);
+        const uint64_t pair = S ? pack_pair(B, v) : pack_pair(v, A);
         ++checked;
         const uint64_t h = fmix64(pair ^ a.pf.seed);
         const uint32_t m = reg32_mask((uint32_t)h, a.pf.k);
@@ -1613,6 +1614,13 @@ __global__ void __launch_bounds__(kBlock) k_triangles(TriangleArgs a) {
   __syncthreads();
   for (int i = threadIdx.x; i < a.nsub; i += blockDim.x)
     if (s_cnt[i]) atomicAdd(a.counts + i, s_cnt[i]);
+}
+
+__global__ void __launch_bounds__(kBlock) k_gather_i32(const int32_t* col, const int32_t* idx, int64_t n,
+                                                      int32_t* out) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    out[i] = __ldg(col + __ldg(idx + i));
 }
 
 // Self-test of the bounded waits: one warp polls `flag` (which nothing sets)
@@ -1770,6 +1778,11 @@ void launch_pair_filter_build(const PairFilterBuildArgs& a, int num_sms, cudaStr
 
 void launch_pairset_insert(const PairSetArgs& a, int num_sms, cudaStream_t s) {
   k_pairset_insert<<<host_grid(a.n, kBlock, num_sms * 8), kBlock, 0, s>>>(a);
+}
+
+void launch_gather_i32(const int32_t* col, const int32_t* idx, int64_t n, int32_t* out, int num_sms,
+                       cudaStream_t s) {
+  k_gather_i32<<<host_grid(n, kBlock * 4, num_sms * 8), kBlock, 0, s>>>(col, idx, n, out);
 }
 
 void launch_triangles(const TriangleArgs& a, int num_sms, cudaStream_t s) {

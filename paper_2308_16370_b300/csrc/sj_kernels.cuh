@@ -311,6 +311,8 @@ struct TriangleArgs {
   int64_t ne;
   Adjacency out;            // keyed by src
   Adjacency in;             // keyed by dst
+  const int32_t* out_nbr;   // dst of out.rows[t], in the same order (read contiguously)
+  const int32_t* in_nbr;    // src of in.rows[t], in the same order
   FilterView pf;            // pair filter (register-blocked)
   Table pairs;              // exact pair set
   const int32_t* cuts;      // nsub + 1, increasing
@@ -320,5 +322,8 @@ struct TriangleArgs {
   unsigned long long* work;     // edge cursor, zeroed
 };
 void launch_triangles(const TriangleArgs& a, int num_sms, cudaStream_t s);
+// out[i] = col[idx[i]] for i < n.
+void launch_gather_i32(const int32_t* col, const int32_t* idx, int64_t n, int32_t* out, int num_sms,
+                       cudaStream_t s);
 
 }  // namespace sj
