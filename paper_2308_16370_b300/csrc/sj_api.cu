@@ -80,6 +80,7 @@ struct sj_ctx {
     std::vector<uint64_t> caps;
     uint64_t gen = 0;
     int64_t nkernels = 0;
+    int64_t h2d_bytes = 0;      // host-to-device copies inside the graph (staged columns)
     bool failed = false;        // capture not possible for this shape
     std::vector<ProfRec> prof;  // launch events inside the graph (profiled capture); owned
   };
@@ -3033,7 +3034,7 @@ void capture_graph(sj_ctx* c, uint64_t key, const sj_path* path, const sj_sieve_
   auto& G = c->graphs[key];
   drop_graph(G);
   G.failed = true;
-  const int64_t launches0 = c->launches, d2h0 = c->d2h_bytes;
+  const int64_t launches0 = c->launches, d2h0 = c->d2h_bytes, h2d0 = c->h2d_bytes;
   const size_t prof0 = c->prof.size(), ev0 = c->ev_used;
   arena_begin(c);
   const uint64_t gen = c->arena_gen;
@@ -3077,6 +3078,7 @@ void capture_graph(sj_ctx* c, uint64_t key, const sj_path* path, const sj_sieve_
       G.failed = false;
       G.caps = caps;
       G.nkernels = c->launches - launches0;
+      G.h2d_bytes = c->h2d_bytes - h2d0;
     } else {
       if (ei != cudaSuccess) note_graph_failure(c, std::string("instantiate: ") + cudaGetErrorString(ei));
       G.exec = nullptr;
@@ -3107,6 +3109,7 @@ void capture_graph(sj_ctx* c, uint64_t key, const sj_path* path, const sj_sieve_
   else c->graph_captures++;
   c->launches = launches0;
   c->d2h_bytes = d2h0;
+  c->h2d_bytes = h2d0;
 }
 
 }  // namespace
@@ -3142,6 +3145,7 @@ extern "C" sj_status sj_sieve_join(sj_ctx* c, const sj_path* path, const sj_siev
       }
       c->launches += g->second.nkernels;
       c->d2h_bytes += kMiscWords * sizeof(uint64_t);
+      c->h2d_bytes += g->second.h2d_bytes;
       c->graph_replays++;
       if (c->prof_on) prof_replay(c, g->second);
       st = read_status(c);
