@@ -409,8 +409,10 @@ typedef struct {
  * and whose source has an in-edge.  Enumeration follows Sec. 2.3's cyclic
  * case: the filter of the closing condition -- here over the packed pair
  * (c, a) -- is rebuilt on the fly from the pruned edges and screens every
- * wedge before an exact pair-set lookup; each wedge is walked from the
- * shorter of out(b) and in(a).  The pair filter uses the register-blocked
+ * wedge before an exact pair-set lookup.  Each directed 3-cycle is walked
+ * once, from its smallest vertex a (an edge a -> b with a < b, then c > a
+ * from the shorter of out(b) and in(a)), and its three ordered answers are
+ * added to the subqueries of a, b and c.  The pair filter uses the register-blocked
  * layout with `params`' bits_per_key, k (<= 6) and seed (NULL = defaults).
  * 1 <= nsub <= 256; `cuts` (nsub + 1 increasing values) and `counts` are host
  * arrays.  Synchronises.  Errors: SJ_EINVAL, SJ_ENOMEM, SJ_ETABLEFULL, SJ_ECUDA.

@@ -1539,6 +1539,22 @@ __device__ __forceinline__ void adj_of(const Adjacency& g, int32_t v, uint64_t* 
 // the pair (c, a) [walking out(b)] or (b, c) [walking in(a)] is an edge: the
 // pair filter screens it, the pair set confirms it.  Counts go to the
 // subquery whose vertex range holds a.
+// Each directed 3-cycle x -> y -> z -> x (distinct vertices: the edges are
+// distinct and hold no self-loops) is the three ordered answers (x, y, z),
+// (y, z, x) and (z, x, y).  It is enumerated once, from its smallest vertex:
+// an edge (a, b) with a < b, and a third vertex c > a from the shorter of
+// out(b) and in(a), checked against the closing pair (c, a) or (b, c); the
+// three answers are then added to the subqueries of a, b and c.
+__device__ __forceinline__ int sub_of(const int32_t* s_cuts, int nsub, int32_t v) {
+  int lo = 0, hi = nsub;  // largest i with cuts[i] <= v
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (s_cuts[mid] <= v) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo < nsub ? lo : nsub - 1;
+}
+
 __global__ void __launch_bounds__(kBlock) k_triangles(TriangleArgs a) {
   __shared__ int32_t s_cuts[257];
   __shared__ unsigned long long s_cnt[256];
@@ -1554,26 +1570,21 @@ __global__ void __launch_bounds__(kBlock) k_triangles(TriangleArgs a) {
     base = __shfl_sync(0xffffffffu, base, 0);
     if (base >= (unsigned long long)a.ne) break;
     const int64_t e = (int64_t)base + lane;
-    int32_t va = 0, vb = 0, sub = 0;
+    int32_t va = 0, vb = 0;
     uint64_t off = 0;
     uint32_t len = 0, side = 0;
     if (e < a.ne) {
       va = __ldg(a.src + e);
       vb = __ldg(a.dst + e);
-      uint64_t o1, o2;
-      uint32_t l1, l2;
-      adj_of(a.out, vb, &o1, &l1);
-      adj_of(a.in, va, &o2, &l2);
-      side = l1 <= l2 ? 0u : 1u;
-      off = side ? o2 : o1;
-      len = side ? l2 : l1;
-      int lo = 0, hi = a.nsub;  // largest i with cuts[i] <= va
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (s_cuts[mid] <= va) lo = mid;
-        else hi = mid - 1;
+      if (va < vb) {  // a is the cycle's smallest vertex only if a < b
+        uint64_t o1, o2;
+        uint32_t l1, l2;
+        adj_of(a.out, vb, &o1, &l1);
+        adj_of(a.in, va, &o2, &l2);
+        side = l1 <= l2 ? 0u : 1u;
+        off = side ? o2 : o1;
+        len = side ? l2 : l1;
       }
-      sub = lo < a.nsub ? lo : a.nsub - 1;
     }
     for (int j = 0; j < 32; ++j) {
       const uint32_t L = __shfl_sync(0xffffffffu, len, j);
@@ -1582,24 +1593,30 @@ __global__ void __launch_bounds__(kBlock) k_triangles(TriangleArgs a) {
       const uint32_t S = __shfl_sync(0xffffffffu, side, j);
       const int32_t A = __shfl_sync(0xffffffffu, va, j);
       const int32_t B = __shfl_sync(0xffffffffu, vb, j);
-      const int SB = __shfl_sync(0xffffffffu, sub, j);
       // the far endpoints, read contiguously from the neighbour arrays
       const int32_t* nbr = S ? a.in_nbr : a.out_nbr;
       unsigned long long found = 0;
       for (uint32_t t = lane; t < L; t += 32) {
         const int32_t v = __ldg(nbr + O + t);
+        if (v <= A || v == B) continue;  // c must be above a (and differ from b)
         const uint64_t pair = S ? pack_pair(B, v) : pack_pair(v, A);
         ++checked;
         const uint64_t h = fmix64(pair ^ a.pf.seed);
         const uint32_t m = reg32_mask((uint32_t)h, a.pf.k);
         if ((__ldg(a.pf.words + reg32_word(h, pnb * 8)) & m) == m) {
           ++passed;
-          if (pairset_contains(a.pairs, pair)) ++found;
+          if (pairset_contains(a.pairs, pair)) {
+            ++found;
+            atomicAdd(s_cnt + sub_of(s_cuts, a.nsub, v), 1ull);
+          }
         }
       }
 #pragma unroll
       for (int d = 16; d > 0; d >>= 1) found += __shfl_xor_sync(0xffffffffu, found, d);
-      if (lane == 0 && found) atomicAdd(s_cnt + SB, found);
+      if (lane == 0 && found) {
+        atomicAdd(s_cnt + sub_of(s_cuts, a.nsub, A), found);
+        atomicAdd(s_cnt + sub_of(s_cuts, a.nsub, B), found);
+      }
     }
   }
 #pragma unroll
