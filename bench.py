@@ -294,13 +294,14 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------- steps
 TUNED = {}
+TUNED_ROOT = []  # the autotuner's sieve order (root relation), when it ran
 
 
 def sieved_step(ctx, rels, w, stats=False):
     """Pruning then enumeration in one library call (sj_sieve_join), with the
     autotuned filter parameters and schedule when tuning ran."""
-    res = ctx.sieve_join(rels, w["edges"], w["preds"], w["root"], refs=w["sum"], stats=stats,
-                         **TUNED)
+    root = TUNED_ROOT[0] if TUNED_ROOT else w["root"]
+    res = ctx.sieve_join(rels, w["edges"], w["preds"], root, refs=w["sum"], stats=stats, **TUNED)
     return res, res.get("steps")
 
 
@@ -854,7 +855,8 @@ def main():
         tr = autotune.tune(ctx, rels, w["edges"], w["preds"], w["root"], w["sum"], reps=9,
                            use_cache=False, flush=flush)
         TUNED.update(tr["params"])
-        tune_info = {"params": tr["params"], "candidates": len(tr["timings"]),
+        TUNED_ROOT[:] = [tr["root"]]
+        tune_info = {"params": tr["params"], "root": tr["root"], "candidates": len(tr["timings"]),
                      "best_ms_untimed_loop": tr["ms"]}
     # per-step statistics of the timed path, once, before timing (the tests check
     # the same path against the oracle)
@@ -921,7 +923,8 @@ def main():
     fwd_bwd = None
     if TUNED.get("passes", sj.FWD_BWD) != sj.FWD_BWD:
         fb = dict(TUNED, passes=sj.FWD_BWD)
-        fone = lambda: ctx.sieve_join(rels, w["edges"], w["preds"], w["root"], refs=w["sum"], **fb)
+        froot = TUNED_ROOT[0] if TUNED_ROOT else w["root"]
+        fone = lambda: ctx.sieve_join(rels, w["edges"], w["preds"], froot, refs=w["sum"], **fb)
         fsteps = max(3, min(args.steps, 20))
         fms, fres = timed(torch, stream, fone, fsteps, 4, flush, ws)
         assert (fres["count"], fres["sum"]) == (res["count"], res["sum"])
@@ -1012,6 +1015,7 @@ def main():
                    "count": res["count"], "sum": res["sum"],
                    "sieve_steps": [list(s) for s in steps0],
                    "filter_params": dict(TUNED) or "defaults (8 bits/key, k=3, register-blocked, fwd+bwd)",
+                   "sieve_root": TUNED_ROOT[0] if TUNED_ROOT else w["root"],
                    "autotune": tune_info,
                    "default_params_ms_per_step": default_ms,
                    "sieved_intermediate_tuples": res["intermediate"]},

@@ -1,5 +1,6 @@
 """Autotuner for the sieved join: filter size (bits per key), hash count k,
-filter layout and sieve schedule.
+filter layout, sieve schedule and sieve order (the relation the pruning
+passes are rooted at).
 
 The paper fixes none of these (Sec. 2.1 sizes Bloomjoin's filter at one bit
 per tuple; Sec. 2.2 leaves the second pruning pass optional).  The tuner times
@@ -23,6 +24,7 @@ DEFAULT_CANDIDATES = {
     "k": (2, 3, 4),
     "layout": (REGBLOCKED32, BLOCKED256),
     "passes": (FWD_BWD, BWD_ONLY),
+    "root": "all",  # relation indices to root the passes at, or "all"
 }
 
 
@@ -57,9 +59,11 @@ def _store(path, data):
 
 def tune(ctx, rels, edges, preds=None, root=-1, refs=(), candidates=None, reps=3,
          use_cache=True, path=None, flush=None):
-    """Return {"params": {...}, "ms": best, "timings": [...], "cached": bool}.
+    """Return {"params": {...}, "root": r, "ms": best, "timings": [...], "cached": bool}.
 
-    ``params`` holds bits_per_key, k, layout and passes for ``sieve_join``.
+    ``params`` holds bits_per_key, k, layout and passes for ``sieve_join``;
+    ``root`` is the relation to root the pruning passes at (the sieve order;
+    the join result does not depend on it).
     ``flush``: a device tensor larger than L2, zeroed before every timed
     repetition so that candidates are timed with inputs coming from HBM.
     """
@@ -68,18 +72,22 @@ def tune(ctx, rels, edges, preds=None, root=-1, refs=(), candidates=None, reps=3
     gpu = torch.cuda.get_device_name(ctx.device)
     key = shape_key(gpu, rels, edges, root)
     cache = _load(path) if use_cache else {}
-    if use_cache and key in cache:
+    if use_cache and key in cache and "root" in cache[key]:
         return {**cache[key], "cached": True}
     cand = dict(DEFAULT_CANDIDATES)
     cand.update(candidates or {})
     timings = []
     reference = None
     stream = ctx.stream
-    for bpk, k, layout, passes in itertools.product(cand["bits_per_key"], cand["k"],
-                                                    cand["layout"], cand["passes"]):
+    roots = cand["root"]
+    if roots == "all":
+        roots = tuple(range(len(rels)))
+    for r, bpk, k, layout, passes in itertools.product(roots, cand["bits_per_key"], cand["k"],
+                                                       cand["layout"], cand["passes"]):
         if layout == BLOCKED256 and k > 4:
             continue
         kw = dict(bits_per_key=bpk, k=k, layout=layout, passes=passes)
+        root = int(r)
         # warm-up: the first call of a shape is the exact path, the next ones
         # size their buffers from the previous run; the third captures the
         # CUDA graph that the timed repetitions replay
@@ -103,9 +111,9 @@ def tune(ctx, rels, edges, preds=None, root=-1, refs=(), candidates=None, reps=3
             e1.record(stream)
             torch.cuda.synchronize()
             ts.append(e0.elapsed_time(e1))
-        timings.append({"params": kw, "ms": sorted(ts)[len(ts) // 2]})
+        timings.append({"params": kw, "root": root, "ms": sorted(ts)[len(ts) // 2]})
     best = min(timings, key=lambda t: t["ms"])
-    out = {"params": best["params"], "ms": best["ms"], "timings": timings}
+    out = {"params": best["params"], "root": best["root"], "ms": best["ms"], "timings": timings}
     if use_cache:
         cache = _load(path)
         cache[key] = out
