@@ -975,27 +975,29 @@ def main():
                              "path": "every column copied to the device (SJ_HOST_COPY), then the query"}}
 
     chain3 = None
-    if not args.no_chain3:
+    # the other configurations once, at N = 1 (a replica run needs only the step)
+    extras = ws == 1
+    if extras and not args.no_chain3:
         chain3 = chain3_run(torch, sj, ctx, stream)
 
     serving = None
-    if not args.no_serve:
+    if extras and not args.no_serve:
         serving = serving_run(args, torch, sj)
 
     cyclic = None
-    if not args.no_cyclic:
+    if extras and not args.no_cyclic:
         cyclic = cyclic_run(torch, sj, ctx, stream)
 
     star = None
-    if not args.no_star:
+    if extras and not args.no_star:
         star = star_run(torch, sj, ctx, stream)
 
     rst = None
-    if not args.no_rst:
+    if extras and not args.no_rst:
         rst = freitag_run(torch, sj, ctx, stream)
 
     cpu = None
-    if rank == 0 and not args.no_cpu:
+    if rank == 0 and ws == 1 and not args.no_cpu:
         cpu = cpu_oracle_run(spec, w, res)
 
     if rank != 0:
