@@ -169,7 +169,7 @@ class _CtypesNvml:
 
 class ClockSampler:
     """SM clock and throttle reasons sampled during the timed region: NVML
-    queries every few milliseconds from a thread (read-only), or nvidia-smi's
+    queries every half millisecond from a thread (read-only), or nvidia-smi's
     query loop where NVML is unavailable."""
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -213,7 +213,7 @@ class ClockSampler:
                 self.lines.append(", ".join([str(sm), str(mx), "", hex(r)] + flags))
             except Exception:
                 pass
-            time.sleep(0.002)
+            time.sleep(0.0005)
 
     def __enter__(self):
         try:
