@@ -471,21 +471,57 @@ __device__ __forceinline__ void ck_test_reg32(const uint32_t* words, uint32_t nw
   }
 }
 
-// Any tests: predicates and filters of every layout, later tests loading only
-// the rows still alive.
+// One row against one test (any layout, or a range predicate).
+__device__ __forceinline__ bool test_one(const SieveTest& t, int32_t key) {
+  if (t.is_pred) return key >= t.lo && key < t.hi;
+  return filter_contains(t.f, __ldg(t.f.hdr), key);
+}
+
+// Any tests: predicates and filters of every layout.  The first test runs on
+// the tile's 8 keys per lane; the rows it keeps are listed in the warp's
+// shared-memory list (`wlist`, 256 entries) and each lane then takes one of
+// them, loading its keys for all remaining tests at once and testing them
+// together (one dependent round instead of one per test); survivors set
+// their bit in the warp's 8 words `wbits` (row order).
 __device__ __forceinline__ void ck_test_generic(const SieveArgs& a, int32_t (&key)[8], int64_t base,
-                                                int64_t n, int lane, uint32_t (&b)[8]) {
+                                                int64_t n, int lane, uint32_t (&b)[8], uint16_t* wlist,
+                                                uint32_t* wbits) {
   uint32_t alive = 0;
 #pragma unroll
   for (int j = 0; j < 8; ++j) alive |= (base + 32 * j + lane < n) ? (1u << j) : 0u;
   if (a.ntest > 0) alive = test8<0>(a.test[0], key, alive);
-#pragma unroll 1
-  for (int t = 1; t < a.ntest; ++t) {
-    if (!__any_sync(0xffffffffu, alive != 0u)) break;
-    const int32_t* p = a.test[t].col + base + lane;
+  if (a.ntest > 1) {
+    const uint32_t c = __popc(alive);
+    uint32_t inc = c;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) key[j] = ((alive >> j) & 1u) ? __ldcs(p + 32 * j) : 0;
-    alive = test8<0>(a.test[t], key, alive);
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, inc, d);
+      if (lane >= d) inc += y;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, inc, 31);
+    uint32_t pos = inc - c;
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if ((alive >> j) & 1u) wlist[pos++] = (uint16_t)(32 * j + lane);
+    if (lane < 8) wbits[lane] = 0u;
+    __syncwarp();
+    for (uint32_t r = lane; r < total; r += 32) {
+      const uint32_t row = wlist[r];
+      int32_t k[kMaxTests];
+#pragma unroll
+      for (int t = 1; t < kMaxTests; ++t)
+        k[t] = t < a.ntest ? __ldcs(a.test[t].col + base + row) : 0;
+      bool ok = true;
+#pragma unroll
+      for (int t = 1; t < kMaxTests; ++t)
+        if (t < a.ntest) ok &= test_one(a.test[t], k[t]);
+      if (ok) atomicOr(wbits + (row >> 5), 1u << (row & 31));
+    }
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < 8; ++j) b[j] = wbits[j];
+    __syncwarp();  // wlist and wbits serve the warp's next tile
+    return;
   }
 #pragma unroll
   for (int j = 0; j < 8; ++j) b[j] = __ballot_sync(0xffffffffu, (alive >> j) & 1u);
@@ -650,11 +686,13 @@ struct CkSmem {
   static constexpr int kMaxTiles = kCkMaxRows / kCkTileRows;
   __align__(16) uint32_t bits[kMaxTiles * 8];
   uint32_t toff[kMaxTiles + 1];
-  uint16_t list[kCkList];
+  uint16_t list[kCkList];               // phase 1: each warp's 256-entry row list (generic tests)
+  uint32_t wbits[kCkThreads / 32][8];   // phase 1: each warp's survivor words (generic tests)
   Vec<1> warp[kCkThreads / 32];
   uint64_t red[kCkThreads / 32];
   int stop;
 };
+static_assert(kCkList >= (kCkThreads / 32) * kCkTileRows, "a warp's row list needs 256 entries");
 
 // Chunk t of the sieve step `a` (steps 1-6 of k_sieve_chunk); every thread of
 // the CTA calls it.
@@ -708,7 +746,7 @@ __device__ __forceinline__ void ck_run_chunk(const SieveArgs& a, uint32_t t, CkS
       if (Tn < ntile && col0) ck_load8(col0, cbase + (int64_t)Tn * kCkTileRows, n, lane, nxt);
       uint32_t b[8];
       if (K > 0) ck_test_reg32<(K > 0 ? K : 1)>(a.test[0].f.words, nwords, hf, pol, cur, base, n, lane, b);
-      else ck_test_generic(a, cur, base, n, lane, b);
+      else ck_test_generic(a, cur, base, n, lane, b, s_list + warp * kCkTileRows, sm.wbits[warp]);
       if (lane == 0) {
         uint4* d = reinterpret_cast<uint4*>(s_bits + T * 8);
         d[0] = make_uint4(b[0], b[1], b[2], b[3]);
