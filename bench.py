@@ -169,7 +169,8 @@ class _CtypesNvml:
 
 class ClockSampler:
     """SM clock and throttle reasons sampled during the timed region: NVML
-    queries every half millisecond from a thread (read-only), or nvidia-smi's
+    queries every two milliseconds from a thread (read-only, plus one at the
+    end of the region), or nvidia-smi's
     query loop where NVML is unavailable."""
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -184,6 +185,7 @@ class ClockSampler:
         self.lines = []
         self.skip = 0
         self.nvml = None
+        self.max_mhz = None
         self.stop = False
         self.source = None
 
@@ -200,20 +202,24 @@ class ClockSampler:
         except Exception:
             return pynvml, pynvml.nvmlDeviceGetHandleByIndex(self.device)
 
-    def _nvml_loop(self):
+    def _nvml_sample(self):
         nv, h = self.nvml
-        mx = nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM)
+        try:
+            if self.max_mhz is None:
+                self.max_mhz = nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM)
+            sm = nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM)
+            r = nv.nvmlDeviceGetCurrentClocksThrottleReasons(h)
+            flags = ["Active" if r & b else "Not Active" for b in
+                     (self.REASON_BITS["hw_slowdown"], self.REASON_BITS["hw_thermal_slowdown"],
+                      self.REASON_BITS["sw_thermal_slowdown"], self.REASON_BITS["sw_power_cap"])]
+            self.lines.append(", ".join([str(sm), str(self.max_mhz), "", hex(r)] + flags))
+        except Exception:
+            pass
+
+    def _nvml_loop(self):
         while not self.stop:
-            try:
-                sm = nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM)
-                r = nv.nvmlDeviceGetCurrentClocksThrottleReasons(h)
-                flags = ["Active" if r & b else "Not Active" for b in
-                         (self.REASON_BITS["hw_slowdown"], self.REASON_BITS["hw_thermal_slowdown"],
-                          self.REASON_BITS["sw_thermal_slowdown"], self.REASON_BITS["sw_power_cap"])]
-                self.lines.append(", ".join([str(sm), str(mx), "", hex(r)] + flags))
-            except Exception:
-                pass
-            time.sleep(0.0005)
+            self._nvml_sample()
+            time.sleep(0.002)
 
     def __enter__(self):
         try:
@@ -249,6 +255,7 @@ class ClockSampler:
         self.stop = True
         if self.nvml:
             self.th.join(timeout=2)
+            self._nvml_sample()  # the end of the region (short regions get few samples)
         if self.proc:
             self.proc.terminate()
             try:
