@@ -6,10 +6,14 @@
 //   k_sieve_chunk    -- one pruning step (Sec. 2.2): key loads, filter probes,
 //                       survivor bits by warp ballots, order-preserving
 //                       compaction with a CTA-wide decoupled look-back
+//   k_sieve_batch, k_bloom_build_batch -- the sieve steps / filter builds of
+//                       many queries' pruning phases in one launch each
+//   k_insert_*       -- insert maintenance of a built filter (Sec. 2.4)
 //   k_group_offsets  -- row-group offsets of a multimap (one atomic per tile)
 //   k_mm_*           -- multimap hash join level (Sec. 2.2 enumeration phase)
 //   k_agg_*          -- last join level folded into COUNT(*) / SUM
-//   k_pair_*, k_triangles -- the cyclic query with its closing filter (Sec. 2.3)
+//   k_pair_*, k_gather_i32, k_triangles -- the cyclic query with its closing
+//                       filter (Sec. 2.3)
 //
 // Nothing here is a dense contraction, so there are no tensor-core paths: all
 // kernels are bound by HBM bandwidth or by L2 latency of random accesses.
