@@ -68,6 +68,7 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving run")
     ap.add_argument("--no-chain3", action="store_true", help="skip the 3-way chain latency run")
+    ap.add_argument("--no-insert", action="store_true", help="skip the insert-maintenance run")
     ap.add_argument("--serve-queries", type=int, default=10_000)
     ap.add_argument("--serve-max-rows", type=int, default=50_000_000,
                     help="largest pool relation")
@@ -571,6 +572,42 @@ def chain3_run(torch, sj, ctx, stream):
                                sample="the full 3-way chain; the oracle's plain binary hash join")}
 
 
+# ----------------------------------------------------------------------------- insert maintenance
+def insert_run(torch, sj, ctx, stream, rels, w):
+    """Insert maintenance (Sec. 2.4) on the 4-way chain: R2's filter on k2
+    (built from its 10M rows) takes 1M new R2 tuples drawn like R2, gated by
+    R1's filter on k1; a fresh filter for every timed call."""
+    from paper_2308_16370_b300 import inputs
+    new = inputs.zipf_chain(nrows=1_000_000, domain=5_000_000, seed=99)["rels"][1]
+    nrel = ctx.load_relation([torch.from_numpy(c).cuda() for c in new], where="copy")
+    gate = ctx.build_filter(rels[0], 1, bits_per_key=8, k=3)
+    ts, counts = [], None
+    for rep in range(12):
+        f = ctx.build_filter(rels[1], 1, bits_per_key=8, k=3)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, counts = ctx.filter_insert(f, nrel, 1, gates=[(0, gate)])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if rep >= 2:
+            ts.append(e0.elapsed_time(e1))
+        f.free()
+    gate.free()
+    nrel.free()
+    ms = float(np.median(ts))
+    n = len(new[0])
+    assert sum(counts) == n
+    # the key and the gate column of every row, its status byte, the new keys' words
+    alg = (4.0 + 4.0 + 1.0) * n + 4.0 * counts[2]
+    return {"rows": n, "ms": ms, "rows_per_s": n / (ms / 1000.0),
+            "gated": counts[0], "contained": counts[1], "new": counts[2],
+            "alg_bytes": alg, "achieved_gbs": alg / (ms / 1000.0) / 1e9,
+            "workload": "1M new R2 tuples (drawn like R2) into R2's 10M-row filter on k2, "
+                        "gated by R1's filter on k1; counts read back (one sync)"}
+
+
 # ----------------------------------------------------------------------------- star join
 def freitag_run(torch, sj, ctx, stream, r=1_000_000, d=4):
     """The synthetic R, S, T benchmark of Sec. 3.1.1 at r = 1e6, d = 4: unary
@@ -995,6 +1032,10 @@ def main():
     if extras and not args.no_cyclic:
         cyclic = cyclic_run(torch, sj, ctx, stream)
 
+    insert = None
+    if extras and not args.no_insert:
+        insert = insert_run(torch, sj, ctx, stream, rels, w)
+
     star = None
     if extras and not args.no_star:
         star = star_run(torch, sj, ctx, stream)
@@ -1048,6 +1089,7 @@ def main():
                            "GBps": (v["bytes"] / (v["ms"] / 1000.0) / 1e9) if v["ms"] > 0 else None}
                        for k, v in kstats.items() if v["launches"]}},
         "chain3_latency": chain3,
+        "insert_maintenance": insert,
         "serving": serving,
         "cyclic_triangles": cyclic,
         "star": star,
