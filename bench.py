@@ -464,6 +464,39 @@ def serving_run(args, torch, sj):
                        "filter_cache_misses": st_c["cache_misses"],
                        "peak_concurrency": st_c["peak_concurrency"],
                        "batches": st_c["batches"], "peak_batch": st_c["peak_batch"]}
+    # the pruning phases alone: small queries one call each, then 16 per
+    # batched call (the same filters and sieved rows; host clock, each call
+    # synchronises)
+    prune = None
+    with sj.Context(0) as pctx:
+        prels = [pctx.load_relation(c, where="borrow") for c in dev]
+        small = [q for q in qs if sum(sizes[r] for r in q["rels"]) <= args.serve_batch_max_rows][:256]
+        pq = [{"rels": [prels[r] for r in q["rels"]], "edges": q["edges"], "preds": q["preds"],
+               "root": q["root"]} for q in small]
+        if pq:
+            def alone():
+                for q in pq:
+                    pctx.sieve_path(q["rels"], q["edges"], q["preds"], q["root"])
+
+            def batched():
+                for i in range(0, len(pq), 16):
+                    pctx.sieve_path_batch(pq[i:i + 16])
+
+            def best_of(fn, reps=3):
+                out = float("inf")
+                for _ in range(reps):
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    fn()
+                    torch.cuda.synchronize()
+                    out = min(out, time.perf_counter() - t0)
+                return out
+
+            alone(), batched()
+            ta, tb = best_of(alone), best_of(batched)
+            prune = {"queries": len(pq), "us_per_query_alone": ta / len(pq) * 1e6,
+                     "us_per_query_batched_16": tb / len(pq) * 1e6,
+                     "queries_below_rows": args.serve_batch_max_rows}
     # every result (or as many as the CPU budget allows, in a seeded random
     # order) against the oracle's chain counting over all host cores
     nth = os.cpu_count() or 1
@@ -489,6 +522,7 @@ def serving_run(args, torch, sj):
             "rate_qps": at07["rate_qps"], "qps": at07["qps"], "closed_loop_qps": base["closed_loop_qps"],
             "p50_ms": at07["p50_ms"], "p99_ms": at07["p99_ms"], "failed": base["failed"],
             "modes": modes, "mix_equals_closed_loop": all(m["same_results"] for m in modes.values()),
+            "pruning_alone_vs_batched": prune,
             "oracle_checked": checked, "oracle_agree": agree, "oracle_threads": nth,
             "oracle_check_s": check_s,
             "oracle_check": "all queries" if checked == len(qs) else
