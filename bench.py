@@ -497,8 +497,28 @@ def serving_run(args, torch, sj):
             prune = {"queries": len(pq), "us_per_query_alone": ta / len(pq) * 1e6,
                      "us_per_query_batched_16": tb / len(pq) * 1e6,
                      "queries_below_rows": args.serve_batch_max_rows}
-    # every result (or as many as the CPU budget allows, in a seeded random
-    # order) against the oracle's chain counting over all host cores
+    # every result against the oracle's stored values for this workload
+    # (tests/golden/serving_expected.txt, written by the oracle alone),
+    # when the workload is the stored one
+    stored = None
+    gpath = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden",
+                         "serving_expected.txt")
+    tag = (f"serving_pool(nrel=40, min_rows=10000, max_rows={int(args.serve_max_rows)}, "
+           f"domain={domain}, seed=5); serving_queries(nq={len(qs)}, seed=6)")
+    if os.path.exists(gpath):
+        head, exp_rows = [], {}
+        with open(gpath) as f:
+            for line in f:
+                if line.startswith("#"):
+                    head.append(line[1:].strip())
+                elif line.strip():
+                    i, c, sm = line.split()
+                    exp_rows[int(i)] = (0, int(c), int(sm))
+        if tag in head and len(exp_rows) == len(qs):
+            stored = {"file": "tests/golden/serving_expected.txt", "checked": len(qs),
+                      "agree": int(sum(ref[i] == exp_rows[i] for i in range(len(qs))))}
+    # and a seeded random sample (or all, as the CPU budget allows) recomputed
+    # live by the oracle's chain counting over all host cores
     nth = os.cpu_count() or 1
     oracle.set_threads(nth)
     order = [int(i) for i in np.random.default_rng(8).permutation(len(qs))]
@@ -523,10 +543,13 @@ def serving_run(args, torch, sj):
             "p50_ms": at07["p50_ms"], "p99_ms": at07["p99_ms"], "failed": base["failed"],
             "modes": modes, "mix_equals_closed_loop": all(m["same_results"] for m in modes.values()),
             "pruning_alone_vs_batched": prune,
+            "stored_oracle_check": stored,
             "oracle_checked": checked, "oracle_agree": agree, "oracle_threads": nth,
             "oracle_check_s": check_s,
-            "oracle_check": "all queries" if checked == len(qs) else
-                            f"a seeded random {checked} of {len(qs)} (CPU budget {args.serve_check_s} s)",
+            "oracle_check": ((f"all {len(qs)} against the oracle's stored values, " if stored else "") +
+                             ("all queries recomputed live" if checked == len(qs) else
+                              f"a seeded random {checked} of {len(qs)} recomputed live "
+                              f"(CPU budget {args.serve_check_s} s)")),
             "pool_rows": int(sum(sizes)), "pool_gen_s": gen_s,
             "pool": f"40 relations (x, y), log-uniform 1e4..{args.serve_max_rows:.0e} rows, "
                     f"Zipf(0.8) keys over 2^22; chains of 2-6, predicate on the first relation "
@@ -553,7 +576,7 @@ def cpu_rates(fn, units, budget_s=8.0, max_reps=20):
     return {"1_thread": out[1], "nproc": out[nproc]}
 
 
-# ----------------------------------------------------------------------------- C1 latency
+# ----------------------------------------------------------------------------- 3-way chain latency
 def chain3_run(torch, sj, ctx, stream):
     """The 3-way chain R(a,b) S(b,c) T(c,d), 100k rows each, keys uniform in
     [0, 50000), 8 bits per key and k = 3: the latency of one query as a caller

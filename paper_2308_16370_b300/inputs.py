@@ -168,16 +168,25 @@ def random_tree_join(g: np.random.Generator, nrel: int, nrows, domain: int,
             "root": int(g.integers(0, nrel)), "sum": sums}
 
 
+def serving_pool_sizes(nrel: int = 40, min_rows: int = 10_000, max_rows: int = 50_000_000,
+                       seed: int = 5) -> np.ndarray:
+    """Row counts of the serving pool's relations (log-uniform in [min_rows, max_rows])."""
+    g = _rng(seed, 0)
+    return np.exp(g.uniform(np.log(min_rows), np.log(max_rows), nrel)).astype(np.int64)
+
+
 def serving_pool(nrel: int = 40, min_rows: int = 10_000, max_rows: int = 50_000_000,
-                 domain: int = 1 << 22, s: float = 0.8, seed: int = 5, device=None):
+                 domain: int = 1 << 22, s: float = 0.8, seed: int = 5, device=None, only=None):
     """Resident relation pool for the serving workload: relations R_j(x, y)
     with log-uniform sizes in [min_rows, max_rows] and Zipf(s) keys over the
     domain, each column through its own seeded permutation.  ``device`` (a
     torch device) runs the inverse-CDF lookup and the permutation there: the
     same comparisons on the same float64 values, so the same columns, faster
-    for pools of hundreds of millions of rows.  Returns numpy columns."""
-    g = _rng(seed, 0)
-    sizes = np.exp(g.uniform(np.log(min_rows), np.log(max_rows), nrel)).astype(np.int64)
+    for pools of hundreds of millions of rows.  ``only`` (relation indices)
+    generates just those relations, each as in the full pool (every relation
+    draws from its own seeded stream); the others are None.  Returns numpy
+    columns."""
+    sizes = serving_pool_sizes(nrel, min_rows, max_rows, seed)
     w = 1.0 / np.power(np.arange(1, domain + 1, dtype=np.float64), s)
     cdf = np.cumsum(w)
     cdf /= cdf[-1]
@@ -187,6 +196,9 @@ def serving_pool(nrel: int = 40, min_rows: int = 10_000, max_rows: int = 50_000_
         cdf_t = torch.from_numpy(cdf).to(device)
     pool = []
     for j in range(nrel):
+        if only is not None and j not in only:
+            pool.append(None)
+            continue
         cols = []
         for c in range(2):
             gj = _rng(seed, 1 + j, c)
