@@ -239,7 +239,7 @@ SJ_API sj_status sj_sieve(sj_ctx *ctx, sj_rel rel, int nprobe, const int *key_co
  * not valid.  The work is enqueued on cuda_stream (NULL = legacy default
  * stream) of the current device; nothing is synchronised.
  *
- * Its scratch is one fixed device array of about 64 KiB inside this library
+ * Its scratch is one fixed device array of about 66 KiB inside this library
  * (held by every GPU that loads the library until the process exits), sized
  * for SJ_NOALLOC_MAX_ROWS rows; larger relations are rejected with SJ_EINVAL.
  * Every call shares that array and clears what must start at zero, so calls

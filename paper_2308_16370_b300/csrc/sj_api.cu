@@ -393,14 +393,19 @@ sj_status sync_read(sj_ctx* c) {
 
 uint32_t* status_ptr(sj_ctx* c) { return reinterpret_cast<uint32_t*>(c->d_misc + kMiscStatus); }
 
-// Scratch for one look-back scan: the tile ticket counter and NCH packed state
-// words per tile.  States carry a per-launch epoch and the kernel resets the
-// ticket counter, so the area is zeroed only when (re)allocated or when the
-// 16-bit epoch wraps.
+// Scratch for one look-back scan: a kAlign-byte header with the tile ticket
+// counter (byte 0) and the finish counter of a group-prefix sieve (byte 4),
+// then the group words (one for every 33 words of the area, so at least one
+// per 32 state words; their place depends only on the area's size), then NCH
+// packed state words per tile.  States carry a per-launch epoch, and the
+// kernels reset the ticket counter, the group words and the finish counter,
+// so the area is zeroed only when (re)allocated or when the 16-bit epoch
+// wraps.
 template <int NCH>
-sj_status scratch_for(sj_ctx* c, int64_t ntiles, uint32_t** counter, LookBack<NCH>* lb) {
+sj_status scratch_for(sj_ctx* c, int64_t ntiles, uint32_t** counter, LookBack<NCH>* lb,
+                      uint64_t** grp = nullptr, uint32_t** fin = nullptr) {
   if (ntiles < 1) ntiles = 1;
-  const size_t need = kAlign + (size_t)ntiles * NCH * 8;
+  const size_t need = kAlign + 33 * 8 * (((size_t)ntiles * NCH + 31) / 32 + 1);
   if (need > c->scratch_bytes) {
     // the old scratch may still be used by enqueued work: stream-ordered free
     raw_free(c, c->scratch, c->scratch_bytes);
@@ -416,8 +421,11 @@ sj_status scratch_for(sj_ctx* c, int64_t ntiles, uint32_t** counter, LookBack<NC
     SJ_CUDA(c, cudaMemsetAsync(c->scratch, 0, c->scratch_bytes, c->stream));
     c->epoch = 1;
   }
+  const size_t ngrp = (c->scratch_bytes - kAlign) / 8 / 33;
   *counter = reinterpret_cast<uint32_t*>(c->scratch);
-  lb->st = reinterpret_cast<uint64_t*>(c->scratch + kAlign);
+  if (grp) *grp = reinterpret_cast<uint64_t*>(c->scratch + kAlign);
+  if (fin) *fin = reinterpret_cast<uint32_t*>(c->scratch + 4);
+  lb->st = reinterpret_cast<uint64_t*>(c->scratch + kAlign) + ngrp;
   lb->status = status_ptr(c);
   lb->epoch = c->epoch;
   return SJ_OK;
@@ -517,7 +525,8 @@ sj_status sieve_step_timed(sj_ctx* c, const sj_rel_s* in, const std::vector<Test
     }
   }
   a.chunk_rows = sieve_chunk_rows(cap, c->num_sms);
-  sj_status st = scratch_for<1>(c, (cap + a.chunk_rows - 1) / a.chunk_rows, &a.tile_counter, &a.lb);
+  sj_status st = scratch_for<1>(c, (cap + a.chunk_rows - 1) / a.chunk_rows, &a.tile_counter, &a.lb,
+                                &a.grp, &a.fin);
   if (st != SJ_OK) {
     free_rel(c, r);
     return st;

@@ -5,7 +5,8 @@
 //   k_bloom_probe    -- membership test (Sec. 2.1 step 3)
 //   k_sieve_chunk    -- one pruning step (Sec. 2.2): key loads, filter probes,
 //                       survivor bits by warp ballots, order-preserving
-//                       compaction with a CTA-wide decoupled look-back
+//                       compaction with chunk offsets from per-32-chunk
+//                       group sums (or a CTA-wide decoupled look-back)
 //   k_sieve_batch, k_bloom_build_batch -- the sieve steps / filter builds of
 //                       many queries' pruning phases in one launch each
 //   k_insert_*       -- insert maintenance of a built filter (Sec. 2.4)
@@ -418,11 +419,15 @@ __device__ __forceinline__ uint32_t test8(const SieveTest& t, const int32_t* key
 //     of rows 32 j .. 32 j + 31 in row order; lane 0 stores the tile's eight
 //     words in shared memory;
 //  2. count: a block scan of the tiles' popcounts gives each tile's offset in
-//     the chunk and the chunk total, which is published for the look-back;
+//     the chunk and the chunk total, which is published in the chunk's state
+//     word and added to its group's word (groups of 32 chunks);
 //  3. list: every survivor's row offset (16 bits) goes to its rank in a
 //     shared-memory list;
-//  4. look-back: the whole CTA reads the states of the 1024 chunks before it at
-//     once and sums back to the nearest inclusive prefix (bounded waits);
+//  4. offset: the sum of the earlier groups (each once all 32 of its chunks
+//     have arrived) plus the states of the earlier chunks of the chunk's own
+//     group (bounded waits); without group words, a look-back in which the
+//     whole CTA reads the states of the 1024 chunks before it at once and
+//     sums back to the nearest inclusive prefix;
 //  5. write: thread i moves survivors i, i + 256, ... of every column, so a
 //     chunk's gathers are in flight together and its output stores contiguous;
 //  6. filters that the following builds write (a.zero_*) are cleared here,
@@ -594,6 +599,78 @@ __device__ uint64_t ck_lookback(const LookBack<1>& lb, uint32_t t, int* s_stop, 
     __syncthreads();  // s_stop and s_red are reused
     if (stop != 0x7fffffff) return excl;
     hi -= kCkWindow;
+  }
+}
+
+// Exclusive prefix of chunk t from the group words (all threads get it).
+// Chunk t's kept-row count is in its state word and in grp[t / 32]
+// (arrivals << 32 | sum of counts).  Warp 0 adds the earlier groups, each once
+// it shows all 32 arrivals (their chunks hold earlier tickets, so they are
+// running or done); warp 1 adds the state words of the earlier chunks of t's
+// own group.  A chunk reads at most t / 32 + 31 words, where the look-back
+// reads all t states of the chunks before it.  A wait that gives up records
+// kErrTimeout and counts as 0, so the kernel always finishes.
+__device__ uint64_t ck_group_prefix(const LookBack<1>& lb, const uint64_t* grp, uint32_t t,
+                                    uint64_t* s_red) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t g = t >> 5;
+  uint64_t part = 0;
+  if (warp == 0) {
+    for (uint32_t g0 = 0; g0 < g; g0 += 32) {
+      const uint32_t gi = g0 + lane;
+      if (gi >= g) continue;
+      uint64_t w = ld_volatile_u64(grp + gi);
+      uint32_t spins = 0, ns = 8;
+      while ((w >> 32) != 32u) {
+        if (++spins > kSpinLimit) break;
+        __nanosleep(ns);
+        if (ns < 256) ns <<= 1;
+        w = ld_volatile_u64(grp + gi);
+      }
+      if ((w >> 32) == 32u) part += w & 0xffffffffull;
+      else atomicOr(lb.status, kErrTimeout);
+    }
+  } else if (warp == 1) {
+    const uint32_t ti = (g << 5) + (uint32_t)lane;
+    if (ti < t) {
+      uint64_t w = ld_volatile_u64(lb.st + ti);
+      uint32_t spins = 0, ns = 8;
+      while (lb_state<1>(lb, w) == 0) {
+        if (++spins > kSpinLimit) break;
+        __nanosleep(ns);
+        if (ns < 256) ns <<= 1;
+        w = ld_volatile_u64(lb.st + ti);
+      }
+      if (lb_state<1>(lb, w) != 0) part = w & kValueMask;
+      else atomicOr(lb.status, kErrTimeout);
+    }
+  }
+  if (warp < 2) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) part += __shfl_xor_sync(0xffffffffu, part, d);
+    if (lane == 0) s_red[warp] = part;
+  }
+  __syncthreads();
+  const uint64_t p = s_red[0] + s_red[1];
+  __syncthreads();  // s_red is reused
+  return p;
+}
+
+// Every CTA of a group-prefix launch calls this after its last read of the
+// group words; the last one to arrive clears the `ngroups` group words and the
+// finish counter, so the next launch on the same scratch starts from zeros.
+__device__ __forceinline__ void ck_group_finish(uint64_t* grp, uint32_t* fin, uint32_t ngroups) {
+  __shared__ uint32_t s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();  // this CTA's group atomic is performed before it counts as finished
+    s_last = atomicAdd(fin, 1u) == gridDim.x - 1 ? 1u : 0u;
+    if (s_last) __threadfence();
+  }
+  __syncthreads();
+  if (s_last) {
+    for (uint32_t i = threadIdx.x; i < ngroups; i += blockDim.x) grp[i] = 0ull;
+    if (threadIdx.x == 0) *fin = 0u;
   }
 }
 
@@ -783,14 +860,17 @@ __device__ __forceinline__ void ck_run_chunk(const SieveArgs& a, uint32_t t, CkS
   if (tid == 0) {
     Vec<1> agg;
     agg.v[0] = total;
-    lb_publish<1>(a.lb, t, t == 0 ? 2u : 1u, agg);
+    lb_publish<1>(a.lb, t, (t == 0 && !a.grp) ? 2u : 1u, agg);
+    if (a.grp) atomicAdd(reinterpret_cast<unsigned long long*>(a.grp + (t >> 5)), (1ull << 32) | total);
   }
   __syncthreads();
 
-  // 3.-5. survivors listed, look-back, writes
+  // 3.-5. survivors listed, offset (group prefix or look-back), writes
   const uint64_t prefix = ck_list_and_write(a, cbase, ntile, total, s_bits, s_toff, s_list, [&]() {
     uint64_t p = 0;
-    if (t > 0) {
+    if (a.grp) {
+      p = ck_group_prefix(a.lb, a.grp, t, s_red);
+    } else if (t > 0) {
       p = ck_lookback(a.lb, t, &sm.stop, s_red);
       if (tid == 0) {
         Vec<1> inc;
@@ -816,6 +896,11 @@ __global__ void __launch_bounds__(kCkThreads, K > 0 ? kCkMinBlocks : 4) k_sieve_
   if (threadIdx.x == 0) s_ticket = draw_ticket(a.tile_counter);
   __syncthreads();
   ck_run_chunk<K>(a, s_ticket, sm);
+  if (a.grp) {
+    const int64_t n = a.n_dev ? (int64_t)(*a.n_dev) : a.n_host;
+    const int64_t nchunks = (n + a.chunk_rows - 1) / a.chunk_rows;
+    ck_group_finish(a.grp, a.fin, (uint32_t)((nchunks + 31) / 32));
+  }
 }
 
 // Many sieve steps in one launch (the serving runtime's batches): task i's

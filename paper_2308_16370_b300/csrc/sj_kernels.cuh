@@ -64,14 +64,23 @@ struct SieveArgs {
   uint32_t* zero_words[kMaxZero];
   uint32_t zero_bpk[kMaxZero];
   uint64_t zero_cap_words[kMaxZero];
+  // group prefix (k_sieve_chunk): one word per 32 chunks, arrivals << 32 |
+  // kept rows, and a counter of finished CTAs; both zero at launch and
+  // cleared again by the launch's last CTA.  Null: the chunk offsets come
+  // from the look-back over the chunk states instead.
+  uint64_t* grp;
+  uint32_t* fin;
 };
 
 // Chunked single-launch sieve (k_sieve_chunk).  A CTA takes one chunk of
 // chunk_rows rows by ticket: it probes the chunk (survivor bits per row in
 // shared memory), lists its survivors in shared memory, gets its output offset
-// from a decoupled look-back over the chunks before it (read 1024 at a time by
-// the whole CTA) and writes its survivors.  Scratch: one ticket counter and
-// one look-back word per chunk (a.tile_counter, a.lb).  One wave of CTAs
+// from the counts of the chunks before it and writes its survivors.  The
+// offset is the sum of the earlier groups of 32 chunks (a.grp) plus the
+// states of the earlier chunks of its own group, or, without a.grp, a
+// decoupled look-back over the chunk states (read 1024 at a time by the whole
+// CTA).  Scratch: one ticket counter and one state word per chunk
+// (a.tile_counter, a.lb), plus the group words and finish counter.  One wave of CTAs
 // covers the input (chunks of up to kCkMaxRows rows; larger inputs take
 // several waves), so a launch runs fastest when it has the GPU to itself.
 constexpr int kCkThreads = 256;

@@ -24,11 +24,14 @@ namespace {
 // GPU with fewer than 1638 SMs; checked per call).
 constexpr int64_t kMaxRows = SJ_NOALLOC_MAX_ROWS;
 constexpr int64_t kMaxChunks = (kMaxRows + sj::kCkMaxRows - 1) / sj::kCkMaxRows;
+constexpr int64_t kMaxGroups = (kMaxChunks + 31) / 32;
 constexpr size_t kOffCounter = 0;    // uint32 chunk ticket
 constexpr size_t kOffStatus = 64;    // uint32 status word (when the caller passes none)
 constexpr size_t kOffHdr = 128;      // uint64 nblocks, uint64 rows inserted
-constexpr size_t kOffStates = 256;   // one packed look-back word per chunk
-constexpr size_t kScratchBytes = kOffStates + 8 * kMaxChunks;  // 64 KiB + 256 B
+constexpr size_t kOffFin = 192;      // uint32 finished-CTA counter of the group prefix
+constexpr size_t kOffGroups = 256;   // one word per 32 chunks (arrivals, kept rows)
+constexpr size_t kOffStates = kOffGroups + 8 * kMaxGroups;  // one packed state word per chunk
+constexpr size_t kScratchBytes = kOffStates + 8 * kMaxChunks;  // 66 KiB + 256 B
 
 static __device__ __align__(256) unsigned char g_sieve_scratch[kScratchBytes];
 
@@ -38,6 +41,7 @@ __global__ void k_noalloc_prepare(uint64_t nblocks, uint32_t nchunks, int clear_
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0) {
     *reinterpret_cast<uint32_t*>(g_sieve_scratch + kOffCounter) = 0u;
+    *reinterpret_cast<uint32_t*>(g_sieve_scratch + kOffFin) = 0u;
     if (clear_status) *reinterpret_cast<uint32_t*>(g_sieve_scratch + kOffStatus) = 0u;
     uint64_t* hdr = reinterpret_cast<uint64_t*>(g_sieve_scratch + kOffHdr);
     hdr[0] = nblocks;
@@ -45,6 +49,8 @@ __global__ void k_noalloc_prepare(uint64_t nblocks, uint32_t nchunks, int clear_
   }
   uint64_t* states = reinterpret_cast<uint64_t*>(g_sieve_scratch + kOffStates);
   for (uint32_t t = i; t < nchunks; t += gridDim.x * blockDim.x) states[t] = 0ull;
+  uint64_t* groups = reinterpret_cast<uint64_t*>(g_sieve_scratch + kOffGroups);
+  for (uint32_t t = i; t < (nchunks + 31) / 32; t += gridDim.x * blockDim.x) groups[t] = 0ull;
 }
 
 // Host code must not use g_sieve_scratch as an address: in host code the name
@@ -150,6 +156,8 @@ extern "C" sj_status sj_sieve_noalloc(void* cuda_stream, int ncols, const int32_
   a.lb.st = reinterpret_cast<uint64_t*>(base + kOffStates);
   a.lb.status = status ? status : reinterpret_cast<uint32_t*>(base + kOffStatus);
   a.lb.epoch = 0;  // the states are zeroed by k_noalloc_prepare
+  a.grp = reinterpret_cast<uint64_t*>(base + kOffGroups);  // zeroed there too
+  a.fin = reinterpret_cast<uint32_t*>(base + kOffFin);
   a.chunk_rows = chunk_rows;
   a.fast_words_ok = 1;  // nblocks < 2^32 is checked above, but the word count must be too
   if (nblocks * 8 >= (uint64_t(1) << 32)) a.fast_words_ok = 0;
