@@ -124,6 +124,26 @@ def test_sieve_step_exact(ctx, n, nprobe, use_pred):
     assert_rel_equal(rel_np(out), exp)
 
 
+@pytest.mark.parametrize("generic", [False, True])
+def test_sieve_step_more_chunks_than_one_wave(ctx, generic):
+    """13M rows: more 16,384-row chunks (794) than one wave of CTAs holds on a
+    148-SM GPU (740), so later chunks take their offsets from the groups of
+    chunks that have already finished; the register-blocked k = 4 probe and
+    the generic path (a predicate plus a filter)."""
+    n = 13_000_013
+    g = np.random.default_rng(77 + generic)
+    cols = [g.integers(0, 1 << 22, n, dtype=np.int32) for _ in range(2)]
+    src = g.integers(0, 1 << 22, 40_000, dtype=np.int32)
+    rel = ctx.load_relation(cols, where="host")
+    f = ctx.build_filter(ctx.load_relation([src], where="host"), 0, bits_per_key=8, k=4, seed=3)
+    of = oracle.bloom_build(src, 8, 4, 0, 3)
+    pred = (0, 1 << 20, 3 << 20) if generic else None
+    out = ctx.sieve(rel, [1], [f], pred)
+    exp = oracle.sieve(oracle.select(cols, pred), [(1, of)])
+    assert out.nrows == len(exp[0]) > 0
+    assert_rel_equal(rel_np(out), exp)
+
+
 # ------------------------------------------------------------------ sieve path
 def check_path(ctx, w, passes=sj.FWD_BWD, bpk=8, k=3, layout=0, seed=0):
     rels = load(ctx, w)
