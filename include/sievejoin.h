@@ -24,8 +24,9 @@
  *   - Device memory is taken from the allocator given to sj_create (or, when
  *     none is given, from the device's stream-ordered pool via
  *     cudaMallocAsync on the context stream).
- *   - Device-side waits (the look-back of the compaction scans and the probe
- *     chains of the hash tables) are bounded: when a bound is hit the kernel
+ *   - Device-side waits (the compaction scans' waits on the counts of earlier
+ *     chunks and tiles, and the probe chains of the hash tables) are
+ *     bounded: when a bound is hit the kernel
  *     records the error in a device status word and returns; the next call
  *     that synchronises reports SJ_ETIMEOUT or SJ_ETABLEFULL.
  */
@@ -524,7 +525,7 @@ SJ_API sj_status sj_sieve_join(sj_ctx *ctx, const sj_path *path, const sj_sieve_
 /*
  * Self-test of the bounded device waits (no counterpart in the paper): one
  * warp polls a device flag that nothing sets, with the bound and backoff of
- * the look-back waits.  The wait gives up after about a second, records
+ * the compaction scans' waits.  The wait gives up after about a second, records
  * SJ_ETIMEOUT in the status word and the kernel finishes; this call then
  * synchronises and returns SJ_ETIMEOUT, and the context stays usable.  It
  * faults or traps nothing.
