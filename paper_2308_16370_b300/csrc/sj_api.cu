@@ -61,10 +61,10 @@ struct sj_ctx {
   uint64_t* h_misc = nullptr;  // pinned
   uint8_t* scratch = nullptr;
   size_t scratch_bytes = 0;
-  uint32_t epoch = 0;  // look-back flag epoch of the last scan launch
+  uint32_t epoch = 0;  // state-word epoch of the last scan launch
   cudaEvent_t ev_wait = nullptr;  // host waits on one point of the stream
   // second stream: the device-sized join builds its multimaps there while the
-  // main stream probes; it has its own look-back scratch
+  // main stream probes; it has its own scan scratch
   cudaStream_t side = nullptr;
   uint8_t* scratch2 = nullptr;
   size_t scratch2_bytes = 0;
@@ -393,7 +393,7 @@ sj_status sync_read(sj_ctx* c) {
 
 uint32_t* status_ptr(sj_ctx* c) { return reinterpret_cast<uint32_t*>(c->d_misc + kMiscStatus); }
 
-// Scratch for one look-back scan: a kAlign-byte header with the tile ticket
+// Scratch for one compaction scan: a kAlign-byte header with the tile ticket
 // counter (byte 0) and the finish counter of a group-prefix sieve (byte 4),
 // then the group words (one for every 33 words of the area, so at least one
 // per 32 state words; their place depends only on the area's size), then NCH
@@ -3068,7 +3068,7 @@ void capture_graph(sj_ctx* c, uint64_t key, const sj_path* path, const sj_sieve_
   if (swapped) std::swap(c->stream, c->cap_stream);
   if (swapped && cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
     c->capturing = true;
-    // look-back flags and tile tickets start from zero in every replay
+    // state words, group words and tickets start from zero in every replay
     sj_status st = SJ_OK;
     if (c->scratch && cudaMemsetAsync(c->scratch, 0, c->scratch_bytes, c->stream) != cudaSuccess)
       st = SJ_ECUDA;
