@@ -1364,10 +1364,41 @@ __global__ void __launch_bounds__(kBlock) k_mm_expand(MMExpandArgs a) {
   }
 }
 
+// Largest q in [lo, hi] with o[q] <= j (o strictly increasing, o[lo] <= j),
+// by a whole warp: each round the 32 lanes test 32 evenly spaced entries and
+// keep the interval after the last one that is <= j, so a search over Q
+// entries takes about log32(Q) dependent loads instead of log2(Q).  All lanes
+// return the answer.
+__device__ __forceinline__ uint64_t warp_upper_q(const uint64_t* o, uint64_t lo, uint64_t hi,
+                                                 uint64_t j) {
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    const uint64_t n = hi - lo + 1;
+    const uint64_t step = n <= 32 ? 1 : (n + 31) / 32;  // 32 steps cover [lo, hi]
+    const uint64_t pos = lo + (uint64_t)lane * step;
+    const bool le = pos <= hi && __ldg(o + pos) <= j;
+    const uint32_t m = __ballot_sync(0xffffffffu, le);  // lane 0 always: o[lo] <= j
+    const int k = 31 - __clz(m);
+    if (step == 1) return lo + (uint64_t)k;
+    const uint64_t nlo = lo + (uint64_t)k * step;
+    const uint64_t nhi = nlo + step - 1;
+    lo = nlo;
+    if (nhi < hi) hi = nhi;
+  }
+}
+
 // Device-sized expand: T and Q come from the probe's totals on the device;
 // outputs beyond `cap` are not written and the overflow is reported, so the
-// host can rerun the level with an exact buffer.
+// host can rerun the level with an exact buffer.  A CTA takes kExpRange
+// consecutive outputs [J0, J1): warps 0 and 1 find the hits holding J0 and
+// J1 - 1 (warp_upper_q), the offsets of the hits in between (at most
+// kExpRange, as every hit has at least one output) go to shared memory, and
+// each thread finds its output's hit there, so an output waits on a few
+// global round trips instead of a binary search through global memory.
+constexpr int kExpRange = kBlock;
 __global__ void __launch_bounds__(kBlock) k_mm_expand_dev(MMExpandArgs a) {
+  __shared__ uint64_t s_o[kExpRange];
+  __shared__ uint64_t s_q[2];
   const uint64_t Q = __ldg(a.totals_dev);
   const uint64_t T = __ldg(a.totals_dev + 1);
   const uint64_t lim = T < a.cap ? T : a.cap;
@@ -1375,19 +1406,39 @@ __global__ void __launch_bounds__(kBlock) k_mm_expand_dev(MMExpandArgs a) {
     *a.n_out = lim;
     if (T > a.cap) atomicOr(a.status, kErrCapacity);
   }
-  const uint64_t stride = (uint64_t)gridDim.x * kBlock;
-  for (uint64_t j = (uint64_t)blockIdx.x * kBlock + threadIdx.x; j < lim; j += stride) {
-    const uint64_t q = upper_q(a.o, 0, Q - 1, j);
-    const uint64_t t = j - __ldg(a.o + q);
-    const int32_t prow = __ldg(a.prow + q);
-    const int32_t brow = __ldg(a.rows + __ldg(a.off + __ldg(a.pid + q)) + t);
-#pragma unroll
-    for (int c = 0; c < kMaxCols; ++c)
-      if (c < a.nout) a.out[c][j] = __ldg(a.src[c] + (a.src_build[c] ? brow : prow));
-    if (a.psum_out) {
-      const uint64_t ps = a.psum_in ? __ldg(a.psum_in + prow) : term_sum(a.probe_terms, prow);
-      a.psum_out[j] = ps + term_sum(a.build_terms, brow);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  for (uint64_t J0 = (uint64_t)blockIdx.x * kExpRange; J0 < lim; J0 += (uint64_t)gridDim.x * kExpRange) {
+    const uint64_t J1 = J0 + kExpRange < lim ? J0 + kExpRange : lim;
+    if (warp < 2) {
+      const uint64_t q = warp_upper_q(a.o, 0, Q - 1, warp == 0 ? J0 : J1 - 1);
+      if ((tid & 31) == 0) s_q[warp] = q;
     }
+    __syncthreads();
+    const uint64_t q0 = s_q[0];
+    const uint32_t nq = (uint32_t)(s_q[1] - q0 + 1);
+    if ((uint32_t)tid < nq) s_o[tid] = __ldg(a.o + q0 + tid);
+    __syncthreads();
+    const uint64_t j = J0 + (uint64_t)tid;
+    if (j < J1) {
+      uint32_t lo = 0, hi = nq - 1;  // largest i with s_o[i] <= j; s_o[0] <= J0 <= j
+      while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (s_o[mid] <= j) lo = mid;
+        else hi = mid - 1;
+      }
+      const uint64_t q = q0 + lo;
+      const uint64_t t = j - s_o[lo];
+      const int32_t prow = __ldg(a.prow + q);
+      const int32_t brow = __ldg(a.rows + __ldg(a.off + __ldg(a.pid + q)) + t);
+#pragma unroll
+      for (int c = 0; c < kMaxCols; ++c)
+        if (c < a.nout) a.out[c][j] = __ldg(a.src[c] + (a.src_build[c] ? brow : prow));
+      if (a.psum_out) {
+        const uint64_t ps = a.psum_in ? __ldg(a.psum_in + prow) : term_sum(a.probe_terms, prow);
+        a.psum_out[j] = ps + term_sum(a.build_terms, brow);
+      }
+    }
+    __syncthreads();  // s_o and s_q are rewritten for the next range
   }
 }
 
