@@ -1333,42 +1333,11 @@ __global__ void __launch_bounds__(kBlock) k_mm_probe(MMProbeArgs a) {
   }  // tile loop (the scan's barriers order s_tile / s_prefix reuse)
 }
 
-// Largest q in [lo, hi] with o[q] <= j (o strictly increasing, o[lo] <= j).
-__device__ __forceinline__ uint64_t upper_q(const uint64_t* o, uint64_t lo, uint64_t hi,
-                                            uint64_t j) {
-  while (lo < hi) {
-    const uint64_t mid = (lo + hi + 1) >> 1;
-    if (__ldg(o + mid) <= j) lo = mid;
-    else hi = mid - 1;
-  }
-  return lo;
-}
-
-// One thread per output tuple j: the matching probe row is the largest q with
-// o[q] <= j (binary search; the upper levels of the search stay in L1), and
-// the build row is the (j - o[q])-th row of that key's group.  A hot key's
-// fan-out is spread over as many threads as it has outputs.
-__global__ void __launch_bounds__(kBlock) k_mm_expand(MMExpandArgs a) {
-  const uint64_t j = (uint64_t)blockIdx.x * kBlock + threadIdx.x;
-  if (j >= a.T) return;
-  const uint64_t q = upper_q(a.o, 0, a.Q - 1, j);
-  const uint64_t t = j - __ldg(a.o + q);
-  const int32_t prow = __ldg(a.prow + q);
-  const int32_t brow = __ldg(a.rows + __ldg(a.off + __ldg(a.pid + q)) + t);
-#pragma unroll
-  for (int c = 0; c < kMaxCols; ++c)
-    if (c < a.nout) a.out[c][j] = __ldg(a.src[c] + (a.src_build[c] ? brow : prow));
-  if (a.psum_out) {
-    const uint64_t ps = a.psum_in ? __ldg(a.psum_in + prow) : term_sum(a.probe_terms, prow);
-    a.psum_out[j] = ps + term_sum(a.build_terms, brow);
-  }
-}
-
 // Largest q in [lo, hi] with o[q] <= j (o strictly increasing, o[lo] <= j),
 // by a whole warp: each round the 32 lanes test 32 evenly spaced entries and
 // keep the interval after the last one that is <= j, so a search over Q
-// entries takes about log32(Q) dependent loads instead of log2(Q).  All lanes
-// return the answer.
+// entries takes about log32(Q) dependent loads instead of the log2(Q) of a
+// per-thread binary search.  All lanes return the answer.
 __device__ __forceinline__ uint64_t warp_upper_q(const uint64_t* o, uint64_t lo, uint64_t hi,
                                                  uint64_t j) {
   const int lane = threadIdx.x & 31;
@@ -1387,25 +1356,18 @@ __device__ __forceinline__ uint64_t warp_upper_q(const uint64_t* o, uint64_t lo,
   }
 }
 
-// Device-sized expand: T and Q come from the probe's totals on the device;
-// outputs beyond `cap` are not written and the overflow is reported, so the
-// host can rerun the level with an exact buffer.  A CTA takes kExpRange
-// consecutive outputs [J0, J1): warps 0 and 1 find the hits holding J0 and
-// J1 - 1 (warp_upper_q), the offsets of the hits in between (at most
-// kExpRange, as every hit has at least one output) go to shared memory, and
-// each thread finds its output's hit there, so an output waits on a few
-// global round trips instead of a binary search through global memory.
+// Expansion: one thread per output tuple j; its hit is the largest q with
+// o[q] <= j and its build row the (j - o[q])-th row of that key's group, so a
+// hot key's fan-out is spread over as many threads as it has outputs.  A CTA
+// takes kExpRange consecutive outputs [J0, J1): warps 0 and 1 find the hits
+// holding J0 and J1 - 1 (warp_upper_q), the offsets of the hits in between
+// (at most kExpRange, as every hit has at least one output) go to shared
+// memory, and each thread finds its output's hit there, so an output waits on
+// a few global round trips instead of a binary search through global memory.
 constexpr int kExpRange = kBlock;
-__global__ void __launch_bounds__(kBlock) k_mm_expand_dev(MMExpandArgs a) {
+__device__ __forceinline__ void expand_ranges(const MMExpandArgs& a, uint64_t Q, uint64_t lim) {
   __shared__ uint64_t s_o[kExpRange];
   __shared__ uint64_t s_q[2];
-  const uint64_t Q = __ldg(a.totals_dev);
-  const uint64_t T = __ldg(a.totals_dev + 1);
-  const uint64_t lim = T < a.cap ? T : a.cap;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    *a.n_out = lim;
-    if (T > a.cap) atomicOr(a.status, kErrCapacity);
-  }
   const int tid = threadIdx.x, warp = tid >> 5;
   for (uint64_t J0 = (uint64_t)blockIdx.x * kExpRange; J0 < lim; J0 += (uint64_t)gridDim.x * kExpRange) {
     const uint64_t J1 = J0 + kExpRange < lim ? J0 + kExpRange : lim;
@@ -1440,6 +1402,25 @@ __global__ void __launch_bounds__(kBlock) k_mm_expand_dev(MMExpandArgs a) {
     }
     __syncthreads();  // s_o and s_q are rewritten for the next range
   }
+}
+
+// Host-sized expand: T and Q known on the host.
+__global__ void __launch_bounds__(kBlock) k_mm_expand(MMExpandArgs a) {
+  if (a.T > 0) expand_ranges(a, a.Q, a.T);
+}
+
+// Device-sized expand: T and Q come from the probe's totals on the device;
+// outputs beyond `cap` are not written and the overflow is reported, so the
+// host can rerun the level with an exact buffer.
+__global__ void __launch_bounds__(kBlock) k_mm_expand_dev(MMExpandArgs a) {
+  const uint64_t Q = __ldg(a.totals_dev);
+  const uint64_t T = __ldg(a.totals_dev + 1);
+  const uint64_t lim = T < a.cap ? T : a.cap;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *a.n_out = lim;
+    if (T > a.cap) atomicOr(a.status, kErrCapacity);
+  }
+  expand_ranges(a, Q, lim);
 }
 
 __global__ void __launch_bounds__(kBlock) k_table_init(TableInitArgs a) {
