@@ -2152,7 +2152,7 @@ sj_status join_impl(sj_ctx* c, const sj_path* path, const sj_rel* inputs, int mo
       ap.status = status_ptr(c);
       {
         // the key of every probe row; a matching row's terms are not counted
-        // (their count is not known on the host, and they are a few per cent)
+        // (their count is known only on the device)
         Launch Lk(c, SJ_K_AGG, 4.0 * (double)ap.n);
         launch_agg_probe(ap, nsm, c->stream);
       }
@@ -2575,7 +2575,8 @@ sj_status join_async(sj_ctx* c, const sj_path* path, const sj_rel* in_rels, int 
       ap.status = status_ptr(c);
       {
         // the key of every probe row (a matching row's SUM terms or partial
-        // sum are read too but not counted: a few per cent of the rows)
+        // sum are read too but not counted: their count is known only on the
+        // device)
         Launch Lk = rows_launch(c, SJ_K_AGG, 4.0, pslot, phost);
         launch_agg_probe(ap, c->num_sms, c->stream);
       }

@@ -1540,8 +1540,9 @@ __global__ void __launch_bounds__(kBlock, 4) k_agg_probe(AggProbeArgs a) {
       int64_t sl[4];
 #pragma unroll
       for (int e = 0; e < 4; ++e) sl[e] = table_find_first(a.t, kk[e], b[e], q[e]);
-      // the SUM term of a row is read only when its key matches (a few per
-      // cent of the rows here), so the term column is not streamed
+      // the SUM term of a row is read only when its key matches, so rows
+      // without a match cost no term read (a term column in host memory is
+      // read only where a row matches)
       ulonglong2 cs[4];
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
