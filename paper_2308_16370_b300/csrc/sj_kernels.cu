@@ -1134,25 +1134,35 @@ __device__ __forceinline__ int64_t table_find_first(const Table& t, int32_t key,
 }
 
 // Per-CTA aggregation of skewed keys: a CTA takes kAggRows rows per round and
-// combines the rows of each key (dense id or table slot) in a shared-memory
-// table before touching global memory, so a key repeated r times in a round
-// costs one global atomic instead of r (Zipf-hot keys would otherwise
-// serialise on one address).
+// combines the rows of each key in a shared-memory table before touching the
+// global table, so a key repeated r times in a round costs one global insert
+// and one global atomic instead of r: the thread that entered the key in the
+// shared table (its leader) does both for the whole round.  Without it, the
+// first rows of a Zipf-hot key would all race on the same global slot with
+// compare-and-swaps that serialise.
 constexpr int kAggPerThread = 2;
 constexpr int kAggRows = kBlock * kAggPerThread;
 constexpr int kAggSlotsLog2 = 10;
 constexpr int kAggSlots = 1 << kAggSlotsLog2;  // 2x the rows of a round: never full
 static_assert(kAggSlots >= 2 * kAggRows, "per-CTA table must hold every key of a round");
 
-// Shared-memory slot of `v` (inserted if absent), or -1 if the table is full.
-__device__ __forceinline__ int smem_slot(uint32_t* s_key, uint32_t v) {
-  uint32_t h = (v * 2654435761u) >> (32 - kAggSlotsLog2);
+// Shared-memory entry of `key` (entries hold (1 << 32) | key, 0 = empty),
+// inserted if absent; *lead is set for the one caller that inserted it.
+// Returns -1 if the table is full.
+__device__ __forceinline__ int smem_key_slot(unsigned long long* s_key, int32_t key, bool* lead) {
+  const unsigned long long want = (1ull << 32) | (uint32_t)key;
+  uint32_t h = ((uint32_t)key * 2654435761u) >> (32 - kAggSlotsLog2);
+  *lead = false;
   for (int p = 0; p < kAggSlots; ++p) {
-    const uint32_t cur = s_key[h];
-    if (cur == v) return (int)h;
-    if (cur == 0xffffffffu) {
-      const uint32_t old = atomicCAS(s_key + h, 0xffffffffu, v);
-      if (old == 0xffffffffu || old == v) return (int)h;
+    const unsigned long long cur = s_key[h];
+    if (cur == want) return (int)h;
+    if (cur == 0ull) {
+      const unsigned long long old = atomicCAS(s_key + h, 0ull, want);
+      if (old == 0ull) {
+        *lead = true;
+        return (int)h;
+      }
+      if (old == want) return (int)h;
     }
     h = (h + 1) & (kAggSlots - 1);
   }
@@ -1160,41 +1170,62 @@ __device__ __forceinline__ int smem_slot(uint32_t* s_key, uint32_t v) {
 }
 
 __global__ void __launch_bounds__(kBlock) k_mm_insert(MMInsertArgs a) {
-  __shared__ uint32_t s_key[kAggSlots];  // table slot, 0xffffffff = empty
-  __shared__ uint32_t s_cnt[kAggSlots];  // rows of the round, then their global base
+  __shared__ unsigned long long s_key[kAggSlots];  // tagged key, 0 = empty
+  __shared__ uint32_t s_cnt[kAggSlots];            // rows of the round, then their global base
+  __shared__ uint32_t s_slot[kAggSlots];           // the key's table slot, 0xffffffff = none
   a.t = resolve(a.t);
   a.n = dev_n(a.n_dev, a.n);
   const int tid = threadIdx.x;
   for (int64_t r0 = (int64_t)blockIdx.x * kAggRows; r0 < a.n; r0 += (int64_t)gridDim.x * kAggRows) {
     for (int i = tid; i < kAggSlots; i += kBlock) {
-      s_key[i] = 0xffffffffu;
+      s_key[i] = 0ull;
       s_cnt[i] = 0;
     }
     __syncthreads();
-    int64_t sl[kAggPerThread];
+    int32_t key[kAggPerThread];
     int j[kAggPerThread];
+    bool lead[kAggPerThread];
     uint32_t lr[kAggPerThread];
+    int64_t sl[kAggPerThread];  // rows of a full shared table go straight to the global one
 #pragma unroll
     for (int e = 0; e < kAggPerThread; ++e) {
       const int64_t row = r0 + e * kBlock + tid;
-      sl[e] = row < a.n ? table_find_or_insert(a.t, __ldcs(a.keys + row), a.status) : -1;
       j[e] = -1;
+      lead[e] = false;
       lr[e] = 0;
-      if (sl[e] >= 0) {
-        j[e] = smem_slot(s_key, (uint32_t)sl[e]);
-        lr[e] = j[e] >= 0 ? atomicAdd(s_cnt + j[e], 1u) : atomicAdd(a.cnt + sl[e], 1u);
+      sl[e] = -1;
+      if (row < a.n) {
+        key[e] = __ldcs(a.keys + row);
+        j[e] = smem_key_slot(s_key, key[e], &lead[e]);
+        if (j[e] >= 0) {
+          lr[e] = atomicAdd(s_cnt + j[e], 1u);
+        } else {
+          sl[e] = table_find_or_insert(a.t, key[e], a.status);
+          if (sl[e] >= 0) lr[e] = atomicAdd(a.cnt + sl[e], 1u);
+        }
       }
     }
     __syncthreads();
-    for (int i = tid; i < kAggSlots; i += kBlock)
-      if (s_key[i] != 0xffffffffu) s_cnt[i] = atomicAdd(a.cnt + s_key[i], s_cnt[i]);
+#pragma unroll
+    for (int e = 0; e < kAggPerThread; ++e) {
+      if (!lead[e]) continue;
+      const int64_t g = table_find_or_insert(a.t, key[e], a.status);
+      s_slot[j[e]] = g >= 0 ? (uint32_t)g : 0xffffffffu;
+      if (g >= 0) s_cnt[j[e]] = atomicAdd(a.cnt + g, s_cnt[j[e]]);
+    }
     __syncthreads();
 #pragma unroll
     for (int e = 0; e < kAggPerThread; ++e) {
       const int64_t row = r0 + e * kBlock + tid;
-      if (sl[e] >= 0) {
+      if (j[e] >= 0) {
+        const uint32_t g = s_slot[j[e]];
+        if (g != 0xffffffffu) {
+          a.rid[row] = g;
+          a.rank[row] = s_cnt[j[e]] + lr[e];
+        }
+      } else if (sl[e] >= 0) {
         a.rid[row] = (uint32_t)sl[e];
-        a.rank[row] = (j[e] >= 0 ? s_cnt[j[e]] : 0u) + lr[e];
+        a.rank[row] = lr[e];
       }
     }
     __syncthreads();  // the table is cleared by the next round
@@ -1444,8 +1475,8 @@ __global__ void __launch_bounds__(kBlock) k_table_init(TableInitArgs a) {
 
 // ---------------------------------------------------------------- aggregate level
 
-__global__ void __launch_bounds__(kBlock) k_agg_insert(AggInsertArgs a) {
-  __shared__ uint32_t s_key[kAggSlots];          // global slot, 0xffffffff = empty
+__global__ void __launch_bounds__(kBlock, 4) k_agg_insert(AggInsertArgs a) {
+  __shared__ unsigned long long s_key[kAggSlots];  // tagged key, 0 = empty
   __shared__ uint32_t s_cnt[kAggSlots];
   __shared__ unsigned long long s_sum[kAggSlots];
   a.t = resolve(a.t);
@@ -1454,23 +1485,29 @@ __global__ void __launch_bounds__(kBlock) k_agg_insert(AggInsertArgs a) {
   const int tid = threadIdx.x;
   for (int64_t r0 = (int64_t)blockIdx.x * kAggRows; r0 < a.n; r0 += (int64_t)gridDim.x * kAggRows) {
     for (int i = tid; i < kAggSlots; i += kBlock) {
-      s_key[i] = 0xffffffffu;
+      s_key[i] = 0ull;
       s_cnt[i] = 0;
       s_sum[i] = 0ull;
     }
     __syncthreads();
+    int32_t key[kAggPerThread];
+    int j[kAggPerThread];
+    bool lead[kAggPerThread];
 #pragma unroll
     for (int e = 0; e < kAggPerThread; ++e) {
       const int64_t row = r0 + e * kBlock + tid;
+      j[e] = -1;
+      lead[e] = false;
       if (row < a.n) {
-        const int64_t sl = table_find_or_insert(a.t, __ldcs(a.keys + row), a.status);
-        if (sl >= 0) {
-          const uint64_t val = with_sum ? (a.vals ? __ldg(a.vals + row) : term_sum(a.terms, row)) : 0ull;
-          const int j = smem_slot(s_key, (uint32_t)sl);
-          if (j >= 0) {
-            atomicAdd(s_cnt + j, 1u);
-            if (with_sum) atomicAdd(s_sum + j, (unsigned long long)val);
-          } else {
+        key[e] = __ldcs(a.keys + row);
+        const uint64_t val = with_sum ? (a.vals ? __ldg(a.vals + row) : term_sum(a.terms, row)) : 0ull;
+        j[e] = smem_key_slot(s_key, key[e], &lead[e]);
+        if (j[e] >= 0) {
+          atomicAdd(s_cnt + j[e], 1u);
+          if (with_sum) atomicAdd(s_sum + j[e], (unsigned long long)val);
+        } else {  // full shared table: straight to the global one
+          const int64_t sl = table_find_or_insert(a.t, key[e], a.status);
+          if (sl >= 0) {
             atomicAdd(&a.cs[sl].x, 1ull);
             if (with_sum) atomicAdd(&a.cs[sl].y, (unsigned long long)val);
           }
@@ -1478,11 +1515,13 @@ __global__ void __launch_bounds__(kBlock) k_agg_insert(AggInsertArgs a) {
       }
     }
     __syncthreads();
-    for (int i = tid; i < kAggSlots; i += kBlock) {
-      const uint32_t sl = s_key[i];
-      if (sl != 0xffffffffu) {
-        atomicAdd(&a.cs[sl].x, (unsigned long long)s_cnt[i]);
-        if (with_sum) atomicAdd(&a.cs[sl].y, s_sum[i]);
+#pragma unroll
+    for (int e = 0; e < kAggPerThread; ++e) {
+      if (!lead[e]) continue;
+      const int64_t sl = table_find_or_insert(a.t, key[e], a.status);
+      if (sl >= 0) {
+        atomicAdd(&a.cs[sl].x, (unsigned long long)s_cnt[j[e]]);
+        if (with_sum) atomicAdd(&a.cs[sl].y, s_sum[j[e]]);
       }
     }
     __syncthreads();  // the table is cleared by the next round
