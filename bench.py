@@ -383,6 +383,32 @@ def profiled_traffic(kernel: str, workload: str):
 
 
 # ----------------------------------------------------------------------------- serving
+STORED_SERVING = "tests/golden/serving_expected.txt"
+
+
+def stored_serving_results(max_rows: int, domain: int, nq: int):
+    """The oracle's stored (status 0, COUNT, SUM) of every query of the
+    serving workload, indexed by query, if the stored file covers this
+    workload (40 relations of 1e4..max_rows rows over `domain`, `nq`
+    queries, the bench's seeds); else None."""
+    path = os.path.join(ROOT, STORED_SERVING)
+    if not os.path.exists(path):
+        return None
+    tag = (f"serving_pool(nrel=40, min_rows=10000, max_rows={max_rows}, "
+           f"domain={domain}, seed=5); serving_queries(nq={nq}, seed=6)")
+    head, rows = [], {}
+    with open(path) as f:
+        for line in f:
+            if line.startswith("#"):
+                head.append(line[1:].strip())
+            elif line.strip():
+                i, c, sm = line.split()
+                rows[int(i)] = (0, int(c), int(sm))
+    if tag not in head or sorted(rows) != list(range(nq)):
+        return None
+    return rows
+
+
 def serving_run(args, torch, sj):
     """Poisson stream of chain queries (2-6 relations) over a resident pool of
     40 relations (log-uniform 1e4 .. --serve-max-rows rows, Zipf(0.8) keys
@@ -501,22 +527,10 @@ def serving_run(args, torch, sj):
     # (tests/golden/serving_expected.txt, written by the oracle alone),
     # when the workload is the stored one
     stored = None
-    gpath = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden",
-                         "serving_expected.txt")
-    tag = (f"serving_pool(nrel=40, min_rows=10000, max_rows={int(args.serve_max_rows)}, "
-           f"domain={domain}, seed=5); serving_queries(nq={len(qs)}, seed=6)")
-    if os.path.exists(gpath):
-        head, exp_rows = [], {}
-        with open(gpath) as f:
-            for line in f:
-                if line.startswith("#"):
-                    head.append(line[1:].strip())
-                elif line.strip():
-                    i, c, sm = line.split()
-                    exp_rows[int(i)] = (0, int(c), int(sm))
-        if tag in head and len(exp_rows) == len(qs):
-            stored = {"file": "tests/golden/serving_expected.txt", "checked": len(qs),
-                      "agree": int(sum(ref[i] == exp_rows[i] for i in range(len(qs))))}
+    exp_rows = stored_serving_results(int(args.serve_max_rows), domain, len(qs))
+    if exp_rows is not None:
+        stored = {"file": STORED_SERVING, "checked": len(qs),
+                  "agree": int(sum(ref[i] == exp_rows[i] for i in range(len(qs))))}
     # and a seeded random sample (or all, as the CPU budget allows) recomputed
     # live by the oracle's chain counting over all host cores
     nth = os.cpu_count() or 1

@@ -81,3 +81,15 @@ def test_subset_pool_equals_full_pool_relations():
     for j in (1, 3):
         for a, b in zip(full[j], part[j]):
             assert np.array_equal(a, b)
+
+
+def test_bench_reads_the_stored_results_for_its_workload_only():
+    """bench.py checks every served result against the stored values only
+    when they are for the workload it ran."""
+    import bench
+    rows = bench.stored_serving_results(MAX_ROWS, DOMAIN, NQ)
+    _, stored = load()
+    assert rows is not None and len(rows) == NQ
+    assert all(rows[i] == (0, c, s) for i, c, s in stored)
+    assert bench.stored_serving_results(5_000_000, DOMAIN, NQ) is None
+    assert bench.stored_serving_results(MAX_ROWS, DOMAIN, 2000) is None
