@@ -24,29 +24,30 @@ NQ, QUERY_SEED = 10_000, 6
 OUT = os.path.join(HERE, "serving_expected.txt")
 
 
-def main():
+def write(out=OUT, nrel=NREL, min_rows=MIN_ROWS, max_rows=MAX_ROWS, domain=DOMAIN, nq=NQ, log=print):
+    """The oracle's COUNT and SUM of every query of the workload, written to `out`."""
     t0 = time.time()
-    pool = inputs.serving_pool(nrel=NREL, min_rows=MIN_ROWS, max_rows=MAX_ROWS, domain=DOMAIN,
+    pool = inputs.serving_pool(nrel=nrel, min_rows=min_rows, max_rows=max_rows, domain=domain,
                                seed=POOL_SEED)
     sizes = [len(r[0]) for r in pool]
-    qs = inputs.serving_queries(sizes, NQ, domain=DOMAIN, seed=QUERY_SEED)
-    print(f"pool and queries in {time.time() - t0:.0f} s", flush=True)
+    qs = inputs.serving_queries(sizes, nq, domain=domain, seed=QUERY_SEED)
+    log(f"pool and queries in {time.time() - t0:.0f} s")
     oracle.set_threads(os.cpu_count() or 1)
-    cp = oracle.ChainPool(pool, DOMAIN)
+    cp = oracle.ChainPool(pool, domain)
     res = []
-    for i in range(0, NQ, 500):
+    for i in range(0, nq, 500):
         res += oracle.chain_agg(cp, qs[i:i + 500])
-        print(f"{len(res)} queries, {time.time() - t0:.0f} s", flush=True)
-    with open(OUT, "w") as f:
+        log(f"{len(res)} queries, {time.time() - t0:.0f} s")
+    with open(out, "w") as f:
         f.write("# Serving workload: the oracle's COUNT and SUM (mod 2^64) per query\n")
-        f.write(f"# serving_pool(nrel={NREL}, min_rows={MIN_ROWS}, max_rows={MAX_ROWS}, "
-                f"domain={DOMAIN}, seed={POOL_SEED}); serving_queries(nq={NQ}, seed={QUERY_SEED})\n")
+        f.write(f"# serving_pool(nrel={nrel}, min_rows={min_rows}, max_rows={max_rows}, "
+                f"domain={domain}, seed={POOL_SEED}); serving_queries(nq={nq}, seed={QUERY_SEED})\n")
         f.write(f"# pool rows {sum(sizes)}\n")
         f.write("# query count sum\n")
         for i, r in enumerate(res):
             f.write(f"{i} {r['count']} {r['sum']}\n")
-    print(f"wrote {OUT} in {time.time() - t0:.0f} s")
+    log(f"wrote {out} in {time.time() - t0:.0f} s")
 
 
 if __name__ == "__main__":
-    main()
+    write(log=lambda m: print(m, flush=True))

@@ -93,3 +93,29 @@ def test_bench_reads_the_stored_results_for_its_workload_only():
     assert all(rows[i] == (0, c, s) for i, c, s in stored)
     assert bench.stored_serving_results(5_000_000, DOMAIN, NQ) is None
     assert bench.stored_serving_results(MAX_ROWS, DOMAIN, 2000) is None
+
+
+def test_writer_on_a_small_workload(tmp_path):
+    """The script that writes the stored values, run on a small pool of the
+    same shape: its entries equal the oracle's second counting method."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("make_serving_expected",
+                                                  os.path.join(HERE, "golden", "make_serving_expected.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    out = tmp_path / "small.txt"
+    nrel, lo, hi, dom, nq = 6, 1_000, 20_000, 1 << 12, 40
+    mod.write(out=str(out), nrel=nrel, min_rows=lo, max_rows=hi, domain=dom, nq=nq, log=lambda m: None)
+    rows = [tuple(int(x) for x in ln.split()) for ln in out.read_text().splitlines()
+            if ln and not ln.startswith("#")]
+    assert [r[0] for r in rows] == list(range(nq))
+    pool = inputs.serving_pool(nrel=nrel, min_rows=lo, max_rows=hi, domain=dom, seed=POOL_SEED)
+    qs = inputs.serving_queries([len(r[0]) for r in pool], nq, domain=dom, seed=QUERY_SEED)
+    nonzero = 0
+    for (i, c, s), q in zip(rows, qs):
+        w = {"rels": [pool[r] for r in q["rels"]], "edges": q["edges"], "preds": q["preds"],
+             "root": q["root"], "sum": q["sum"]}
+        exp = oracle.agg_propagation(w)
+        assert (c, s) == (exp["count"], exp["sum"]), i
+        nonzero += c > 0
+    assert nonzero > 0
