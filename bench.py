@@ -127,7 +127,7 @@ def max_over_ranks(x: float, ws: int) -> float:
 # ----------------------------------------------------------------------------- clocks
 class _CtypesNvml:
     """The few read-only NVML queries the clock sampler needs, bound with
-    ctypes to the driver's libnvidia-ml when the pynvml module is absent."""
+    ctypes to NVIDIA's libnvidia-ml when the pynvml module is absent."""
     NVML_CLOCK_SM = 1
 
     def __init__(self):
@@ -194,7 +194,7 @@ class ClockSampler:
         try:
             import pynvml
         except ImportError:
-            pynvml = _CtypesNvml()  # the driver's libnvidia-ml through ctypes
+            pynvml = _CtypesNvml()  # NVIDIA's libnvidia-ml through ctypes
         pynvml.nvmlInit()
         try:
             import torch
